@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of exact KDE bandwidth selection on GB300 (arXiv 1505.01998).
+
+Metric: pair-bandwidth kernel evaluations per second.  One evaluation is one
+(pair i<j, bandwidth) term: an LSCV_h term for every grid point, or a psi_r
+term of the PLUGIN method.  One step = one LSCV_h selection on a 256-point
+grid over Z(h0) plus one PLUGIN selection (psi_6 and psi_4 over all pairs) of
+the n = 65,536 skewed column (half lognormal(0,1), half U[0,100], seed 2 +
+rank): P = n(n-1)/2 pairs, 258 P evaluations per step.
+
+  value     device time of K steps, samples resident in HBM (CUDA events)
+  e2e       the same selections through the host-buffer entry points:
+            pinned host samples in, results out, host wall clock
+  roofline  the all-pairs LSCV kernel timed live with CUDA events around its
+            launch, against the ALU roofline min(MUFU ex2/clk, FP32 lanes/3)
+            x SMs x the SM clock sampled during the timed region
+  cpu_baseline  the FP64 oracle on a bounded sample (rows of the pair
+            triangle, the same 256-point grid) on the host's cores
+
+--impl reference times the oracle alone (the reference arm).
+Multi-GPU (torchrun): every rank selects its own replica dataset (weak
+scaling, no collective on the data path); value = all ranks' evaluations
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 65536
+N_H = 256
+SEED = 2
+METRIC = "pair-bandwidth kernel evals/s"
+UNIT = "evals/s"
+WORKLOAD = ("skewed column n=65536 FP32 (lognormal(0,1) + U[0,100]); LSCV_h on a 256-point "
+            "log grid over Z(h0) + two-stage PLUGIN (psi_6, psi_4)")
+
+
+def pairs(n):
+    return n * (n - 1) // 2
+
+
+EVALS_LSCV = pairs(N) * N_H
+EVALS_PSI = 2 * pairs(N)
+EVALS_STEP = EVALS_LSCV + EVALS_PSI
+
+
+def set_n(n):
+    global N, EVALS_LSCV, EVALS_PSI, EVALS_STEP, WORKLOAD
+    if n != N:
+        WORKLOAD = WORKLOAD.replace(f"n={N}", f"n={n}")
+    N = n
+    EVALS_LSCV = pairs(N) * N_H
+    EVALS_PSI = 2 * pairs(N)
+    EVALS_STEP = EVALS_LSCV + EVALS_PSI
+LAUNCHES_PER_STEP = 5 + 6  # LSCV: setup, prep, pairs, reduce, finish; PLUGIN: setup, prep, 2 x (pairs, finish)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# --------------------------------------------------------------- oracle leg
+
+def oracle_sample(seconds: float, rank_seed: int = SEED):
+    """Time the FP64 oracle on a bounded sample of the same workload: LSCV
+    pair sums for rows [0, m) of the pair triangle against all later samples,
+    on the 256-point grid.  m is calibrated to take about `seconds`."""
+    import numpy as np
+
+    import oracle
+    from paper_1505_01998_gb300 import datagen
+
+    x = datagen.skewed_column(N, seed=rank_seed).astype(np.float64)
+    h = oracle.grid_default(N, 1, N_H)
+    cores = oracle.openmp_threads() or 1
+    t0 = time.perf_counter()
+    oracle.lscv_sums(x, h, block=(0, 2 * cores, 0, N))
+    dt = time.perf_counter() - t0
+    rate_rows = 2 * cores / max(dt, 1e-6)
+    m = int(max(cores, min(N - 1, rate_rows * seconds)))
+    t0 = time.perf_counter()
+    oracle.lscv_sums(x, h, block=(0, m, 0, N))
+    dt = time.perf_counter() - t0
+    npairs = sum(N - 1 - i for i in range(m))
+    return {"value": npairs * N_H / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"LSCV_h pair sums of rows 0..{m - 1} of the n={N} pair triangle "
+                      f"({npairs} pairs x {N_H} bandwidths, FP64, {dt:.1f} s)",
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    for _ in range(args.warmup):
+        oracle_sample(min(budget, 3.0))
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(budget)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "d": 1, "n_h": N_H, "seed": SEED,
+                       "sample": "rows of the pair triangle per step (bounded oracle sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--n", type=int, default=N,
+                    help="sample count (default 65536; smaller values only for profiling captures)")
+    args = ap.parse_args()
+    set_n(args.n)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, None, rank)
+    return run_gpu(args, world, rank, local)
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    x = datagen.skewed_column(N, seed=SEED + rank)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    grid, _keep = gbkde.make_grid(n_h=N_H)
+    ws_l = gbkde.workspace(gbkde.kde_workspace_size(N, 1, N_H), dev)
+    ws_p = gbkde.workspace(gbkde.kde_workspace_size(N, 1, 0), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    probe = gbkde.kde_probe_alu()
+
+    def step():
+        gbkde.kde_lscv_async(xd, grid, None, ws_l, stream)
+        gbkde.kde_plugin_async(xd, None, ws_p, stream)
+
+    W, K = max(3, args.warmup), args.steps
+    for _ in range(W):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    r_l, _ = gbkde.read_ws_result(ws_l, N_H)
+    r_p, _ = gbkde.read_ws_result(ws_p)
+    assert r_l["status"] == 0 and r_p["status"] == 0, (r_l, r_p)
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    for e6 in ev:
+        for e in e6:
+            e.record(stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for k in range(K):
+        flush.zero_()  # 256 MiB write (> 129 MB L2) between steps, outside the step events
+        e = ev[k]
+        e[0].record(stream)
+        gbkde.kde_set_kernel_events(e[2], e[3], e[4], e[5])
+        step()
+        e[1].record(stream)
+    gbkde.kde_set_kernel_events()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    lscv_ms = statistics.mean(ev[k][2].elapsed_time(ev[k][3]) for k in range(K))
+    psi_ms = statistics.mean(ev[k][4].elapsed_time(ev[k][5]) for k in range(K))
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = EVALS_STEP * world / (ms_per_step * 1e-3)
+
+    # ---- end to end: pinned host samples in, results out, through the public API
+    x_pin = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    xh = x_pin.numpy()
+    for _ in range(W):
+        gbkde.kde_lscv_host(xh, grid, None, ws_l, stream)
+        gbkde.kde_plugin_host(xh, None, ws_p, stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_s = 0.0
+    for _ in range(K):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        gbkde.kde_lscv_host(xh, grid, None, ws_l, stream)
+        gbkde.kde_plugin_host(xh, None, ws_p, stream)
+        e2e_s += time.perf_counter() - t1
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = EVALS_STEP * world * K / e2e_s
+    h2d = 2 * N * 4
+    d2h = 2 * 128 + N_H * 8  # two kde_result structs + g[n_h]
+
+    # ---- roofline of the dominant kernel (all-pairs LSCV)
+    sm_mhz = (clocks or {}).get("sm_mhz") or probe["sm_mhz"]
+    per_clk = min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
+    peak = per_clk * probe["sm_count"] * sm_mhz * 1e6 / 1e9
+    achieved = EVALS_LSCV / (lscv_ms * 1e-3) / 1e9
+    peak_max = per_clk * probe["sm_count"] * 2070.0 * 1e6 / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_lscv (all-pairs, all-bandwidths LSCV)",
+                "kernel_ms": lscv_ms, "evals_per_launch": EVALS_LSCV,
+                "peak_basis": (f"min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM, FP32 lanes "
+                               f"{probe['ffma_lanes_per_clk_sm']:.1f}/clk/SM / 3 per eval) x "
+                               f"{probe['sm_count']} SMs x {sm_mhz:.0f} MHz (median SM clock sampled "
+                               "during the timed region); unit counts measured by kde_probe_alu"),
+                "peak_at_max_clock": peak_max, "frac_at_max_clock": achieved / peak_max,
+                "psi_kernel_ms": psi_ms,
+                "psi_geval_s": pairs(N) / (psi_ms * 1e-3) / 1e9}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "d": 1, "n_h": N_H,
+                       "evals_per_step": EVALS_STEP, "seed": SEED,
+                       "precision": "fp32 terms, Kahan fp32 per-thread sums, fp64 reductions",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": LAUNCHES_PER_STEP * K,
+            "roofline": roofline, "clocks": clocks,
+            "alu_probe": probe,
+            "result": {"lscv_argmin": r_l["argmin"], "lscv_h": r_l["h"], "plugin_h": r_p["h"]}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = oracle_sample(args.cpu_seconds)
+        cb.pop("seconds")
+        line["cpu_baseline"] = cb
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,255 @@
+/*
+ * gbkde.h -- C ABI of libgbkde, exact kernel-density bandwidth selection on
+ * GB300 (sm_103a), following Gramacki & Andrzejewski, "Density Estimations for
+ * Approximate Query Processing on SIMD Architectures" (arXiv 1505.01998).
+ *
+ * The library computes the O(n^2) all-pairs Gaussian-kernel reductions of
+ * three bandwidth selectors:
+ *   - PLUGIN (Sec. 4.4.1): two-stage plug-in h for univariate data, built on
+ *     the density-derivative functionals psi_6 and psi_4;
+ *   - LSCV_h (Sec. 4.4.2): the least-squares cross-validation objective g(h)
+ *     with bandwidth matrix H = h^2 S (S = sample covariance), evaluated on a
+ *     grid of h and minimised by brute force on the grid (Eq. LSCV-finalH);
+ *   - LSCV_H (Sec. 4.4.3): the objective g(H) for general bandwidth matrices.
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns an int status (KDE_OK = 0 or a KDE_E* code).
+ *    kde_last_error() returns a human-readable detail for the calling thread.
+ *  - Samples: a d x n matrix with one sample per column, row-major, i.e.
+ *    x[k*n + i] is coordinate k of sample i (the paper's input matrix of
+ *    Sec. 4.4.2, Eq. LSCV-InputData).  Element type KDE_F32 or KDE_F64.
+ *    1 <= d <= 4, n >= 2, all values finite.
+ *  - Memory: the caller owns every buffer.  Device pointers must be device
+ *    memory of the current CUDA device; the workspace must be at least
+ *    kde_workspace_size() bytes and 256-byte aligned.  No entry point
+ *    allocates device memory.  Host result pointers may be NULL when a result
+ *    is not wanted.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *    device work is queued on it.  Entry points without the _async suffix
+ *    copy their results to the host and synchronise that stream before
+ *    returning.  _async entry points queue work only and write results to
+ *    device memory inside the workspace (see kde_ws_result_offset).
+ *  - Arithmetic: pair terms in FP32 (exp by ex2.approx), per-thread sums in
+ *    FP32 with Kahan compensation (KDE_FP32_KAHAN, default) or plain FP32
+ *    (KDE_FP32_PLAIN); every reduction across threads and blocks, the scalar
+ *    plug-in chain, g(h) and the argmin in FP64.
+ */
+#ifndef GBKDE_H
+#define GBKDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define KDE_OK 0
+#define KDE_EINVAL 1      /* invalid argument (sizes, pointers, d, n, grid)    */
+#define KDE_ENOMEM 2      /* workspace or arena too small                      */
+#define KDE_ECUDA 3       /* a CUDA runtime call failed                        */
+#define KDE_EDEGENERATE 4 /* the method is undefined for these data (see below) */
+#define KDE_EBUSY 5       /* server full: no slot or HBM budget for a request  */
+#define KDE_EAGAIN 6      /* result not ready yet                              */
+#define KDE_ETIMEDOUT 7   /* wait timed out                                    */
+#define KDE_ECANCELLED 8  /* request was cancelled                             */
+#define KDE_ENOTFOUND 9   /* unknown ticket                                    */
+#define KDE_EINTERNAL 10  /* internal consistency check failed                 */
+
+/* sample element types */
+#define KDE_F32 0
+#define KDE_F64 1
+
+/* per-thread summation modes of the pair kernels */
+#define KDE_FP32_KAHAN 0
+#define KDE_FP32_PLAIN 1
+
+/* bandwidth grid kinds */
+#define KDE_GRID_DEFAULT_Z 0 /* n_h log-spaced points over Z(h0) = [h0/4, 4 h0] */
+#define KDE_GRID_EXPLICIT 1  /* the n_h values in h[] (need not be sorted)       */
+#define KDE_GRID_LOG 2       /* n_h log-spaced points over [h_min, h_max]        */
+
+#define KDE_MAX_D 4
+#define KDE_MAX_NH 1024
+
+/* result flags */
+#define KDE_FLAG_MIN_AT_LOWER_EDGE 1 /* argmin is the first grid point */
+#define KDE_FLAG_MIN_AT_UPPER_EDGE 2 /* argmin is the last grid point  */
+
+/* methods (for batch / serving requests) */
+#define KDE_METHOD_LSCV 1
+#define KDE_METHOD_PLUGIN 2
+
+/* A grid of bandwidth multipliers h (H = h^2 S).  For DEFAULT_Z, h0 is the
+ * normal-scale rule (4/((d+2) n))^(1/(d+4)) (Eq. LSCV-h0; equal to the
+ * printed constants at d = 1) and the range is Eq. LSCV-Zh0. */
+typedef struct kde_grid {
+  int kind;
+  int n_h;          /* 1 .. KDE_MAX_NH */
+  const double* h;  /* host array of n_h values, for KDE_GRID_EXPLICIT */
+  double h_min;     /* for KDE_GRID_LOG */
+  double h_max;
+} kde_grid;
+
+/* Tuning knobs; zero means "choose automatically". */
+typedef struct kde_opts {
+  int precision;      /* KDE_FP32_KAHAN (0) or KDE_FP32_PLAIN                  */
+  int tile;           /* LSCV pair tile edge T: 32 or 128 samples               */
+  int bw_per_thread;  /* LSCV bandwidths per thread B: 8 or 16                  */
+  int tiles_per_item; /* tiles per work item K (1 .. 4096)                      */
+  int ctas_per_sm;    /* resident CTAs per SM of the persistent pair kernels    */
+} kde_opts;
+
+/* Result of one selection.  Fields that do not apply are 0. */
+typedef struct kde_result {
+  int status;     /* KDE_OK or KDE_EDEGENERATE                                  */
+  int method;     /* KDE_METHOD_LSCV or KDE_METHOD_PLUGIN                       */
+  int argmin;     /* LSCV: first grid index attaining the minimum of g          */
+  int flags;      /* KDE_FLAG_*                                                 */
+  int n_h;
+  int d;
+  double h;       /* LSCV: selected multiplier (H = h^2 S); PLUGIN: h (data units) */
+  double h_data;  /* d = 1: selected bandwidth in data units                    */
+  double g_min;   /* LSCV: g at the argmin                                      */
+  double sigma;   /* d = 1: sample standard deviation (Eq. PLUGIN-StdDevEstimator) */
+  double psi8_ns; /* PLUGIN: Eq. PLUGIN-Psi8Estimate                            */
+  double g1;      /* PLUGIN: Eq. PLUGIN-g1                                      */
+  double psi6;    /* PLUGIN: Eq. PLUGIN-Psi6Estimate (reading R1)               */
+  double g2;      /* PLUGIN: Eq. PLUGIN-g2                                      */
+  double psi4;    /* PLUGIN: Eq. PLUGIN-Psi4Estimate (reading R1)               */
+  double logdet_S;/* log det S                                                  */
+} kde_result;
+
+/* ------------------------------------------------------------- utilities */
+
+/* Library version string (static storage). */
+const char* kde_version(void);
+
+/* Copies the calling thread's last error detail into buf (NUL-terminated,
+ * truncated to len).  Returns the status of that error (KDE_OK if none). */
+int kde_last_error(char* buf, size_t len);
+
+/* Static description of a status code. */
+const char* kde_status_string(int status);
+
+/* Number of tiles of the upper pair triangle for n samples and tile edge T:
+ * NT (NT + 1) / 2 with NT = ceil(n / T) (Sec. 5.4.1, pair triangle in k x k
+ * tiles with zero padding of n to a multiple of k). */
+int kde_tile_count(int64_t n, int tile, int64_t* tiles);
+
+/* The tile map of Sec. 5.4.2 (Eqs. colInTriangleMatrix, rowInTriangleMatrix;
+ * Appendix A): tile number bx -> column l and row q, q <= l, of the upper
+ * triangle, column l holding tiles l(l+1)/2 .. l(l+1)/2 + l.  The float
+ * square-root formula is followed by an exact integer correction.  This is
+ * the same function the kernels run, compiled for the host. */
+int kde_tile_coords(int64_t bx, int64_t* l, int64_t* q);
+
+/* The library's default grid for n samples in d dimensions (host output). */
+int kde_default_grid(int64_t n, int d, int n_h, double* h_out);
+
+/* ------------------------------------------------------------ workspace */
+
+/* Bytes of workspace needed by kde_lscv / kde_plugin / kde_lscv_tile_sums /
+ * kde_psi_tile_sums / kde_lscv_H for n samples in d dimensions and n_h
+ * bandwidths (use n_h = 1 for plug-in only) with the given options (NULL =
+ * defaults).  The workspace also holds the device-side copy of a host input
+ * (the *_host entry points). */
+int kde_workspace_size(int64_t n, int d, int n_h, const kde_opts* opts, size_t* bytes);
+
+/* Offset, in bytes from the workspace base, of the kde_result written by
+ * the last _async call that used that workspace, and of its g[n_h] array. */
+int kde_ws_result_offset(size_t* result_offset, size_t* g_offset);
+
+/* ------------------------------------------------------------- LSCV_h */
+
+/* LSCV_h bandwidth selection (Sec. 4.4.2; GPU design of Sec. 6.2 replaced by a
+ * fused all-pairs, all-bandwidths kernel).  Computes the covariance S
+ * (Eq. LSCV-covariance), its Cholesky factor, and for every grid point
+ * g(h) = h^-d [2 n^-2 sum_{i<j} T((X_i - X_j)/h) + n^-1 R(K)] (Eq. LSCV-gh,
+ * R(K) = (4 pi)^(-d/2) |S|^(-1/2)); then the argmin over the grid.
+ *   x_dev   device samples, d x n row-major, element type dtype
+ *   g_host  optional host output, n_h values of g in grid order
+ *   h_host  optional host output, the n_h grid values used
+ *   out     host result (required)
+ * Errors: KDE_EINVAL (bad sizes/pointers/grid), KDE_ENOMEM (workspace too
+ * small), KDE_EDEGENERATE (S singular or not positive definite; also
+ * reported in out->status), KDE_ECUDA. */
+int kde_lscv(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
+             const kde_opts* opts, void* ws, size_t ws_bytes, void* stream,
+             double* g_host, double* h_host, kde_result* out);
+
+/* As kde_lscv, queue only: the result and g[] stay in the workspace. */
+int kde_lscv_async(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
+                   const kde_opts* opts, void* ws, size_t ws_bytes, void* stream);
+
+/* As kde_lscv with HOST samples: copies x_host into the workspace on the
+ * stream (pageable or pinned host memory), runs, copies the result back. */
+int kde_lscv_host(const void* x_host, int dtype, int64_t n, int d, const kde_grid* grid,
+                  const kde_opts* opts, void* ws, size_t ws_bytes, void* stream,
+                  double* g_host, kde_result* out);
+
+/* Raw LSCV pair sums over the tiles [tile_begin, tile_end) of the pair
+ * triangle (tile edge opts->tile, tile numbering of kde_tile_coords), for the
+ * n_h multipliers h_host[]:
+ *   s1[k] = sum exp(-S(v)/(4 h_k^2)),  s2[k] = sum exp(-S(v)/(2 h_k^2))
+ * over pairs i < j < n in those tiles, S(v) = v^T S^-1 v (Eq. LSCV_MOD-Pv).
+ * The sums over disjoint tile ranges add up to the full sums: this is the
+ * unit of multi-GPU sharding and of sampled parity checks. */
+int kde_lscv_tile_sums(const void* x_dev, int dtype, int64_t n, int d, const double* h_host,
+                       int n_h, int64_t tile_begin, int64_t tile_end, const kde_opts* opts,
+                       void* ws, size_t ws_bytes, void* stream, double* s1_host,
+                       double* s2_host);
+
+/* ------------------------------------------------------------- PLUGIN */
+
+/* PLUGIN bandwidth selection for univariate data (Sec. 4.4.1, steps 1-8; GPU
+ * composition of Sec. 6.1 with the scalar steps on the device in FP64):
+ * variance, sigma, psi_8^NS, g1, psi_6(g1) over all pairs, g2, psi_4(g2) over
+ * all pairs, h.  psi_r(g) = n^-2 g^-(r+1) [2 sum_{i<j} K^(r)((x_i-x_j)/g) +
+ * n K^(r)(0)] (reading R1 of the garbled Eqs. PLUGIN-Psi6Estimate/Psi4Estimate).
+ * Errors: KDE_EINVAL, KDE_ENOMEM, KDE_EDEGENERATE (sigma = 0, psi_6 >= 0 or
+ * psi_4 <= 0; also in out->status), KDE_ECUDA. */
+int kde_plugin(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, void* ws,
+               size_t ws_bytes, void* stream, kde_result* out);
+
+/* As kde_plugin, queue only (result stays in the workspace). */
+int kde_plugin_async(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, void* ws,
+                     size_t ws_bytes, void* stream);
+
+/* As kde_plugin with HOST samples (copied into the workspace on the stream). */
+int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* opts, void* ws,
+                    size_t ws_bytes, void* stream, kde_result* out);
+
+/* Raw psi pair sum over the tiles [tile_begin, tile_end) of the pair
+ * triangle (tile edge 32 * psi rows per lane, see kde_psi_tile_edge):
+ *   sum K^(r)((x_i - x_j)/g) over pairs i < j < n in those tiles, r in {4,6,8}. */
+int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double g,
+                      int64_t tile_begin, int64_t tile_end, const kde_opts* opts, void* ws,
+                      size_t ws_bytes, void* stream, double* sum_host);
+
+/* Tile edge used by the psi kernels for n samples (for kde_psi_tile_sums). */
+int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile);
+
+/* ------------------------------------------------------- measurement aids */
+
+/* Kernel timing hook for the calling thread.  When set (non-NULL cudaEvent_t
+ * handles created by the caller), the next LSCV_h / PLUGIN calls of this
+ * thread record lscv_begin / lscv_end on their stream immediately around the
+ * launch of the all-pairs LSCV kernel, and psi_begin / psi_end around the
+ * first all-pairs psi kernel.  Pass NULLs to clear.  Never fails. */
+int kde_set_kernel_events(void* lscv_begin, void* lscv_end, void* psi_begin, void* psi_end);
+
+/* Sustained per-SM throughput of the units the pair kernels are bound by,
+ * measured with clock64() on the current device: MUFU ex2 results, FP32 FMA
+ * lanes (scalar FFMA) and packed FP32x2 FMA lanes, each per SM per clock.
+ * Also returns the SM count and the effective SM clock (MHz) seen by the
+ * probe.  Device-synchronous; allocates nothing (uses the workspace). */
+int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu_ex2_per_clk_sm,
+                  double* ffma_lanes_per_clk_sm, double* ffma2_lanes_per_clk_sm,
+                  int* sm_count, double* sm_mhz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBKDE_H */

@@ -67,6 +67,7 @@ def _load():
             "kdeo_gauss_deriv": (D, [I, D]),
             "kdeo_psi_pair_sum_block": (D, [P, L, I, D, L, L, L, L, I]),
             "kdeo_psi_pair_sum": (D, [P, L, I, D, I]),
+            "kdeo_psi_abs_pair_sum_block": (D, [P, L, I, D, L, L, L, L, I]),
             "kdeo_psi": (D, [P, L, I, D, I]),
             "kdeo_psi8_ns": (D, [D]),
             "kdeo_plugin_g1": (D, [D, L]),
@@ -148,6 +149,14 @@ def psi_pair_sum(x, r: int, g: float, threads: int = 0, block=None) -> float:
         return _load().kdeo_psi_pair_sum(_p(a), n, r, float(g), threads)
     i0, i1, j0, j1 = (int(v) for v in block)
     return _load().kdeo_psi_pair_sum_block(_p(a), n, r, float(g), i0, i1, j0, j1, threads)
+
+
+def psi_abs_pair_sum(x, r: int, g: float, threads: int = 0, block=None) -> float:
+    """sum over i<j of |K^(r)((x_i - x_j)/g)| (magnitude scale for error statements)."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    n = a.size
+    i0, i1, j0, j1 = (0, n, 0, n) if block is None else (int(v) for v in block)
+    return _load().kdeo_psi_abs_pair_sum_block(_p(a), n, r, float(g), i0, i1, j0, j1, threads)
 
 
 def psi(x, r: int, g: float, threads: int = 0) -> float:

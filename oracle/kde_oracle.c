@@ -198,6 +198,32 @@ double kdeo_psi_pair_sum_block(const double *x, long n, int r, double g, long i0
   return nsum_get(&tot);
 }
 
+/* Magnitude scale of the same block: sum of |K^(r)((x_i - x_j)/g)|.  Used only
+ * to state the error of a signed sum relative to the size of its terms. */
+double kdeo_psi_abs_pair_sum_block(const double *x, long n, int r, double g, long i0, long i1,
+                                   long j0, long j1, int threads) {
+  if (i0 < 0) i0 = 0;
+  if (i1 > n) i1 = n;
+  if (j1 > n) j1 = n;
+  long rows = i1 > i0 ? i1 - i0 : 0;
+  if (rows == 0) return 0.0;
+  double *row = (double *)calloc((size_t)rows, sizeof(double));
+  if (!row) return NAN;
+  int nt = pick_threads(threads);
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nt)
+  for (long ii = 0; ii < rows; ++ii) {
+    long i = i0 + ii;
+    nsum_t s = {0, 0};
+    long jb = j0 > i + 1 ? j0 : i + 1;
+    for (long j = jb; j < j1; ++j) nsum_add(&s, fabs(kdeo_gauss_deriv(r, (x[i] - x[j]) / g)));
+    row[ii] = nsum_get(&s);
+  }
+  nsum_t tot = {0, 0};
+  for (long ii = 0; ii < rows; ++ii) nsum_add(&tot, row[ii]);
+  free(row);
+  return nsum_get(&tot);
+}
+
 double kdeo_psi_pair_sum(const double *x, long n, int r, double g, int threads) {
   return kdeo_psi_pair_sum_block(x, n, r, g, 0, n, 0, n, threads);
 }

@@ -1,0 +1,628 @@
+// Host side of the C ABI declared in include/gbkde.h: argument checks, work
+// plans, workspace layout and the launch sequences of the single-dataset
+// entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "host.hpp"
+
+namespace gbkde {
+
+namespace {
+thread_local int t_err_status = KDE_OK;
+thread_local char t_err_msg[512] = "";
+thread_local cudaEvent_t t_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+}  // namespace
+
+static cudaError_t mark(int k, cudaStream_t st) {
+  return t_ev[k] ? cudaEventRecord(t_ev[k], st) : cudaSuccess;
+}
+
+int fail(int status, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err_msg, sizeof(t_err_msg), fmt, ap);
+  va_end(ap);
+  t_err_status = status;
+  return status;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(KDE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int check_opts(const kde_opts* o) {
+  if (!o) return KDE_OK;
+  if (o->precision != KDE_FP32_KAHAN && o->precision != KDE_FP32_PLAIN)
+    return fail(KDE_EINVAL, "opts.precision %d invalid", o->precision);
+  if (o->tile != 0 && o->tile != 32 && o->tile != 128)
+    return fail(KDE_EINVAL, "opts.tile %d invalid (0, 32 or 128)", o->tile);
+  if (o->bw_per_thread != 0 && o->bw_per_thread != 8 && o->bw_per_thread != 16)
+    return fail(KDE_EINVAL, "opts.bw_per_thread %d invalid (0, 8 or 16)", o->bw_per_thread);
+  if (o->tiles_per_item < 0 || o->tiles_per_item > 4096)
+    return fail(KDE_EINVAL, "opts.tiles_per_item %d invalid", o->tiles_per_item);
+  if (o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
+    return fail(KDE_EINVAL, "opts.ctas_per_sm %d invalid", o->ctas_per_sm);
+  return KDE_OK;
+}
+
+// Geometry of one selection.  Deterministic in (n, d, n_h, opts, SM count).
+int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g) {
+  memset(g, 0, sizeof(*g));
+  g->n = n;
+  g->d = d;
+  g->n_h = n_h;
+  g->n_pad = (int64_t)align_up((size_t)n, kPadTo);
+  g->kahan = !(o && o->precision == KDE_FP32_PLAIN);
+  const int cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : 2;
+  g->ctas = std::max(1, sms) * cps;
+  // LSCV
+  g->T = (o && o->tile) ? o->tile : (n <= 2048 ? 32 : 128);
+  g->R = g->T / 32;
+  g->B = (o && o->bw_per_thread) ? o->bw_per_thread : (n_h <= 64 ? 8 : 16);
+  const int nh = std::max(n_h, 1);
+  g->n_h_pad = (nh + g->B - 1) / g->B * g->B;
+  g->n_chunks = g->n_h_pad / g->B;
+  g->G = (g->n_chunks + kWarps - 1) / kWarps;
+  g->tiles = tri_tiles(n, g->T);
+  if (o && o->tiles_per_item) {
+    g->K = o->tiles_per_item;
+  } else {
+    const int64_t target = 4 * (int64_t)g->ctas;
+    g->K = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
+  }
+  g->rows = (g->tiles + g->K - 1) / g->K;
+  g->items = g->rows * g->G;
+  // psi
+  g->Tp = n >= 16384 ? 256 : 64;
+  g->Rp = g->Tp / 32;
+  g->ptiles = tri_tiles(n, g->Tp);
+  {
+    const int64_t target = 4 * (int64_t)g->ctas;
+    g->Kp = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (g->ptiles + target - 1) / target));
+  }
+  g->prows = (g->ptiles + g->Kp - 1) / g->Kp;
+  // workspace layout
+  size_t o0 = 0;
+  g->off_ds = o0;
+  o0 = align_up(o0 + sizeof(DsDev), 256);
+  g->off_off = o0;
+  o0 = align_up(o0 + 8 * sizeof(int64_t), 256);
+  g->off_h = o0;
+  o0 = align_up(o0 + KDE_MAX_NH * sizeof(double), 256);
+  g->off_nc = o0;
+  o0 = align_up(o0 + KDE_MAX_NH * sizeof(float), 256);
+  g->off_g = o0;
+  o0 = align_up(o0 + KDE_MAX_NH * sizeof(double), 256);
+  g->off_sum = o0;
+  o0 = align_up(o0 + 2 * KDE_MAX_NH * sizeof(double), 256);
+  g->off_x = o0;
+  o0 = align_up(o0 + (size_t)d * n * sizeof(double), 256);
+  g->off_y = o0;
+  o0 = align_up(o0 + (size_t)d * g->n_pad * sizeof(float), 256);
+  g->off_xc = o0;
+  o0 = align_up(o0 + (size_t)g->n_pad * sizeof(float), 256);
+  g->off_lpart = o0;
+  o0 = align_up(o0 + (n_h > 0 ? (size_t)g->rows * 2 * g->n_h_pad * sizeof(double) : 0), 256);
+  g->off_ppart = o0;
+  o0 = align_up(o0 + (size_t)g->prows * sizeof(double), 256);
+  g->total = o0;
+  return KDE_OK;
+}
+
+int check_common(const void* x, int dtype, int64_t n, int d, void* ws) {
+  if (!x) return fail(KDE_EINVAL, "x is NULL");
+  if (dtype != KDE_F32 && dtype != KDE_F64) return fail(KDE_EINVAL, "dtype %d invalid", dtype);
+  if (n < 2) return fail(KDE_EINVAL, "n = %lld: need at least 2 samples", (long long)n);
+  if (n > ((int64_t)1 << 31)) return fail(KDE_EINVAL, "n = %lld too large", (long long)n);
+  if (d < 1 || d > KDE_MAX_D) return fail(KDE_EINVAL, "d = %d outside [1, %d]", d, KDE_MAX_D);
+  if (!ws) return fail(KDE_EINVAL, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(KDE_EINVAL, "workspace not 256-byte aligned");
+  return KDE_OK;
+}
+
+int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h) {
+  if (!grid) return fail(KDE_EINVAL, "grid is NULL");
+  if (grid->n_h < 1 || grid->n_h > KDE_MAX_NH)
+    return fail(KDE_EINVAL, "grid n_h = %d outside [1, %d]", grid->n_h, KDE_MAX_NH);
+  h->resize(grid->n_h);
+  double lo = 0, hi = 0;
+  switch (grid->kind) {
+    case KDE_GRID_EXPLICIT:
+      if (!grid->h) return fail(KDE_EINVAL, "explicit grid with NULL h");
+      for (int k = 0; k < grid->n_h; ++k) (*h)[k] = grid->h[k];
+      break;
+    case KDE_GRID_DEFAULT_Z: {
+      // h0 = (4 / ((d+2) n))^(1/(d+4)) (Eq. LSCV-h0, normal scale), Z = [h0/4, 4 h0]
+      const double h0 = std::pow(4.0 / ((double)(d + 2) * (double)n), 1.0 / (double)(d + 4));
+      lo = h0 / 4.0;
+      hi = h0 * 4.0;
+    }  // fall through
+    case KDE_GRID_LOG:
+      if (grid->kind == KDE_GRID_LOG) {
+        lo = grid->h_min;
+        hi = grid->h_max;
+      }
+      if (!(lo > 0) || !(hi >= lo) || !std::isfinite(hi))
+        return fail(KDE_EINVAL, "grid range [%g, %g] invalid", lo, hi);
+      for (int k = 0; k < grid->n_h; ++k)
+        (*h)[k] = grid->n_h == 1 ? lo
+                                 : lo * std::exp(std::log(hi / lo) * (double)k / (double)(grid->n_h - 1));
+      break;
+    default:
+      return fail(KDE_EINVAL, "grid kind %d invalid", grid->kind);
+  }
+  for (double v : *h)
+    if (!(v > 0) || !std::isfinite(v)) return fail(KDE_EINVAL, "grid value %g invalid", v);
+  return KDE_OK;
+}
+
+// Descriptor for one selection on workspace `ws` laid out by `g`.
+DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsigned char* ws) {
+  DsDev s;
+  memset(&s, 0, sizeof(s));
+  s.x = x;
+  s.n = g.n;
+  s.d = g.d;
+  s.dtype = dtype;
+  s.n_pad = g.n_pad;
+  s.methods = methods;
+  s.y = reinterpret_cast<float*>(ws + g.off_y);
+  s.xc = g.d == 1 ? reinterpret_cast<float*>(ws + g.off_xc) : nullptr;
+  s.n_h = g.n_h;
+  s.n_h_pad = g.n_h > 0 ? g.n_h_pad : 0;
+  s.n_chunks = g.n_chunks;
+  s.n_groups = g.G;
+  s.lscv_tile = g.T;
+  s.lscv_K = g.K;
+  s.lscv_tiles = g.tiles;
+  s.lscv_rows = g.rows;
+  s.lscv_t0 = 0;
+  s.h = reinterpret_cast<double*>(ws + g.off_h);
+  s.nc = reinterpret_cast<float*>(ws + g.off_nc);
+  s.lscv_part = reinterpret_cast<double*>(ws + g.off_lpart);
+  s.lscv_sum = reinterpret_cast<double*>(ws + g.off_sum);
+  s.g = reinterpret_cast<double*>(ws + g.off_g);
+  s.psi_tile = g.Tp;
+  s.psi_K = g.Kp;
+  s.psi_tiles = g.ptiles;
+  s.psi_rows = g.prows;
+  s.psi_t0 = 0;
+  s.psi_part = reinterpret_cast<double*>(ws + g.off_ppart);
+  s.res.status = KDE_OK;
+  return s;
+}
+
+// Monic polynomial p_r(y) with He_r(u) = kappa^(r/2) p_r(y), u^2 = kappa y,
+// kappa = 2 ln 2 (see psi.cu), in Horner order.  He_r from its recurrence.
+PsiCoef psi_coef(int r) {
+  std::vector<double> hm1(r + 2, 0.0), h(r + 2, 0.0), hp(r + 2, 0.0);
+  hm1[0] = 1.0;  // He_0
+  h[1] = 1.0;    // He_1
+  for (int k = 1; k < r; ++k) {
+    std::fill(hp.begin(), hp.end(), 0.0);
+    for (int j = 0; j <= r; ++j) {
+      if (j + 1 <= r + 1) hp[j + 1] += h[j];
+      hp[j] -= (double)k * hm1[j];
+    }
+    hm1 = h;
+    h = hp;
+  }
+  const double kappa = 2.0 * std::log(2.0);
+  const int M = r / 2;
+  PsiCoef cf;
+  memset(&cf, 0, sizeof(cf));
+  // coefficient of y^m in p_r: a_{2m} kappa^(m - M); Horner c_i multiplies y^(M-1-i)
+  for (int i = 0; i < M; ++i) {
+    const int m = M - 1 - i;
+    cf.c[i] = (float)(h[2 * m] * std::pow(kappa, (double)(m - M)));
+  }
+  return cf;
+}
+
+}  // namespace gbkde
+
+using namespace gbkde;
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+extern "C" {
+
+const char* kde_version(void) { return "gbkde 0.1 (sm_103a)"; }
+
+int kde_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    strncpy(buf, t_err_msg, len - 1);
+    buf[len - 1] = 0;
+  }
+  return t_err_status;
+}
+
+const char* kde_status_string(int s) {
+  switch (s) {
+    case KDE_OK: return "ok";
+    case KDE_EINVAL: return "invalid argument";
+    case KDE_ENOMEM: return "workspace or arena too small";
+    case KDE_ECUDA: return "CUDA error";
+    case KDE_EDEGENERATE: return "method undefined for these data";
+    case KDE_EBUSY: return "server busy";
+    case KDE_EAGAIN: return "not ready";
+    case KDE_ETIMEDOUT: return "timed out";
+    case KDE_ECANCELLED: return "cancelled";
+    case KDE_ENOTFOUND: return "unknown ticket";
+    case KDE_EINTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+int kde_tile_count(int64_t n, int tile, int64_t* tiles) {
+  if (!tiles || n < 0 || tile <= 0) return fail(KDE_EINVAL, "kde_tile_count: bad arguments");
+  *tiles = tri_tiles(n, tile);
+  return KDE_OK;
+}
+
+int kde_tile_coords(int64_t bx, int64_t* l, int64_t* q) {
+  if (!l || !q || bx < 0) return fail(KDE_EINVAL, "kde_tile_coords: bad arguments");
+  tile_coords(bx, *l, *q);
+  return KDE_OK;
+}
+
+int kde_default_grid(int64_t n, int d, int n_h, double* h_out) {
+  if (!h_out || n < 2 || d < 1 || d > KDE_MAX_D) return fail(KDE_EINVAL, "kde_default_grid: bad arguments");
+  kde_grid gr{KDE_GRID_DEFAULT_Z, n_h, nullptr, 0, 0};
+  std::vector<double> h;
+  int rc = build_grid(&gr, n, d, &h);
+  if (rc) return rc;
+  for (int k = 0; k < n_h; ++k) h_out[k] = h[k];
+  return KDE_OK;
+}
+
+int kde_workspace_size(int64_t n, int d, int n_h, const kde_opts* opts, size_t* bytes) {
+  if (!bytes) return fail(KDE_EINVAL, "bytes is NULL");
+  if (n < 2 || d < 1 || d > KDE_MAX_D || n_h < 0 || n_h > KDE_MAX_NH)
+    return fail(KDE_EINVAL, "kde_workspace_size: bad sizes");
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, d, n_h, opts, device_sms(), &g);
+  *bytes = g.total;
+  return KDE_OK;
+}
+
+int kde_ws_result_offset(size_t* result_offset, size_t* g_offset) {
+  Geometry g;
+  make_geometry(2, 1, 1, nullptr, 1, &g);
+  if (result_offset) *result_offset = g.off_ds + offsetof(DsDev, res);
+  if (g_offset) *g_offset = g.off_g;
+  return KDE_OK;
+}
+
+int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile) {
+  if (!tile || n < 2) return fail(KDE_EINVAL, "kde_psi_tile_edge: bad arguments");
+  Geometry g;
+  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  *tile = g.Tp;
+  return KDE_OK;
+}
+
+// -------------------------------------------------------------- LSCV_h
+
+static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std::vector<double>& h,
+                      const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st,
+                      int64_t tile_begin, int64_t tile_end, Geometry* gout) {
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, d, (int)h.size(), opts, device_sms(), &g);
+  if (ws_bytes < g.total)
+    return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  DsDev init = make_desc(g, x_dev, dtype, KDE_METHOD_LSCV, w);
+  if (tile_begin >= 0) {
+    init.lscv_t0 = tile_begin;
+    init.lscv_tiles = tile_end;
+    init.lscv_rows = (tile_end - tile_begin + g.K - 1) / g.K;
+    g.rows = init.lscv_rows;
+    g.items = g.rows * g.G;
+  }
+  DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
+  int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
+  const int64_t offs[4] = {0, g.items, 0, 0};
+  CK(launch_setup(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
+  CK(launch_prep(ds, 1, dtype, st));
+  Phase ph{ds, off, 1, 0, g.items};
+  const int grid = (int)std::min<int64_t>(g.items, g.ctas);
+  CK(mark(0, st));
+  CK(launch_lscv(ph, d, g.B, g.R, g.kahan, std::max(grid, 1), st));
+  CK(mark(1, st));
+  CK(launch_lscv_reduce(ds, 1, g.n_h_pad, st));
+  CK(launch_lscv_finish(ds, 1, st));
+  if (gout) *gout = g;
+  return KDE_OK;
+}
+
+int kde_lscv_async(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
+                   const kde_opts* opts, void* ws, size_t ws_bytes, void* stream) {
+  int rc = check_common(x_dev, dtype, n, d, ws);
+  if (rc) return rc;
+  std::vector<double> h;
+  rc = build_grid(grid, n, d, &h);
+  if (rc) return rc;
+  return lscv_queue(x_dev, dtype, n, d, h, opts, ws, ws_bytes, (cudaStream_t)stream, -1, -1, nullptr);
+}
+
+static int fetch_result(const Geometry& g, void* ws, cudaStream_t st, double* g_host,
+                        double* h_host, kde_result* out) {
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  kde_result r;
+  CK(cudaMemcpyAsync(&r, w + g.off_ds + offsetof(DsDev, res), sizeof(r), cudaMemcpyDeviceToHost, st));
+  if (g_host && g.n_h > 0)
+    CK(cudaMemcpyAsync(g_host, w + g.off_g, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost, st));
+  if (h_host && g.n_h > 0)
+    CK(cudaMemcpyAsync(h_host, w + g.off_h, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (out) *out = r;
+  if (r.status != KDE_OK) return fail(r.status, "selection failed on the device: %s", kde_status_string(r.status));
+  return KDE_OK;
+}
+
+int kde_lscv(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
+             const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host,
+             double* h_host, kde_result* out) {
+  if (!out) return fail(KDE_EINVAL, "out is NULL");
+  int rc = check_common(x_dev, dtype, n, d, ws);
+  if (rc) return rc;
+  std::vector<double> h;
+  rc = build_grid(grid, n, d, &h);
+  if (rc) return rc;
+  Geometry g;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = lscv_queue(x_dev, dtype, n, d, h, opts, ws, ws_bytes, st, -1, -1, &g);
+  if (rc) return rc;
+  return fetch_result(g, ws, st, g_host, h_host, out);
+}
+
+int kde_lscv_host(const void* x_host, int dtype, int64_t n, int d, const kde_grid* grid,
+                  const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host,
+                  kde_result* out) {
+  if (!out) return fail(KDE_EINVAL, "out is NULL");
+  int rc = check_common(x_host, dtype, n, d, ws);
+  if (rc) return rc;
+  std::vector<double> h;
+  rc = build_grid(grid, n, d, &h);
+  if (rc) return rc;
+  rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, d, (int)h.size(), opts, device_sms(), &g);
+  if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* xd = static_cast<unsigned char*>(ws) + g.off_x;
+  const size_t bytes = (size_t)d * n * (dtype == KDE_F64 ? 8 : 4);
+  CK(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, st));
+  rc = lscv_queue(xd, dtype, n, d, h, opts, ws, ws_bytes, st, -1, -1, &g);
+  if (rc) return rc;
+  return fetch_result(g, ws, st, g_host, nullptr, out);
+}
+
+int kde_lscv_tile_sums(const void* x_dev, int dtype, int64_t n, int d, const double* h_host,
+                       int n_h, int64_t tile_begin, int64_t tile_end, const kde_opts* opts,
+                       void* ws, size_t ws_bytes, void* stream, double* s1_host,
+                       double* s2_host) {
+  int rc = check_common(x_dev, dtype, n, d, ws);
+  if (rc) return rc;
+  if (!h_host || n_h < 1 || n_h > KDE_MAX_NH) return fail(KDE_EINVAL, "bad h / n_h");
+  kde_grid gr{KDE_GRID_EXPLICIT, n_h, h_host, 0, 0};
+  std::vector<double> h;
+  rc = build_grid(&gr, n, d, &h);
+  if (rc) return rc;
+  rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, d, n_h, opts, device_sms(), &g);
+  if (tile_begin < 0 || tile_end < tile_begin || tile_end > g.tiles)
+    return fail(KDE_EINVAL, "tile range [%lld, %lld) outside [0, %lld)", (long long)tile_begin,
+                (long long)tile_end, (long long)g.tiles);
+  if (tile_end == tile_begin) {
+    for (int k = 0; k < n_h; ++k) {
+      if (s1_host) s1_host[k] = 0;
+      if (s2_host) s2_host[k] = 0;
+    }
+    return KDE_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = lscv_queue(x_dev, dtype, n, d, h, opts, ws, ws_bytes, st, tile_begin, tile_end, &g);
+  if (rc) return rc;
+  std::vector<double> sums(2 * g.n_h_pad);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  kde_result r;
+  CK(cudaMemcpyAsync(sums.data(), w + g.off_sum, sizeof(double) * 2 * g.n_h_pad, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&r, w + g.off_ds + offsetof(DsDev, res), sizeof(r), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (r.status != KDE_OK) return fail(r.status, "tile sums failed on the device: %s", kde_status_string(r.status));
+  for (int k = 0; k < n_h; ++k) {
+    if (s1_host) s1_host[k] = sums[2 * k];
+    if (s2_host) s2_host[k] = sums[2 * k + 1];
+  }
+  return KDE_OK;
+}
+
+// -------------------------------------------------------------- PLUGIN
+
+static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, void* ws,
+                        size_t ws_bytes, cudaStream_t st, Geometry* gout) {
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  DsDev init = make_desc(g, x_dev, dtype, KDE_METHOD_PLUGIN, w);
+  init.y = nullptr;  // plug-in needs only the centred samples
+  DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
+  int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
+  const int64_t offs[4] = {0, 0, 0, g.prows};
+  CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
+  CK(launch_prep(ds, 1, dtype, st));
+  Phase ph{ds, off + 2, 1, 0, g.prows};
+  const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));
+  CK(mark(2, st));
+  CK(launch_psi(ph, 6, g.Rp, g.kahan, psi_coef(6), grid, st));
+  CK(mark(3, st));
+  CK(launch_psi_finish(ds, 1, 6, 6, st));
+  CK(launch_psi(ph, 4, g.Rp, g.kahan, psi_coef(4), grid, st));
+  CK(launch_psi_finish(ds, 1, 4, 4, st));
+  if (gout) *gout = g;
+  return KDE_OK;
+}
+
+int kde_plugin_async(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, void* ws,
+                     size_t ws_bytes, void* stream) {
+  int rc = check_common(x_dev, dtype, n, 1, ws);
+  if (rc) return rc;
+  return plugin_queue(x_dev, dtype, n, opts, ws, ws_bytes, (cudaStream_t)stream, nullptr);
+}
+
+int kde_plugin(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, void* ws,
+               size_t ws_bytes, void* stream, kde_result* out) {
+  if (!out) return fail(KDE_EINVAL, "out is NULL");
+  int rc = check_common(x_dev, dtype, n, 1, ws);
+  if (rc) return rc;
+  Geometry g;
+  cudaStream_t st = (cudaStream_t)stream;
+  rc = plugin_queue(x_dev, dtype, n, opts, ws, ws_bytes, st, &g);
+  if (rc) return rc;
+  return fetch_result(g, ws, st, nullptr, nullptr, out);
+}
+
+int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* opts, void* ws,
+                    size_t ws_bytes, void* stream, kde_result* out) {
+  if (!out) return fail(KDE_EINVAL, "out is NULL");
+  int rc = check_common(x_host, dtype, n, 1, ws);
+  if (rc) return rc;
+  rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
+  cudaStream_t st = (cudaStream_t)stream;
+  void* xd = static_cast<unsigned char*>(ws) + g.off_x;
+  CK(cudaMemcpyAsync(xd, x_host, (size_t)n * (dtype == KDE_F64 ? 8 : 4), cudaMemcpyHostToDevice, st));
+  rc = plugin_queue(xd, dtype, n, opts, ws, ws_bytes, st, &g);
+  if (rc) return rc;
+  return fetch_result(g, ws, st, nullptr, nullptr, out);
+}
+
+int kde_set_kernel_events(void* lscv_begin, void* lscv_end, void* psi_begin, void* psi_end) {
+  t_ev[0] = (cudaEvent_t)lscv_begin;
+  t_ev[1] = (cudaEvent_t)lscv_end;
+  t_ev[2] = (cudaEvent_t)psi_begin;
+  t_ev[3] = (cudaEvent_t)psi_end;
+  return KDE_OK;
+}
+
+int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpil,
+                      int64_t tile_begin, int64_t tile_end, const kde_opts* opts, void* ws,
+                      size_t ws_bytes, void* stream, double* sum_host) {
+  int rc = check_common(x_dev, dtype, n, 1, ws);
+  if (rc) return rc;
+  if (r != 4 && r != 6 && r != 8) return fail(KDE_EINVAL, "r = %d: only 4, 6, 8", r);
+  if (!(gpil > 0) || !std::isfinite(gpil)) return fail(KDE_EINVAL, "g = %g invalid", gpil);
+  rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
+  if (tile_begin < 0 || tile_end < tile_begin || tile_end > g.ptiles)
+    return fail(KDE_EINVAL, "tile range outside [0, %lld)", (long long)g.ptiles);
+  if (tile_end == tile_begin) {
+    if (sum_host) *sum_host = 0;
+    return KDE_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  DsDev init = make_desc(g, x_dev, dtype, 0, w);
+  init.y = nullptr;
+  init.psi_t0 = tile_begin;
+  init.psi_tiles = tile_end;
+  init.psi_rows = (tile_end - tile_begin + g.Kp - 1) / g.Kp;
+  init.psi_scale = (float)(std::sqrt(0.5 / std::log(2.0)) / gpil);
+  DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
+  int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
+  const int64_t offs[4] = {0, 0, 0, init.psi_rows};
+  CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
+  CK(launch_prep(ds, 1, dtype, st));
+  Phase ph{ds, off + 2, 1, 0, init.psi_rows};
+  const int grid = std::max(1, (int)std::min<int64_t>(init.psi_rows, g.ctas));
+  CK(launch_psi(ph, r, g.Rp, g.kahan, psi_coef(r), grid, st));
+  CK(launch_psi_finish(ds, 1, 0, r, st));
+  kde_result res;
+  CK(cudaMemcpyAsync(&res, w + g.off_ds + offsetof(DsDev, res), sizeof(res), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (res.status != KDE_OK) return fail(res.status, "psi tile sums failed on the device: %s", kde_status_string(res.status));
+  if (sum_host) *sum_host = res.g_min;
+  return KDE_OK;
+}
+
+// ------------------------------------------------------------- probe
+
+int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu, double* ffma,
+                  double* ffma2, int* sm_count, double* sm_mhz) {
+  const int sms = device_sms();
+  if (sms <= 0) return fail(KDE_ECUDA, "no CUDA device");
+  const int per_sm = 4, grid = sms * per_sm;
+  if (!ws || ws_bytes < sizeof(double) * 2 * grid) return fail(KDE_ENOMEM, "probe needs %zu bytes", sizeof(double) * 2 * grid);
+  cudaStream_t st = (cudaStream_t)stream;
+  double* dout = static_cast<double*>(ws);
+  const int iters[3] = {1500, 6000, 6000};
+  const double lanes_per_op[3] = {1.0, 1.0, 2.0};
+  double rate[3] = {0, 0, 0}, mhz = 0;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<double> cyc(grid);
+  for (int mode = 0; mode < 3; ++mode) {
+    CK(launch_probe_mode(mode, dout, iters[mode] / 4, grid, st));  // warm-up
+    CK(cudaEventRecord(e0, st));
+    CK(launch_probe_mode(mode, dout, iters[mode], grid, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaMemcpyAsync(cyc.data(), dout, sizeof(double) * grid, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    std::vector<double> s = cyc;
+    std::sort(s.begin(), s.end());
+    const double med = s[grid / 2];
+    const double ops_per_sm = (double)per_sm * 256.0 * iters[mode] * 32.0 * lanes_per_op[mode];
+    rate[mode] = ops_per_sm / med;
+    if (mode == 0) mhz = s[grid - 1] / (ms * 1e3);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (mufu) *mufu = rate[0];
+  if (ffma) *ffma = rate[1];
+  if (ffma2) *ffma2 = rate[2];
+  if (sm_count) *sm_count = sms;
+  if (sm_mhz) *sm_mhz = mhz;
+  return KDE_OK;
+}
+
+}  // extern "C"

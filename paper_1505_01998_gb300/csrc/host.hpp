@@ -1,0 +1,41 @@
+// Host-side declarations shared by the C-ABI translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace gbkde {
+
+// Geometry and workspace layout of one selection (see make_geometry).
+struct Geometry {
+  int64_t n;
+  int d;
+  int n_h;
+  int64_t n_pad;
+  bool kahan;
+  int ctas;  // persistent CTAs of the pair kernels
+  // LSCV: tile T = 32 R, B bandwidths per thread, K tiles per item
+  int T, R, B, n_h_pad, n_chunks, G, K;
+  int64_t tiles, rows, items;
+  // psi: tile Tp = 32 Rp, Kp tiles per item
+  int Tp, Rp, Kp;
+  int64_t ptiles, prows;
+  // workspace offsets (bytes)
+  size_t off_ds, off_off, off_h, off_nc, off_g, off_sum, off_x, off_y, off_xc, off_lpart,
+      off_ppart, total;
+};
+
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+int device_sms();
+int check_opts(const kde_opts* o);
+int check_common(const void* x, int dtype, int64_t n, int d, void* ws);
+int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g);
+int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h);
+DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsigned char* ws);
+PsiCoef psi_coef(int r);
+
+}  // namespace gbkde

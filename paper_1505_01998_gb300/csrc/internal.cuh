@@ -1,0 +1,158 @@
+// Internal declarations shared by the CUDA translation units of libgbkde.
+// Device descriptors, the triangular tile map, and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gbkde.h"
+
+namespace gbkde {
+
+constexpr int kThreads = 256;  // threads per CTA of every pair kernel (8 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kPadTo = 256;    // sample arrays are zero-padded to a multiple of this
+
+// Per-dataset descriptor, resident in device memory for the whole selection.
+// Host code fills the geometry; the prologue kernel fills the statistics; the
+// finishing kernels fill `res`.
+struct DsDev {
+  // ---- input
+  const void* x;    // d x n samples, row-major (coordinate-major)
+  int64_t n;
+  int32_t d;
+  int32_t dtype;    // KDE_F32 / KDE_F64
+  int64_t n_pad;    // n rounded up to kPadTo
+  int32_t methods;  // KDE_METHOD_* bits to run
+  int32_t given_H;  // 1: whiten by the matrix in cov[] (LSCV_H) instead of the sample covariance
+  // ---- prepared samples
+  float* y;   // [d][n_pad]  sqrt(log2(e)/4) L^-1 (x - mean), zero padded   (LSCV)
+  float* xc;  // [n_pad]     x - mean, zero padded                           (d = 1)
+  // ---- LSCV geometry
+  int32_t n_h, n_h_pad;    // grid size and size padded to a multiple of B
+  int32_t n_chunks;        // n_h_pad / B
+  int32_t n_groups;        // ceil(n_chunks / kWarps): one CTA item covers one group
+  int32_t lscv_tile;       // T
+  int32_t lscv_K;          // tiles per item
+  int64_t lscv_tiles;      // end of the tile range walked (NT (NT+1)/2 for a full selection)
+  int64_t lscv_rows;       // ceil((lscv_tiles - lscv_t0) / lscv_K)
+  int64_t lscv_t0;         // first tile of the range walked (0 for a full selection)
+  double* h;               // [n_h]   bandwidth multipliers
+  float* nc;               // [n_h_pad] -1/h^2 (padded entries -1)
+  double* lscv_part;       // [lscv_rows][2 n_h_pad] per-item (S1, S2) partials
+  double* lscv_sum;        // [2 n_h_pad] reduced (S1, S2)
+  double* g;               // [n_h] objective
+  // ---- psi geometry
+  int32_t psi_tile;
+  int32_t psi_K;
+  int64_t psi_tiles;
+  int64_t psi_rows;
+  int64_t psi_t0;
+  double* psi_part;        // [psi_rows]
+  float psi_scale;         // sqrt(log2(e)/2) / g for the pilot g of the running phase
+  int32_t pad1;
+  // ---- statistics (written on the device)
+  double mean[KDE_MAX_D];
+  double cov[KDE_MAX_D * KDE_MAX_D];
+  double logdet;
+  double sigma;
+  double A;                // (4 pi)^(-d/2) |S|^(-1/2)
+  float M[KDE_MAX_D * KDE_MAX_D];  // sqrt(log2(e)/4) L^-1, row-major, lower triangular
+  kde_result res;
+};
+
+// One launch of a pair kernel walks the items of several datasets:
+// item k belongs to dataset i with off[i] <= k < off[i+1].
+struct Phase {
+  DsDev* ds;
+  const int64_t* off;
+  int32_t n_ds;
+  int32_t pad;
+  int64_t total;
+};
+
+// Horner coefficients of the psi kernel polynomial (see psi kernels).
+struct PsiCoef {
+  float c[5];  // p(y) = ((y + c0) y + c1) y ... ; degree r/2, monic
+};
+
+// Tile map of the upper pair triangle (Sec. 5.4.2, Eqs. colInTriangleMatrix,
+// rowInTriangleMatrix; Appendix A): column l holds the l+1 tiles numbered
+// l(l+1)/2 .. l(l+1)/2 + l, row q = bx - l(l+1)/2.  The single-precision
+// square root can land one column off for large bx; an exact integer
+// correction follows.
+__host__ __device__ inline void tile_coords(int64_t bx, int64_t& l, int64_t& q) {
+  float s = sqrtf(8.0f * (float)bx + 9.0f);
+  int64_t L = (int64_t)ceilf((s - 3.0f) * 0.5f);
+  if (L < 0) L = 0;
+  while (L > 0 && L * (L + 1) / 2 > bx) --L;
+  while ((L + 1) * (L + 2) / 2 <= bx) ++L;
+  l = L;
+  q = bx - L * (L + 1) / 2;
+}
+
+__host__ __device__ inline int64_t tri_tiles(int64_t n, int tile) {
+  int64_t nt = (n + tile - 1) / tile;
+  return nt * (nt + 1) / 2;
+}
+
+#ifdef __CUDACC__
+// 2^a by the MUFU unit (PTX ex2.approx.ftz.f32).
+__device__ __forceinline__ float ex2(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+// Kahan compensated update of (s, c) by v; the running total is s - c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  float y = v - c;
+  float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Index of the dataset owning global item `it` (largest i with off[i] <= it).
+__device__ __forceinline__ int find_ds(const int64_t* off, int n, int64_t it) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+#endif
+
+// ------------------------------------------------------------- launchers
+// (defined in the .cu files; return a cudaError_t)
+cudaError_t launch_prep(DsDev* ds, int n_ds, int dtype, cudaStream_t st);
+cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
+                        cudaStream_t st);
+size_t lscv_smem_bytes(int d, int B, int R, bool kahan);
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, int n_h_pad_max, cudaStream_t st);
+cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, cudaStream_t st);
+cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef& cf, int grid,
+                       cudaStream_t st);
+// stage: 6 -> reduce psi_6, set g2; 4 -> reduce psi_4, set h; 0 -> raw sum only (into res.g_min)
+cudaError_t launch_psi_finish(DsDev* ds, int n_ds, int stage, int r, cudaStream_t st);
+cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
+                         int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st);
+cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st);
+
+}  // namespace gbkde

@@ -1,0 +1,330 @@
+// Fused all-pairs, all-bandwidths LSCV kernel and its reductions.
+//
+// For every pair i < j of a dataset and every grid multiplier h it accumulates
+//   S1(h) = sum exp(-S(v)/(4 h^2)),   S2(h) = sum exp(-S(v)/(2 h^2)) = sum e^2,
+// from which g(h) = h^-d A [2 n^-2 (S1 - 2^(1+d/2) S2) + n^-1] (Sec. 4.4.2,
+// Eqs. LSCV-gh, LSCV-Tx, LSCV-Kx, LSCV-KKx with A = (4 pi)^(-d/2)|S|^(-1/2)).
+// S(v) = v^T S^-1 v (Eq. LSCV_MOD-Pv) is formed once per pair from samples
+// whitened on the device (y = sqrt(log2 e / 4) L^-1 (x - mean), S = L L^T), so
+// Q = |y_i - y_j|^2 and e = 2^(-Q/h^2).  The paper precomputes and stores all
+// n(n-1)/2 values S(v) and re-reads them once per h (Sec. 5.5, Sec. 6.2); here
+// the value lives in a register and feeds a whole chunk of bandwidths.
+//
+// Work decomposition: the pair triangle is cut into T x T tiles numbered by
+// the tile map of Sec. 5.4.2; an item is K consecutive tiles times one group
+// of up to 8 chunks of B bandwidths.  A persistent CTA of 8 warps takes items
+// in a grid-stride loop; each warp owns one chunk of B bandwidths (and a
+// column slice of the tile when a group has fewer than 8 chunks); each lane
+// holds R row samples in registers and walks the column samples staged in
+// shared memory (broadcast reads).  Per-thread sums: FP32 runs over a tile,
+// folded into Kahan-compensated FP32 accumulators; per-item totals in FP64.
+// Every item writes its own partial row, and rows are added in a fixed order,
+// so results do not depend on the grid size or on which CTA ran an item.
+#include "internal.cuh"
+
+namespace gbkde {
+
+namespace {
+
+template <int D>
+struct DPad {
+  static constexpr int value = (D == 3) ? 4 : D;
+};
+
+// Columns [j_lo, j_hi) of one tile for this lane's R rows and B bandwidths.
+// Bandwidths are processed in pairs with packed FP32x2 arithmetic.
+template <int D, int B, int R, bool EDGE>
+__device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j_lo, int j_hi,
+                                             const float (&y)[R][D], const float2 (&nc2)[B / 2],
+                                             float2 (&t1)[B / 2], float2 (&t2)[B / 2],
+                                             int64_t i0, int64_t jg0, int64_t n) {
+  constexpr int DP = DPad<D>::value;
+  constexpr int CPI = 4 / DP;  // columns per 16-byte shared-memory load
+#pragma unroll 1
+  for (int jj = j_lo; jj < j_hi; jj += CPI) {
+    const float4 v = *reinterpret_cast<const float4*>(sF + jj * DP);
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < CPI; ++c) {
+      float2 q2[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float dl = y[r][k] - vv[c * DP + k];
+          acc = fmaf(dl, dl, acc);
+        }
+        if (EDGE) {
+          const int64_t i = i0 + 32 * r, j = jg0 + jj + c;
+          if (!(i < j && j < n)) acc = __int_as_float(0x7f800000);  // +inf -> e = 0
+        }
+        q2[r] = make_float2(acc, acc);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int bp = 0; bp < B / 2; ++bp) {
+          const float2 a = __fmul2_rn(q2[r], nc2[bp]);
+          const float2 e = make_float2(ex2(a.x), ex2(a.y));
+          t1[bp] = __fadd2_rn(t1[bp], e);
+          t2[bp] = __ffma2_rn(e, e, t2[bp]);
+        }
+      }
+    }
+  }
+}
+
+template <int D, int B, int R, bool KAHAN>
+__global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
+  constexpr int T = 32 * R;
+  constexpr int DP = DPad<D>::value;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* sF = reinterpret_cast<float*>(smem);                                 // [T][DP]
+  double* sRed = reinterpret_cast<double*>(smem + T * DP * 4);                // [8][B][2]
+  float4* sK = reinterpret_cast<float4*>(smem + T * DP * 4 + kWarps * B * 16);  // [8][B][32]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  for (int64_t it = blockIdx.x; it < ph.total; it += gridDim.x) {
+    const int di = find_ds(ph.off, ph.n_ds, it);
+    const DsDev* ds = ph.ds + di;
+    if (ds->res.status != KDE_OK) continue;
+    const int64_t li = it - ph.off[di];
+    const int G = ds->n_groups;
+    const int hg = (int)(li % G);
+    const int64_t row = li / G;
+    const int64_t tb = ds->lscv_t0 + row * ds->lscv_K;
+    const int64_t te = min(tb + (int64_t)ds->lscv_K, ds->lscv_tiles);
+    const int cg = min(kWarps, ds->n_chunks - hg * kWarps);
+    const int S = cg >= 8 ? 1 : cg >= 4 ? 2 : cg >= 2 ? 4 : 8;
+    const int my_chunk = warp % cg, my_slice = warp / cg;
+    const bool active = my_slice < S;
+    const int cols = T / S;
+    const int j_lo = active ? my_slice * cols : 0;
+    const int j_hi = active ? j_lo + cols : 0;
+    const int hbase = (hg * kWarps + my_chunk) * B;
+
+    float2 nc2[B / 2], t1[B / 2], t2[B / 2];
+#pragma unroll
+    for (int bp = 0; bp < B / 2; ++bp) {
+      nc2[bp] = make_float2(ds->nc[hbase + 2 * bp], ds->nc[hbase + 2 * bp + 1]);
+      t1[bp] = make_float2(0.f, 0.f);
+      t2[bp] = make_float2(0.f, 0.f);
+    }
+    if (KAHAN) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) sK[(warp * B + b) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int64_t n = ds->n, n_pad = ds->n_pad;
+    const float* __restrict__ Y = ds->y;
+    const int flush_every = max(1, 256 / (R * cols));
+    int64_t l, q;
+    tile_coords(tb, l, q);
+    int64_t l_loaded = -1;
+    int run = 0;
+    for (int64_t t = tb; t < te; ++t) {
+      if (l != l_loaded) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < T * DP; idx += kThreads) {
+          const int jj = idx / DP, k = idx - jj * DP;
+          sF[idx] = (k < D) ? Y[(int64_t)k * n_pad + l * T + jj] : 0.f;
+        }
+        __syncthreads();
+        l_loaded = l;
+      }
+      float y[R][D];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) y[r][k] = Y[(int64_t)k * n_pad + q * T + lane + 32 * r];
+      const bool edge = (q == l) || ((l + 1) * T > n);
+      const int64_t i0 = q * T + lane, jg0 = l * T;
+      if (edge)
+        lscv_columns<D, B, R, true>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
+      else
+        lscv_columns<D, B, R, false>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
+      if (KAHAN && ++run >= flush_every) {
+#pragma unroll
+        for (int bp = 0; bp < B / 2; ++bp) {
+          float4 k0 = sK[(warp * B + 2 * bp) * 32 + lane];
+          float4 k1 = sK[(warp * B + 2 * bp + 1) * 32 + lane];
+          kahan_add(k0.x, k0.y, t1[bp].x);
+          kahan_add(k0.z, k0.w, t2[bp].x);
+          kahan_add(k1.x, k1.y, t1[bp].y);
+          kahan_add(k1.z, k1.w, t2[bp].y);
+          sK[(warp * B + 2 * bp) * 32 + lane] = k0;
+          sK[(warp * B + 2 * bp + 1) * 32 + lane] = k1;
+          t1[bp] = make_float2(0.f, 0.f);
+          t2[bp] = make_float2(0.f, 0.f);
+        }
+        run = 0;
+      }
+      if (++q > l) {
+        ++l;
+        q = 0;
+      }
+    }
+    // ---- item total: lanes (FP64 butterfly), then column slices in fixed order
+    __syncthreads();
+#pragma unroll
+    for (int bp = 0; bp < B / 2; ++bp) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int b = 2 * bp + half;
+        double v1, v2;
+        if (KAHAN) {
+          float4 k = sK[(warp * B + b) * 32 + lane];
+          const float r1 = half ? t1[bp].y : t1[bp].x;  // unflushed tail of the run
+          const float r2 = half ? t2[bp].y : t2[bp].x;
+          kahan_add(k.x, k.y, r1);
+          kahan_add(k.z, k.w, r2);
+          v1 = (double)k.x - (double)k.y;
+          v2 = (double)k.z - (double)k.w;
+        } else {
+          v1 = half ? t1[bp].y : t1[bp].x;
+          v2 = half ? t2[bp].y : t2[bp].x;
+        }
+        if (!active) v1 = v2 = 0.0;
+        v1 = warp_sum(v1);
+        v2 = warp_sum(v2);
+        if (lane == 0) {
+          sRed[(warp * B + b) * 2] = v1;
+          sRed[(warp * B + b) * 2 + 1] = v2;
+        }
+      }
+    }
+    __syncthreads();
+    double* out = ds->lscv_part + row * (2 * (int64_t)ds->n_h_pad) + (int64_t)hg * kWarps * B * 2;
+    for (int o = threadIdx.x; o < cg * B * 2; o += kThreads) {
+      const int c = o / (2 * B), rem = o - c * 2 * B;
+      double s = 0.0;
+      for (int sl = 0; sl < S; ++sl) s += sRed[(sl * cg + c) * B * 2 + rem];
+      out[o] = s;
+    }
+  }
+}
+
+// Sum of the per-item partial rows, one 32-column strip per CTA: warp w adds
+// rows w, w+8, ... ; the 8 warp sums are added in order.
+__global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa) {
+  DsDev* ds = dsa + blockIdx.x;
+  __shared__ double s[kWarps][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
+  const int W = 2 * ds->n_h_pad;
+  const int col = blockIdx.y * 32 + lane;
+  double acc = 0.0;
+  if (col < W) {
+    const double* p = ds->lscv_part + col;
+    for (int64_t r = warp; r < ds->lscv_rows; r += kWarps) acc += p[r * W];
+  }
+  s[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && col < W) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s[w][lane];
+    ds->lscv_sum[col] = t;
+  }
+}
+
+// g(h) on the grid and its first-index argmin (Eqs. LSCV-gh, LSCV-finalH).
+__global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa) {
+  DsDev* ds = dsa + blockIdx.x;
+  if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
+  const int d = ds->d, n_h = ds->n_h;
+  const double n = (double)ds->n;
+  const double c2 = exp2(1.0 + 0.5 * d);
+  for (int k = threadIdx.x; k < n_h; k += blockDim.x) {
+    const double s1 = ds->lscv_sum[2 * k], s2 = ds->lscv_sum[2 * k + 1];
+    ds->g[k] = pow(ds->h[k], -(double)d) * ds->A * (2.0 / (n * n) * (s1 - c2 * s2) + 1.0 / n);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int best = 0;
+    double gb = ds->g[0];
+    for (int k = 1; k < n_h; ++k)
+      if (ds->g[k] < gb) {
+        gb = ds->g[k];
+        best = k;
+      }
+    kde_result& r = ds->res;
+    r.method |= KDE_METHOD_LSCV;
+    r.argmin = best;
+    r.n_h = n_h;
+    r.g_min = gb;
+    r.h = ds->h[best];
+    r.h_data = (d == 1) ? ds->h[best] * ds->sigma : 0.0;
+    r.flags = (best == 0 ? KDE_FLAG_MIN_AT_LOWER_EDGE : 0) |
+              (best == n_h - 1 ? KDE_FLAG_MIN_AT_UPPER_EDGE : 0);
+  }
+}
+
+template <int D, int B, int R, bool KAHAN>
+cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
+  const size_t smem = lscv_smem_bytes(D, B, R, KAHAN);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_lscv<D, B, R, KAHAN><<<grid, kThreads, smem, st>>>(ph);
+  return cudaGetLastError();
+}
+
+template <int D, int B, int R>
+cudaError_t launch_k(const Phase& ph, bool kahan, int grid, cudaStream_t st) {
+  return kahan ? launch_t<D, B, R, true>(ph, grid, st) : launch_t<D, B, R, false>(ph, grid, st);
+}
+
+template <int D, int B>
+cudaError_t launch_r(const Phase& ph, int R, bool kahan, int grid, cudaStream_t st) {
+  switch (R) {
+    case 1: return launch_k<D, B, 1>(ph, kahan, grid, st);
+    case 4: return launch_k<D, B, 4>(ph, kahan, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int D>
+cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, int grid, cudaStream_t st) {
+  switch (B) {
+    case 8: return launch_r<D, 8>(ph, R, kahan, grid, st);
+    case 16: return launch_r<D, 16>(ph, R, kahan, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+size_t lscv_smem_bytes(int d, int B, int R, bool kahan) {
+  const int dp = (d == 3) ? 4 : d;
+  return (size_t)32 * R * dp * 4 + (size_t)kWarps * B * 16 + (kahan ? (size_t)kWarps * B * 32 * 16 : 0);
+}
+
+cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
+                        cudaStream_t st) {
+  if (ph.total <= 0) return cudaSuccess;
+  switch (d) {
+    case 1: return launch_b<1>(ph, B, R, kahan, grid, st);
+    case 2: return launch_b<2>(ph, B, R, kahan, grid, st);
+    case 3: return launch_b<3>(ph, B, R, kahan, grid, st);
+    case 4: return launch_b<4>(ph, B, R, kahan, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, int n_h_pad_max, cudaStream_t st) {
+  dim3 grid(n_ds, (2 * n_h_pad_max + 31) / 32);
+  k_lscv_reduce<<<grid, kThreads, 0, st>>>(ds);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, cudaStream_t st) {
+  k_lscv_finish<<<n_ds, kThreads, 0, st>>>(ds);
+  return cudaGetLastError();
+}
+
+}  // namespace gbkde

@@ -1,0 +1,237 @@
+// All-pairs kernel of the plug-in functionals psi_r (Sec. 4.4.1,
+// Eqs. PLUGIN-Psi6Estimate, PLUGIN-Psi4Estimate) and the device-side scalar
+// chain of the PLUGIN method (steps 5-8).
+//
+// With z = x sqrt(log2 e / 2) / g and y = (z_i - z_j)^2 we have
+// u^2 = ((x_i - x_j)/g)^2 = kappa y (kappa = 2 ln 2) and exp(-u^2/2) = 2^-y, so
+// K^(r)(u) = He_r(u) phi(u) = kappa^(r/2) p_r(y) 2^-y / sqrt(2 pi), where p_r is
+// He_r rewritten in y and made monic (host code derives its coefficients from
+// the Hermite recurrence).  The kernel sums p_r(y) 2^-y over pairs: per pair one
+// subtraction, one square, one ex2, a Horner chain in y (Sec. 7.1 uses Horner's
+// rule as well) and one fused multiply-add, packed two rows at a time in FP32x2.
+//
+// Schedule: T x T tiles of the pair triangle in the numbering of Sec. 5.4.2;
+// items of K consecutive tiles; persistent CTAs of 8 warps; each warp covers
+// all T rows (R per lane, in registers) against a slice of T/8 columns staged
+// in shared memory.  Per-lane FP32 runs over a tile are folded into a Kahan
+// pair; item totals are reduced in FP64 and written to a per-item slot.
+#include "internal.cuh"
+
+namespace gbkde {
+
+namespace {
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kPi = 3.14159265358979323846;
+
+template <int RD, int R, bool EDGE>
+__device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_lo, int j_hi,
+                                            const float2 (&z)[R / 2], float2 (&acc)[R / 2],
+                                            const PsiCoef& cf, int64_t i0, int64_t jg0,
+                                            int64_t n) {
+  constexpr int M = RD / 2;
+  float2 cc[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) cc[m] = make_float2(cf.c[m], cf.c[m]);
+#pragma unroll 1
+  for (int jj = j_lo; jj < j_hi; jj += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(sF + jj);
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float2 nf = make_float2(-vv[c], -vv[c]);
+#pragma unroll
+      for (int p = 0; p < R / 2; ++p) {
+        const float2 dl = __fadd2_rn(z[p], nf);
+        const float2 y = __fmul2_rn(dl, dl);
+        float2 e = make_float2(ex2(-y.x), ex2(-y.y));
+        if (EDGE) {
+          const int64_t i = i0 + 64 * p, j = jg0 + jj + c;
+          if (!(i < j && j < n)) e.x = 0.f;
+          if (!(i + 32 < j && j < n)) e.y = 0.f;
+        }
+        float2 pq = __fadd2_rn(y, cc[0]);
+#pragma unroll
+        for (int m = 1; m < M; ++m) pq = __ffma2_rn(pq, y, cc[m]);
+        acc[p] = __ffma2_rn(pq, e, acc[p]);
+      }
+    }
+  }
+}
+
+template <int RD, int R, bool KAHAN>
+__global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
+  constexpr int T = 32 * R;
+  __shared__ __align__(16) float sF[T];
+  __shared__ double sRed[kWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int cols = T / kWarps;
+  const int j_lo = warp * cols, j_hi = j_lo + cols;
+
+  for (int64_t it = blockIdx.x; it < ph.total; it += gridDim.x) {
+    const int di = find_ds(ph.off, ph.n_ds, it);
+    const DsDev* ds = ph.ds + di;
+    if (ds->res.status != KDE_OK) continue;
+    const int64_t row = it - ph.off[di];
+    const int64_t t0 = ds->psi_t0 + row * ds->psi_K;
+    const int64_t t1 = min(t0 + (int64_t)ds->psi_K, ds->psi_tiles);
+    const int64_t n = ds->n;
+    const float sc = ds->psi_scale;
+    const float* __restrict__ X = ds->xc;
+    float s = 0.f, c = 0.f;
+    float2 acc[R / 2];
+#pragma unroll
+    for (int p = 0; p < R / 2; ++p) acc[p] = make_float2(0.f, 0.f);
+    int64_t l, q;
+    tile_coords(t0, l, q);
+    int64_t l_loaded = -1;
+    for (int64_t t = t0; t < t1; ++t) {
+      if (l != l_loaded) {
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < T; jj += kThreads) sF[jj] = X[l * T + jj] * sc;
+        __syncthreads();
+        l_loaded = l;
+      }
+      float2 z[R / 2];
+#pragma unroll
+      for (int p = 0; p < R / 2; ++p)
+        z[p] = make_float2(X[q * T + lane + 64 * p] * sc, X[q * T + lane + 64 * p + 32] * sc);
+      const bool edge = (q == l) || ((l + 1) * T > n);
+      const int64_t i0 = q * T + lane, jg0 = l * T;
+      if (edge)
+        psi_columns<RD, R, true>(sF, j_lo, j_hi, z, acc, cf, i0, jg0, n);
+      else
+        psi_columns<RD, R, false>(sF, j_lo, j_hi, z, acc, cf, i0, jg0, n);
+      if (KAHAN) {
+        float run = 0.f;
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+          run += acc[p].x + acc[p].y;
+          acc[p] = make_float2(0.f, 0.f);
+        }
+        kahan_add(s, c, run);
+      }
+      if (++q > l) {
+        ++l;
+        q = 0;
+      }
+    }
+    double v;
+    if (KAHAN) {
+      v = (double)s - (double)c;
+    } else {
+      float run = 0.f;
+#pragma unroll
+      for (int p = 0; p < R / 2; ++p) run += acc[p].x + acc[p].y;
+      v = (double)run;
+    }
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sRed[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) tot += sRed[w];
+      ds->psi_part[row] = tot;
+    }
+  }
+}
+
+// Reduce the per-item psi partials in a fixed order and advance the PLUGIN
+// chain on the device in FP64.
+//   stage 6: psi_6(g1) (Eq. PLUGIN-Psi6Estimate, reading R1), then g2
+//            (Eq. PLUGIN-g2) and the psi_4 sample scale;
+//   stage 4: psi_4(g2) (Eq. PLUGIN-Psi4Estimate, reading R1), then h
+//            (Eq. PLUGIN-Final_h);
+//   stage 0: raw pair sum only (psi tile-sum entry point), into res.g_min.
+__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, int stage, int r) {
+  DsDev* ds = dsa + blockIdx.x;
+  __shared__ double sRed[kWarps];
+  if (ds->res.status != KDE_OK) return;
+  if (stage != 0 && !(ds->methods & KDE_METHOD_PLUGIN)) return;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < ds->psi_rows; k += kThreads) acc += ds->psi_part[k];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double P = 0.0;
+  for (int w = 0; w < kWarps; ++w) P += sRed[w];
+  const double kappa = 2.0 * 0.69314718055994530942;
+  const double inv_sqrt_2pi = 0.39894228040143267794;
+  // sum_{i<j} K^(r)((x_i - x_j)/g) = kappa^(r/2) P / sqrt(2 pi)
+  const double sumK = pow(kappa, 0.5 * r) * P * inv_sqrt_2pi;
+  kde_result& res = ds->res;
+  if (stage == 0) {
+    res.g_min = sumK;
+    return;
+  }
+  const double n = (double)ds->n;
+  if (stage == 6) {
+    const double k6_0 = -15.0 * inv_sqrt_2pi;  // K^(6)(0), Eq. PLUGIN-g1
+    const double k4_0 = 3.0 * inv_sqrt_2pi;    // K^(4)(0), Eq. PLUGIN-g2
+    const double g1 = res.g1;
+    const double psi6 = (2.0 * sumK + n * k6_0) / (n * n * pow(g1, 7.0));
+    res.psi6 = psi6;
+    if (!(psi6 < 0.0)) {
+      res.status = KDE_EDEGENERATE;
+      return;
+    }
+    const double g2 = pow(-2.0 * k4_0 / (psi6 * n), 1.0 / 7.0);
+    res.g2 = g2;
+    ds->psi_scale = (float)(sqrt(0.5 * kLog2e) / g2);
+  } else {
+    const double k4_0 = 3.0 * inv_sqrt_2pi;
+    const double g2 = res.g2;
+    const double psi4 = (2.0 * sumK + n * k4_0) / (n * n * pow(g2, 5.0));
+    res.psi4 = psi4;
+    if (!(psi4 > 0.0)) {
+      res.status = KDE_EDEGENERATE;
+      return;
+    }
+    const double rk = 1.0 / (2.0 * sqrt(kPi));  // R(K), Eq. PLUGIN-Final_h
+    const double h = pow(rk / (psi4 * n), 0.2);
+    res.h = h;
+    res.h_data = h;
+  }
+}
+
+template <int RD, int R>
+cudaError_t launch_k(const Phase& ph, bool kahan, const PsiCoef& cf, int grid, cudaStream_t st) {
+  if (kahan)
+    k_psi<RD, R, true><<<grid, kThreads, 0, st>>>(ph, cf);
+  else
+    k_psi<RD, R, false><<<grid, kThreads, 0, st>>>(ph, cf);
+  return cudaGetLastError();
+}
+
+template <int RD>
+cudaError_t launch_r(const Phase& ph, int R, bool kahan, const PsiCoef& cf, int grid,
+                     cudaStream_t st) {
+  switch (R) {
+    case 2: return launch_k<RD, 2>(ph, kahan, cf, grid, st);
+    case 8: return launch_k<RD, 8>(ph, kahan, cf, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef& cf, int grid,
+                       cudaStream_t st) {
+  if (ph.total <= 0) return cudaSuccess;
+  switch (r) {
+    case 4: return launch_r<4>(ph, R, kahan, cf, grid, st);
+    case 6: return launch_r<6>(ph, R, kahan, cf, grid, st);
+    case 8: return launch_r<8>(ph, R, kahan, cf, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_psi_finish(DsDev* ds, int n_ds, int stage, int r, cudaStream_t st) {
+  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, stage, r);
+  return cudaGetLastError();
+}
+
+}  // namespace gbkde

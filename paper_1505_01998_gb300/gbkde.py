@@ -1,0 +1,343 @@
+"""Thin Python binding of libgbkde (include/gbkde.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+PyTorch provides device memory (the workspace and device-resident samples) and
+CUDA streams.  Functions keep the C names; structs mirror the C structs.
+If the shared library has not been built, every call raises: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbkde.so")
+
+KDE_OK, KDE_EINVAL, KDE_ENOMEM, KDE_ECUDA, KDE_EDEGENERATE = 0, 1, 2, 3, 4
+KDE_EBUSY, KDE_EAGAIN, KDE_ETIMEDOUT, KDE_ECANCELLED, KDE_ENOTFOUND, KDE_EINTERNAL = 5, 6, 7, 8, 9, 10
+KDE_F32, KDE_F64 = 0, 1
+KDE_FP32_KAHAN, KDE_FP32_PLAIN = 0, 1
+KDE_GRID_DEFAULT_Z, KDE_GRID_EXPLICIT, KDE_GRID_LOG = 0, 1, 2
+KDE_METHOD_LSCV, KDE_METHOD_PLUGIN = 1, 2
+KDE_FLAG_MIN_AT_LOWER_EDGE, KDE_FLAG_MIN_AT_UPPER_EDGE = 1, 2
+KDE_MAX_D, KDE_MAX_NH = 4, 1024
+
+
+class KdeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[status {status}] {msg}")
+        self.status = status
+
+
+class kde_grid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n_h", ctypes.c_int),
+                ("h", ctypes.POINTER(ctypes.c_double)),
+                ("h_min", ctypes.c_double), ("h_max", ctypes.c_double)]
+
+
+class kde_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tile", ctypes.c_int),
+                ("bw_per_thread", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int)]
+
+
+class kde_result(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int) for k in ("status", "method", "argmin", "flags", "n_h", "d")] + [
+        (k, ctypes.c_double) for k in ("h", "h_data", "g_min", "sigma", "psi8_ns", "g1", "psi6",
+                                       "g2", "psi4", "logdet_S")]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+# C signatures: name -> (restype, argtypes)
+_P, _I, _L, _D, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+_DP = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "kde_version": (ctypes.c_char_p, []),
+    "kde_last_error": (_I, [ctypes.c_char_p, _S]),
+    "kde_status_string": (ctypes.c_char_p, [_I]),
+    "kde_tile_count": (_I, [_L, _I, ctypes.POINTER(ctypes.c_int64)]),
+    "kde_tile_coords": (_I, [_L, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    "kde_default_grid": (_I, [_L, _I, _I, _DP]),
+    "kde_workspace_size": (_I, [_L, _I, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_size_t)]),
+    "kde_ws_result_offset": (_I, [ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "kde_lscv": (_I, [_P, _I, _L, _I, ctypes.POINTER(kde_grid), ctypes.POINTER(kde_opts), _P, _S, _P,
+                      _DP, _DP, ctypes.POINTER(kde_result)]),
+    "kde_lscv_async": (_I, [_P, _I, _L, _I, ctypes.POINTER(kde_grid), ctypes.POINTER(kde_opts), _P,
+                            _S, _P]),
+    "kde_lscv_host": (_I, [_P, _I, _L, _I, ctypes.POINTER(kde_grid), ctypes.POINTER(kde_opts), _P, _S,
+                           _P, _DP, ctypes.POINTER(kde_result)]),
+    "kde_lscv_tile_sums": (_I, [_P, _I, _L, _I, _DP, _I, _L, _L, ctypes.POINTER(kde_opts), _P, _S, _P,
+                                _DP, _DP]),
+    "kde_plugin": (_I, [_P, _I, _L, ctypes.POINTER(kde_opts), _P, _S, _P, ctypes.POINTER(kde_result)]),
+    "kde_plugin_async": (_I, [_P, _I, _L, ctypes.POINTER(kde_opts), _P, _S, _P]),
+    "kde_plugin_host": (_I, [_P, _I, _L, ctypes.POINTER(kde_opts), _P, _S, _P,
+                             ctypes.POINTER(kde_result)]),
+    "kde_set_kernel_events": (_I, [_P, _P, _P, _P]),
+    "kde_psi_tile_sums": (_I, [_P, _I, _L, _I, _D, _L, _L, ctypes.POINTER(kde_opts), _P, _S, _P, _DP]),
+    "kde_psi_tile_edge": (_I, [_L, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int)]),
+    "kde_probe_alu": (_I, [_P, _S, _P, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), _DP]),
+}
+
+
+def lib():
+    """Load libgbkde.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != KDE_OK:
+        buf = ctypes.create_string_buffer(512)
+        lib().kde_last_error(buf, 512)
+        raise KdeError(rc, buf.value.decode(errors="replace"))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+# ------------------------------------------------------------------ helpers
+
+def make_opts(precision=KDE_FP32_KAHAN, tile=0, bw_per_thread=0, tiles_per_item=0, ctas_per_sm=0):
+    return kde_opts(precision, tile, bw_per_thread, tiles_per_item, ctas_per_sm)
+
+
+def make_grid(h=None, n_h=None, h_min=None, h_max=None):
+    """Explicit grid from an array h, log grid from (h_min, h_max, n_h), or the
+    default Z(h0) grid from n_h alone.  Returns (kde_grid, keepalive)."""
+    if h is not None:
+        arr = np.ascontiguousarray(np.asarray(h, dtype=np.float64).ravel())
+        return kde_grid(KDE_GRID_EXPLICIT, arr.size, _dp(arr), 0.0, 0.0), arr
+    if h_min is not None:
+        return kde_grid(KDE_GRID_LOG, int(n_h), None, float(h_min), float(h_max)), None
+    return kde_grid(KDE_GRID_DEFAULT_Z, int(n_h), None, 0.0, 0.0), None
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return KDE_F32
+    if t.dtype == torch.float64:
+        return KDE_F64
+    raise TypeError(f"samples must be float32 or float64, got {t.dtype}")
+
+
+def _samples(x):
+    """(d, n) contiguous device tensor -> (ptr, dtype, n, d)."""
+    if x.dim() == 1:
+        x = x[None, :]
+    if not x.is_cuda:
+        raise ValueError("samples must be a CUDA tensor; use kde_lscv_host for host data")
+    if not x.is_contiguous():
+        raise ValueError("samples must be contiguous (d, n)")
+    return ctypes.c_void_p(x.data_ptr()), _dtype_code(x), int(x.shape[1]), int(x.shape[0])
+
+
+def kde_version() -> str:
+    return lib().kde_version().decode()
+
+
+def kde_tile_count(n: int, tile: int) -> int:
+    out = ctypes.c_int64(0)
+    _check(lib().kde_tile_count(int(n), int(tile), ctypes.byref(out)))
+    return out.value
+
+
+def kde_tile_coords(bx: int):
+    l, q = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().kde_tile_coords(int(bx), ctypes.byref(l), ctypes.byref(q)))
+    return l.value, q.value
+
+
+def kde_default_grid(n: int, d: int, n_h: int) -> np.ndarray:
+    out = np.zeros(n_h)
+    _check(lib().kde_default_grid(int(n), int(d), int(n_h), _dp(out)))
+    return out
+
+
+def kde_workspace_size(n: int, d: int, n_h: int, opts: kde_opts | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().kde_workspace_size(int(n), int(d), int(n_h),
+                                    ctypes.byref(opts) if opts else None, ctypes.byref(out)))
+    return out.value
+
+
+def kde_ws_result_offset():
+    r, g = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    _check(lib().kde_ws_result_offset(ctypes.byref(r), ctypes.byref(g)))
+    return r.value, g.value
+
+
+def workspace(nbytes: int, device=None):
+    """A device workspace (torch uint8 tensor, 256-byte aligned)."""
+    import torch
+    t = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-t.data_ptr()) % 256
+    return t[off:off + int(nbytes)]
+
+
+def _ws(ws):
+    return ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel())
+
+
+def kde_lscv(x, grid: kde_grid, opts: kde_opts | None = None, ws=None, stream=None):
+    """LSCV_h selection on device samples x (d, n).  Returns (result dict, g, h)."""
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, d, grid.n_h, opts), x.device)
+    wp, wn = _ws(ws)
+    g = np.zeros(grid.n_h)
+    h = np.zeros(grid.n_h)
+    res = kde_result()
+    _check(lib().kde_lscv(ptr, dt, n, d, ctypes.byref(grid), ctypes.byref(opts) if opts else None,
+                          wp, wn, _stream_handle(stream), _dp(g), _dp(h), ctypes.byref(res)))
+    return res.as_dict(), g, h
+
+
+def kde_lscv_async(x, grid: kde_grid, opts: kde_opts | None, ws, stream=None):
+    ptr, dt, n, d = _samples(x)
+    wp, wn = _ws(ws)
+    _check(lib().kde_lscv_async(ptr, dt, n, d, ctypes.byref(grid),
+                                ctypes.byref(opts) if opts else None, wp, wn, _stream_handle(stream)))
+
+
+def kde_lscv_host(x_host: np.ndarray, grid: kde_grid, opts: kde_opts | None, ws, stream=None):
+    """LSCV_h selection on HOST samples (copied into the workspace on the stream)."""
+    a = np.ascontiguousarray(x_host)
+    if a.ndim == 1:
+        a = a[None, :]
+    dt = KDE_F64 if a.dtype == np.float64 else KDE_F32
+    if a.dtype not in (np.float32, np.float64):
+        raise TypeError("samples must be float32 or float64")
+    wp, wn = _ws(ws)
+    g = np.zeros(grid.n_h)
+    res = kde_result()
+    _check(lib().kde_lscv_host(ctypes.c_void_p(a.ctypes.data), dt, a.shape[1], a.shape[0],
+                               ctypes.byref(grid), ctypes.byref(opts) if opts else None, wp, wn,
+                               _stream_handle(stream), _dp(g), ctypes.byref(res)))
+    return res.as_dict(), g
+
+
+def kde_lscv_tile_sums(x, h, tile_begin: int, tile_end: int, opts: kde_opts | None = None,
+                       ws=None, stream=None):
+    ptr, dt, n, d = _samples(x)
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64).ravel())
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, d, hh.size, opts), x.device)
+    wp, wn = _ws(ws)
+    s1, s2 = np.zeros(hh.size), np.zeros(hh.size)
+    _check(lib().kde_lscv_tile_sums(ptr, dt, n, d, _dp(hh), hh.size, int(tile_begin), int(tile_end),
+                                    ctypes.byref(opts) if opts else None, wp, wn,
+                                    _stream_handle(stream), _dp(s1), _dp(s2)))
+    return s1, s2
+
+
+def kde_plugin(x, opts: kde_opts | None = None, ws=None, stream=None) -> dict:
+    ptr, dt, n, d = _samples(x)
+    if d != 1:
+        raise ValueError("PLUGIN is univariate")
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, 1, 0, opts), x.device)
+    wp, wn = _ws(ws)
+    res = kde_result()
+    _check(lib().kde_plugin(ptr, dt, n, ctypes.byref(opts) if opts else None, wp, wn,
+                            _stream_handle(stream), ctypes.byref(res)))
+    return res.as_dict()
+
+
+def kde_plugin_async(x, opts: kde_opts | None, ws, stream=None):
+    ptr, dt, n, d = _samples(x)
+    wp, wn = _ws(ws)
+    _check(lib().kde_plugin_async(ptr, dt, n, ctypes.byref(opts) if opts else None, wp, wn,
+                                  _stream_handle(stream)))
+
+
+def kde_plugin_host(x_host: np.ndarray, opts: kde_opts | None, ws, stream=None) -> dict:
+    a = np.ascontiguousarray(x_host).ravel()
+    if a.dtype not in (np.float32, np.float64):
+        raise TypeError("samples must be float32 or float64")
+    dt = KDE_F64 if a.dtype == np.float64 else KDE_F32
+    wp, wn = _ws(ws)
+    res = kde_result()
+    _check(lib().kde_plugin_host(ctypes.c_void_p(a.ctypes.data), dt, a.size,
+                                 ctypes.byref(opts) if opts else None, wp, wn,
+                                 _stream_handle(stream), ctypes.byref(res)))
+    return res.as_dict()
+
+
+def kde_set_kernel_events(lscv_begin=None, lscv_end=None, psi_begin=None, psi_end=None):
+    """torch.cuda.Event objects (or None) recorded around the pair kernels."""
+    def h(e):
+        return ctypes.c_void_p(e.cuda_event) if e is not None else None
+    _check(lib().kde_set_kernel_events(h(lscv_begin), h(lscv_end), h(psi_begin), h(psi_end)))
+
+
+def kde_psi_tile_edge(n: int, opts: kde_opts | None = None) -> int:
+    t = ctypes.c_int(0)
+    _check(lib().kde_psi_tile_edge(int(n), ctypes.byref(opts) if opts else None, ctypes.byref(t)))
+    return t.value
+
+
+def kde_psi_tile_sums(x, r: int, g: float, tile_begin: int, tile_end: int,
+                      opts: kde_opts | None = None, ws=None, stream=None) -> float:
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, 1, 0, opts), x.device)
+    wp, wn = _ws(ws)
+    out = np.zeros(1)
+    _check(lib().kde_psi_tile_sums(ptr, dt, n, int(r), float(g), int(tile_begin), int(tile_end),
+                                   ctypes.byref(opts) if opts else None, wp, wn,
+                                   _stream_handle(stream), _dp(out)))
+    return float(out[0])
+
+
+def kde_probe_alu(ws=None, stream=None) -> dict:
+    if ws is None:
+        ws = workspace(1 << 20)
+    wp, wn = _ws(ws)
+    m, f, f2, mhz = (np.zeros(1) for _ in range(4))
+    sms = ctypes.c_int(0)
+    _check(lib().kde_probe_alu(wp, wn, _stream_handle(stream), _dp(m), _dp(f), _dp(f2),
+                               ctypes.byref(sms), _dp(mhz)))
+    return {"mufu_ex2_per_clk_sm": float(m[0]), "ffma_lanes_per_clk_sm": float(f[0]),
+            "ffma2_lanes_per_clk_sm": float(f2[0]), "sm_count": sms.value, "sm_mhz": float(mhz[0])}
+
+
+def read_ws_result(ws, n_h: int = 0):
+    """Copy the result (and g[]) left in a workspace by an _async call."""
+    import torch
+    roff, goff = kde_ws_result_offset()
+    raw = ws[roff:roff + ctypes.sizeof(kde_result)].cpu().numpy().tobytes()
+    res = kde_result.from_buffer_copy(raw).as_dict()
+    g = None
+    if n_h:
+        g = ws[goff:goff + 8 * n_h].cpu().view(torch.float64).numpy().copy()
+    return res, g

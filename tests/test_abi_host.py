@@ -1,0 +1,163 @@
+"""C ABI and host logic of libgbkde (CPU only: no kernel is launched)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._helpers import ROOT, built_lib
+
+
+@pytest.fixture(scope="module")
+def kde():
+    return built_lib()
+
+
+def _declared_functions():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(kde_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function(kde):
+    names = _declared_functions()
+    assert len(names) >= 15
+    L = kde.lib()
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    # the Python binding covers the same names
+    assert set(names) <= set(kde.SIGNATURES), set(names) - set(kde.SIGNATURES)
+
+
+def test_version_and_status_strings(kde):
+    assert "sm_103a" in kde.kde_version()
+    L = kde.lib()
+    for s in range(0, 11):
+        assert L.kde_status_string(s)
+
+
+def test_tile_map_exhaustive_against_column_enumeration(kde):
+    # Column l holds l+1 tiles (Appendix A): enumerate columns and rows and
+    # compare with the library's map for every tile number below 200k.
+    L = kde.lib()
+    lv, qv = ctypes.c_int64(), ctypes.c_int64()
+    bx = 0
+    for l in range(0, 632):
+        for q in range(0, l + 1):
+            assert L.kde_tile_coords(bx, ctypes.byref(lv), ctypes.byref(qv)) == 0
+            assert (lv.value, qv.value) == (l, q), bx
+            bx += 1
+
+
+def test_tile_map_large_indices(kde):
+    rng = np.random.default_rng(0)
+    for l in list(rng.integers(1, 3_000_000, size=3000)) + [2**20 - 1, 2**24, 2**24 + 1, 3_999_999]:
+        l = int(l)
+        first = l * (l + 1) // 2
+        for bx, q in ((first, 0), (first + l, l), (first + l // 2, l // 2)):
+            assert kde.kde_tile_coords(bx) == (l, q)
+
+
+def _walk_items(n, T, K):
+    """Replay the kernels' tile walk (items of K consecutive tiles, stepping
+    q -> q+1 and wrapping to the next column) and count pair visits."""
+    tiles = kde_mod.kde_tile_count(n, T)
+    seen = np.zeros((n, n), dtype=np.int32)
+    for row in range((tiles + K - 1) // K):
+        t0, t1 = row * K, min(row * K + K, tiles)
+        l, q = kde_mod.kde_tile_coords(t0)
+        for _t in range(t0, t1):
+            for i in range(q * T, q * T + T):
+                for j in range(l * T, l * T + T):
+                    if i < j < n:
+                        seen[i, j] += 1
+            q += 1
+            if q > l:
+                l, q = l + 1, 0
+    return seen
+
+
+kde_mod = None
+
+
+@pytest.mark.parametrize("n,T,K", [(97, 32, 1), (97, 32, 3), (130, 64, 2), (256, 32, 7), (33, 32, 5)])
+def test_tile_walk_covers_each_pair_once(kde, n, T, K):
+    global kde_mod
+    kde_mod = kde
+    seen = _walk_items(n, T, K)
+    iu = np.triu_indices(n, 1)
+    assert np.all(seen[iu] == 1)
+    assert seen.sum() == n * (n - 1) // 2
+
+
+def test_default_grid_matches_oracle(kde):
+    for n, d in ((1024, 1), (65536, 1), (16384, 3)):
+        assert np.allclose(kde.kde_default_grid(n, d, 128), oracle.grid_default(n, d, 128), rtol=1e-14)
+
+
+def test_workspace_size_monotone_and_bad_args(kde):
+    a = kde.kde_workspace_size(1000, 1, 64)
+    b = kde.kde_workspace_size(100000, 1, 64)
+    assert 0 < a < b
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_workspace_size(1, 1, 64)
+    assert e.value.status == kde.KDE_EINVAL
+    with pytest.raises(kde.KdeError):
+        kde.kde_workspace_size(100, 5, 64)
+    with pytest.raises(kde.KdeError):
+        kde.kde_workspace_size(100, 1, 64, kde.make_opts(tile=48))
+
+
+def test_entry_points_reject_bad_arguments_before_any_launch(kde):
+    L = kde.lib()
+    grid, keep = kde.make_grid(n_h=8)
+    res = kde.kde_result()
+    dummy = ctypes.c_void_p(256)  # never dereferenced: argument checks fail first
+    # NULL samples
+    assert L.kde_lscv(None, 0, 100, 1, ctypes.byref(grid), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    # d out of range
+    assert L.kde_lscv(dummy, 0, 100, 5, ctypes.byref(grid), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    # n < 2
+    assert L.kde_plugin(dummy, 0, 1, None, dummy, 1 << 20, None, ctypes.byref(res)) == kde.KDE_EINVAL
+    # misaligned workspace
+    assert L.kde_plugin(dummy, 0, 100, None, ctypes.c_void_p(260), 1 << 20, None,
+                        ctypes.byref(res)) == kde.KDE_EINVAL
+    # bad dtype
+    assert L.kde_plugin(dummy, 7, 100, None, dummy, 1 << 20, None, ctypes.byref(res)) == kde.KDE_EINVAL
+    # empty grid / too many bandwidths
+    g0 = kde.kde_grid(kde.KDE_GRID_DEFAULT_Z, 0, None, 0.0, 0.0)
+    assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g0), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    g2 = kde.kde_grid(kde.KDE_GRID_DEFAULT_Z, 2000, None, 0.0, 0.0)
+    assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g2), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    # a log grid with a non-positive bound
+    g3 = kde.kde_grid(kde.KDE_GRID_LOG, 8, None, -1.0, 2.0)
+    assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g3), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    buf = ctypes.create_string_buffer(256)
+    assert L.kde_last_error(buf, 256) == kde.KDE_EINVAL
+    assert b"grid" in buf.value
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle never imports the CUDA package and vice versa."""
+    osrc = open(os.path.join(ROOT, "oracle", "__init__.py")).read() + \
+        open(os.path.join(ROOT, "oracle", "kde_oracle.c")).read()
+    assert "paper_1505_01998_gb300" not in osrc.replace("in ``paper_1505_01998_gb300``", "")
+    pkg = os.path.join(ROOT, "paper_1505_01998_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".hpp", ".cpp", ".h")):
+                src = open(os.path.join(dp, f)).read()
+                assert "import oracle" not in src and "from oracle" not in src, f
+                assert "kde_oracle" not in src, f

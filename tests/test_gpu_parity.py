@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Inputs are the same FP32 values on both sides (the oracle widens them to
+FP64), except where an FP64 input path is under test.  Tolerances and error
+metrics: see tests/_helpers.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1505_01998_gb300 import datagen
+from tests._helpers import TOL, argmin_ok, built_lib, g_err, lscv_A, rel_err, s_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kde():
+    return built_lib()
+
+
+def dev(x, dtype="float32"):
+    import torch
+    a = np.ascontiguousarray(np.asarray(x))
+    if a.ndim == 1:
+        a = a[None, :]
+    return torch.from_numpy(a.astype(dtype)).cuda()
+
+
+def host64(x, dtype="float32"):
+    a = np.asarray(x)
+    if a.ndim == 1:
+        a = a[None, :]
+    return a.astype(dtype).astype(np.float64)
+
+
+def oracle_tile_sums_lscv(x64, h, T, tb, te, kde):
+    s1 = np.zeros(len(h))
+    s2 = np.zeros(len(h))
+    for t in range(tb, te):
+        l, q = kde.kde_tile_coords(t)
+        a, b, _ = oracle.lscv_sums(x64, h, block=(q * T, q * T + T, l * T, l * T + T))
+        s1 += a
+        s2 += b
+    return s1, s2
+
+
+def oracle_tile_sums_psi(x64, r, g, T, tb, te, kde):
+    s = 0.0
+    sa = 0.0
+    for t in range(tb, te):
+        l, q = kde.kde_tile_coords(t)
+        blk = (q * T, q * T + T, l * T, l * T + T)
+        s += oracle.psi_pair_sum(x64, r, g, block=blk)
+        sa += oracle.psi_abs_pair_sum(x64, r, g, block=blk)
+    return s, sa
+
+
+# ----------------------------------------------------------------- psi
+
+@pytest.mark.parametrize("n", [2, 3, 65, 1000, 20000])
+@pytest.mark.parametrize("r", [4, 6, 8])
+def test_psi_full_range_sums(kde, n, r):
+    x = datagen.mixture_1d(n, seed=10 + n)[0]
+    xd = dev(x)
+    x64 = host64(x)[0]
+    T = kde.kde_psi_tile_edge(n)
+    tiles = kde.kde_tile_count(n, T)
+    for g in (0.05, 0.4, 2.0):
+        got = kde.kde_psi_tile_sums(xd, r, g, 0, tiles)
+        ref = oracle.psi_pair_sum(x64, r, g)
+        mag = oracle.psi_abs_pair_sum(x64, r, g)
+        assert abs(got - ref) <= TOL * max(abs(ref), mag) + 1e-300, (g, got, ref, mag)
+
+
+@pytest.mark.parametrize("n", [300, 5000])
+def test_psi_tile_ranges_add_up(kde, n):
+    x = datagen.skewed_column(n, seed=3)[0]
+    xd = dev(x)
+    x64 = host64(x)[0]
+    T = kde.kde_psi_tile_edge(n)
+    tiles = kde.kde_tile_count(n, T)
+    cuts = [0, 1, tiles // 3, tiles - 1, tiles]
+    parts = [kde.kde_psi_tile_sums(xd, 6, 3.0, cuts[k], cuts[k + 1]) for k in range(4)]
+    full = kde.kde_psi_tile_sums(xd, 6, 3.0, 0, tiles)
+    assert sum(parts) == pytest.approx(full, rel=1e-11, abs=1e-9)
+    ref, mag = oracle_tile_sums_psi(x64, 6, 3.0, T, cuts[3], cuts[4], kde)
+    assert abs(parts[3] - ref) <= TOL * max(abs(ref), mag)
+
+
+# -------------------------------------------------------------- plug-in
+
+def _plugin_compare(res, ref, x64):
+    assert res["status"] == ref["status"] == 0
+    assert rel_err(res["sigma"], ref["sigma"]) < 1e-6
+    assert rel_err(res["g1"], ref["g1"]) < 1e-6
+    n = x64.size
+    for key, r, gk in (("psi6", 6, "g1"), ("psi4", 4, "g2")):
+        g = ref[gk]
+        mag = (2 * oracle.psi_abs_pair_sum(x64, r, g) + n * abs(oracle.gauss_deriv(r, 0.0))) / (
+            n * n * g ** (r + 1))
+        assert abs(res[key] - ref[key]) <= TOL * max(abs(ref[key]), mag), (key, res[key], ref[key])
+    assert rel_err(res["g2"], ref["g2"]) < TOL
+    assert rel_err(res["h"], ref["h"]) < TOL
+    assert res["h_data"] == res["h"]
+
+
+@pytest.mark.parametrize("n,dtype", [(1024, "float64"), (777, "float32"), (5000, "float32"),
+                                     (20000, "float32")])
+def test_plugin_matches_oracle(kde, n, dtype):
+    x = datagen.mixture_1d(n, seed=1)[0] if n == 1024 else datagen.skewed_column(n, seed=n)[0]
+    res = kde.kde_plugin(dev(x, dtype))
+    x64 = host64(x, dtype)[0]
+    _plugin_compare(res, oracle.plugin(x64), x64)
+
+
+def test_plugin_plain_precision_also_within_tolerance(kde):
+    x = datagen.mixture_1d(3000, seed=4)[0]
+    x64 = host64(x)[0]
+    res = kde.kde_plugin(dev(x), kde.make_opts(precision=kde.KDE_FP32_PLAIN))
+    _plugin_compare(res, oracle.plugin(x64), x64)
+
+
+# ------------------------------------------------------------------ LSCV
+
+def _lscv_check(kde, x, h, opts=None, dtype="float32"):
+    xd = dev(x, dtype)
+    x64 = host64(x, dtype)
+    d, n = x64.shape
+    res, g, hh = kde.kde_lscv(xd, _explicit(kde, h), opts)
+    assert np.array_equal(hh, np.asarray(h, dtype=np.float64))
+    ref = oracle.lscv_h(x64, h)
+    A = lscv_A(x64)
+    err = g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, A)
+    assert err.max() < TOL, (err.max(), int(err.argmax()))
+    # exponential sums over the whole triangle
+    T = opts.tile if (opts and opts.tile) else (32 if n <= 2048 else 128)
+    tiles = kde.kde_tile_count(n, T)
+    s1, s2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles, opts)
+    npairs = n * (n - 1) // 2
+    assert s_err(s1, ref["s_kk"], npairs).max() < TOL
+    assert s_err(s2, ref["s_k"], npairs).max() < TOL
+    assert argmin_ok(res["argmin"], ref["g"], TOL * np.max(np.abs(ref["g"])))
+    assert res["n_h"] == len(h) and res["d"] == d
+    assert res["h"] == h[res["argmin"]]
+    if d == 1:
+        assert rel_err(res["h_data"], h[res["argmin"]] * math.sqrt(np.var(x64, ddof=1))) < 1e-6
+    return res, g, ref
+
+
+_keep = []
+
+
+def _explicit(kde, h):
+    grid, arr = kde.make_grid(h=h)
+    _keep.append(arr)
+    return grid
+
+
+def test_lscv_n1024_mixture_64_point_grid(kde):
+    """The n = 1,024 FP64 mixture with a 64-point log grid over [0.01, 2]."""
+    x = datagen.mixture_1d(1024, seed=1)
+    h = oracle.grid_log(0.01, 2.0, 64)
+    _lscv_check(kde, x, h, dtype="float64")
+    _lscv_check(kde, x, h, dtype="float32")
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("n,n_h", [(700, 64), (2100, 128), (333, 12), (1500, 40), (2500, 256)])
+def test_lscv_dims_sizes_grids(kde, d, n, n_h):
+    x = datagen.correlated_mixture(n, d, seed=7 * d + n)
+    h = oracle.grid_default(n, d, n_h)
+    _lscv_check(kde, x, h)
+
+
+@pytest.mark.parametrize("opts", [dict(precision=1), dict(tile=128), dict(tile=32, bw_per_thread=16),
+                                  dict(bw_per_thread=8, tiles_per_item=3), dict(ctas_per_sm=1)])
+def test_lscv_option_paths(kde, opts):
+    x = datagen.correlated_mixture(1800, 2, seed=99)
+    h = oracle.grid_default(1800, 2, 96)
+    _lscv_check(kde, x, h, kde.make_opts(**opts))
+
+
+def test_lscv_deterministic_and_grid_independent(kde):
+    x = datagen.skewed_column(5000, seed=12)
+    xd = dev(x)
+    grid = _explicit(kde, oracle.grid_default(5000, 1, 128))
+    # item partials depend only on the tile partition (K), not on the grid size
+    r1, g1, _ = kde.kde_lscv(xd, grid, kde.make_opts(tiles_per_item=5))
+    r2, g2, _ = kde.kde_lscv(xd, grid, kde.make_opts(tiles_per_item=5))
+    r3, g3, _ = kde.kde_lscv(xd, grid, kde.make_opts(tiles_per_item=5, ctas_per_sm=1))
+    assert np.array_equal(g1, g2) and np.array_equal(g1, g3)
+    assert r1 == r2 == r3
+
+
+def test_lscv_tile_ranges_add_up(kde):
+    x = datagen.correlated_mixture(3000, 3, seed=5)
+    xd = dev(x)
+    h = oracle.grid_default(3000, 3, 64)
+    tiles = kde.kde_tile_count(3000, 128)
+    cuts = [0, 5, tiles // 2, tiles - 2, tiles]
+    s1 = np.zeros(64)
+    s2 = np.zeros(64)
+    for k in range(4):
+        a, b = kde.kde_lscv_tile_sums(xd, h, cuts[k], cuts[k + 1])
+        s1 += a
+        s2 += b
+    f1, f2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles)
+    assert np.allclose(s1, f1, rtol=1e-11) and np.allclose(s2, f2, rtol=1e-11)
+
+
+def test_lscv_host_and_async_paths_match(kde):
+    import torch
+    x = datagen.correlated_mixture(2500, 2, seed=8)
+    grid = _explicit(kde, oracle.grid_default(2500, 2, 128))
+    r1, g1, _ = kde.kde_lscv(dev(x), grid)
+    ws = kde.workspace(kde.kde_workspace_size(2500, 2, 128))
+    r2, g2 = kde.kde_lscv_host(np.ascontiguousarray(x, dtype=np.float32), grid, None, ws)
+    assert np.array_equal(g1, g2) and r1 == r2
+    kde.kde_lscv_async(dev(x), grid, None, ws)
+    torch.cuda.synchronize()
+    r3, g3 = kde.read_ws_result(ws, 128)
+    assert np.array_equal(g1, g3) and r3 == r1
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_two_and_three_samples(kde):
+    for x in (np.array([[0.3, 1.7]]), np.array([[0.0, 0.5, 2.0]])):
+        h = np.array([0.2, 0.7, 1.5])
+        _lscv_check(kde, x, h)
+        ref = oracle.plugin(host64(x)[0])
+        if ref["status"] == 0:
+            _plugin_compare(kde.kde_plugin(dev(x)), ref, host64(x)[0])
+        else:
+            with pytest.raises(kde.KdeError) as e:
+                kde.kde_plugin(dev(x))
+            assert e.value.status == kde.KDE_EDEGENERATE
+
+
+@pytest.mark.parametrize("n", [32, 33, 64, 2048, 2049])
+def test_tile_boundaries(kde, n):
+    x = datagen.mixture_1d(n, seed=n)
+    _lscv_check(kde, x, oracle.grid_default(n, 1, 16))
+
+
+def test_degenerate_inputs_reported(kde):
+    const = np.full((1, 100), 3.0)
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv(dev(const), _explicit(kde, [0.5, 1.0]))
+    assert e.value.status == kde.KDE_EDEGENERATE
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_plugin(dev(const))
+    assert e.value.status == kde.KDE_EDEGENERATE
+    t = np.linspace(0, 1, 50)
+    collinear = np.stack([t, 2 * t + 1])
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv(dev(collinear), _explicit(kde, [0.5, 1.0]))
+    assert e.value.status == kde.KDE_EDEGENERATE
+    bad = datagen.mixture_1d(100, seed=1)
+    bad[0, 7] = np.nan
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv(dev(bad), _explicit(kde, [0.5, 1.0]))
+    assert e.value.status == kde.KDE_EINVAL
+    # the library stays usable after device-reported errors
+    _lscv_check(kde, datagen.mixture_1d(200, seed=2), np.array([0.3, 0.6]))
+
+
+def test_workspace_too_small_is_reported(kde):
+    x = datagen.mixture_1d(5000, seed=3)
+    need = kde.kde_workspace_size(5000, 1, 64)
+    ws = kde.workspace(need - 1024)
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv(dev(x), _explicit(kde, oracle.grid_default(5000, 1, 64)), None, ws)
+    assert e.value.status == kde.KDE_ENOMEM
+
+
+# ------------------------------------------- full-size workloads (sampled)
+
+def test_full_size_skewed_column_sampled_tiles(kde):
+    """n = 65,536 skewed column, 256-point grid over Z(h0), the launch
+    configuration of the benchmark: sampled tiles against the oracle, tile-range
+    additivity, plug-in chain consistency."""
+    n = 65536
+    x = datagen.skewed_column(n, seed=2)
+    xd = dev(x)
+    x64 = host64(x)
+    h = oracle.grid_default(n, 1, 256)
+    res, g, _ = kde.kde_lscv(xd, _explicit(kde, h))
+    assert res["status"] == 0 and np.all(np.isfinite(g))
+    T = 128
+    tiles = kde.kde_tile_count(n, T)
+    for tb, te in ((0, 3), (tiles // 2, tiles // 2 + 2), (tiles - 3, tiles)):
+        s1, s2 = kde.kde_lscv_tile_sums(xd, h, tb, te)
+        r1, r2 = oracle_tile_sums_lscv(x64, h, T, tb, te, kde)
+        assert s_err(s1, r1, (te - tb) * T * T).max() < TOL
+        assert s_err(s2, r2, (te - tb) * T * T).max() < TOL
+    # plug-in: sigma/g1 against the oracle, psi tile samples at the device's pilots
+    p = kde.kde_plugin(xd)
+    m, S = oracle.mean_cov(x64)
+    sig = math.sqrt(S[0, 0])
+    assert rel_err(p["sigma"], sig) < 1e-6
+    assert rel_err(p["g1"], oracle.plugin_g1(oracle.psi8_ns(sig), n)) < 1e-6
+    Tp = kde.kde_psi_tile_edge(n)
+    ptiles = kde.kde_tile_count(n, Tp)
+    for r, gp in ((6, p["g1"]), (4, p["g2"])):
+        for tb, te in ((0, 2), (ptiles - 2, ptiles)):
+            got = kde.kde_psi_tile_sums(xd, r, gp, tb, te)
+            ref, mag = oracle_tile_sums_psi(x64[0], r, gp, Tp, tb, te, kde)
+            assert abs(got - ref) <= TOL * max(abs(ref), mag)
+        full = kde.kde_psi_tile_sums(xd, r, gp, 0, ptiles)
+        psi = (2 * full + n * oracle.gauss_deriv(r, 0.0)) / (n * n * gp ** (r + 1))
+        assert psi == pytest.approx(p["psi6" if r == 6 else "psi4"], rel=1e-12)
+    assert rel_err(p["g2"], oracle.plugin_g2(p["psi6"], n)) < 1e-12
+    assert rel_err(p["h"], oracle.plugin_h(p["psi4"], n)) < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_full_size_correlated_mixture(kde, d):
+    """n = 16,384, d = 2..4, H = h^2 S on a 128-point grid: the oracle's g at
+    the device argmin and its neighbours, plus sampled tiles."""
+    n = 16384
+    x = datagen.correlated_mixture(n, d, seed=3 + d)
+    xd = dev(x)
+    x64 = host64(x)
+    h = oracle.grid_default(n, d, 128)
+    res, g, _ = kde.kde_lscv(xd, _explicit(kde, h))
+    k = res["argmin"]
+    ks = [kk for kk in (k - 1, k, k + 1) if 0 <= kk < len(h)]
+    ref = oracle.lscv_h(x64, h[ks])
+    A = lscv_A(x64)
+    err = g_err(g[ks], ref["g"], ref["s_kk"], ref["s_k"], h[ks], n, d, A)
+    assert err.max() < TOL
+    # the device minimum is a local minimum of the oracle's objective (or a tie)
+    kk = ks.index(k)
+    assert np.all(ref["g"][kk] <= ref["g"] + TOL * np.abs(ref["g"]).max())
+    T = 128
+    tiles = kde.kde_tile_count(n, T)
+    for tb, te in ((0, 2), (tiles - 2, tiles)):
+        s1, s2 = kde.kde_lscv_tile_sums(xd, h, tb, te)
+        r1, r2 = oracle_tile_sums_lscv(x64, h, T, tb, te, kde)
+        assert s_err(s1, r1, (te - tb) * T * T).max() < TOL
+        assert s_err(s2, r2, (te - tb) * T * T).max() < TOL
