@@ -60,6 +60,27 @@ int check_opts(const kde_opts* o) {
   return KDE_OK;
 }
 
+// Host check of the LSCV kernel's warp roles for every group size cg that
+// the geometry can produce: each chunk is walked by exactly S warps whose
+// column slices tile [0, T) in 16-byte steps, and every shared-memory slot the
+// item-end combine reads (slice * cg + chunk) is a real warp.
+int check_warp_roles(int T) {
+  for (int cg = 1; cg <= kWarps; ++cg) {
+    std::vector<int> cover(cg, 0);
+    for (int w = 0; w < kWarps; ++w) {
+      const WarpRole r = warp_role(w, cg);
+      if (r.S < 1 || r.S * cg > kWarps || T % r.S || (T / r.S) % 4) return KDE_EINTERNAL;
+      if (r.active) {
+        if (r.slice * cg + r.chunk != w) return KDE_EINTERNAL;
+        cover[r.chunk] += 1;
+      }
+    }
+    for (int c = 0; c < cg; ++c)
+      if (cover[c] != warp_role(0, cg).S) return KDE_EINTERNAL;
+  }
+  return KDE_OK;
+}
+
 // Geometry of one selection.  Deterministic in (n, d, n_h, opts, SM count).
 int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g) {
   memset(g, 0, sizeof(*g));
@@ -78,6 +99,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->n_h_pad = (nh + g->B - 1) / g->B * g->B;
   g->n_chunks = g->n_h_pad / g->B;
   g->G = (g->n_chunks + kWarps - 1) / kWarps;
+  if (check_warp_roles(g->T) != KDE_OK) return fail(KDE_EINTERNAL, "warp roles inconsistent for T = %d", g->T);
   g->tiles = tri_tiles(n, g->T);
   if (o && o->tiles_per_item) {
     g->K = o->tiles_per_item;
@@ -302,7 +324,7 @@ int kde_workspace_size(int64_t n, int d, int n_h, const kde_opts* opts, size_t* 
   int rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, d, n_h, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, d, n_h, opts, device_sms(), &g); if (grc) return grc; }
   *bytes = g.total;
   return KDE_OK;
 }
@@ -318,7 +340,7 @@ int kde_ws_result_offset(size_t* result_offset, size_t* g_offset) {
 int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile) {
   if (!tile || n < 2) return fail(KDE_EINVAL, "kde_psi_tile_edge: bad arguments");
   Geometry g;
-  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, 1, 0, opts, device_sms(), &g); if (grc) return grc; }
   *tile = g.Tp;
   return KDE_OK;
 }
@@ -331,7 +353,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   int rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, d, (int)h.size(), opts, device_sms(), &g);
+  { const int grc = make_geometry(n, d, (int)h.size(), opts, device_sms(), &g); if (grc) return grc; }
   if (ws_bytes < g.total)
     return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -412,7 +434,7 @@ int kde_lscv_host(const void* x_host, int dtype, int64_t n, int d, const kde_gri
   rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, d, (int)h.size(), opts, device_sms(), &g);
+  { const int grc = make_geometry(n, d, (int)h.size(), opts, device_sms(), &g); if (grc) return grc; }
   if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   cudaStream_t st = (cudaStream_t)stream;
   void* xd = static_cast<unsigned char*>(ws) + g.off_x;
@@ -437,7 +459,7 @@ int kde_lscv_tile_sums(const void* x_dev, int dtype, int64_t n, int d, const dou
   rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, d, n_h, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, d, n_h, opts, device_sms(), &g); if (grc) return grc; }
   if (tile_begin < 0 || tile_end < tile_begin || tile_end > g.tiles)
     return fail(KDE_EINVAL, "tile range [%lld, %lld) outside [0, %lld)", (long long)tile_begin,
                 (long long)tile_end, (long long)g.tiles);
@@ -472,7 +494,7 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   int rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, 1, 0, opts, device_sms(), &g); if (grc) return grc; }
   if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   unsigned char* w = static_cast<unsigned char*>(ws);
   DsDev init = make_desc(g, x_dev, dtype, KDE_METHOD_PLUGIN, w);
@@ -521,7 +543,7 @@ int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* op
   rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, 1, 0, opts, device_sms(), &g); if (grc) return grc; }
   if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   cudaStream_t st = (cudaStream_t)stream;
   void* xd = static_cast<unsigned char*>(ws) + g.off_x;
@@ -549,7 +571,7 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpi
   rc = check_opts(opts);
   if (rc) return rc;
   Geometry g;
-  make_geometry(n, 1, 0, opts, device_sms(), &g);
+  { const int grc = make_geometry(n, 1, 0, opts, device_sms(), &g); if (grc) return grc; }
   if (ws_bytes < g.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   if (tile_begin < 0 || tile_end < tile_begin || tile_end > g.ptiles)
     return fail(KDE_EINVAL, "tile range outside [0, %lld)", (long long)g.ptiles);
@@ -588,11 +610,11 @@ int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu, double*
                   double* ffma2, int* sm_count, double* sm_mhz) {
   const int sms = device_sms();
   if (sms <= 0) return fail(KDE_ECUDA, "no CUDA device");
-  const int per_sm = 4, grid = sms * per_sm;
+  const int grid = sms;  // one 1024-thread CTA per SM (the probe's shared memory forces it)
   if (!ws || ws_bytes < sizeof(double) * 2 * grid) return fail(KDE_ENOMEM, "probe needs %zu bytes", sizeof(double) * 2 * grid);
   cudaStream_t st = (cudaStream_t)stream;
   double* dout = static_cast<double*>(ws);
-  const int iters[3] = {1500, 6000, 6000};
+  const int iters[3] = {1000, 4000, 4000};
   const double lanes_per_op[3] = {1.0, 1.0, 2.0};
   double rate[3] = {0, 0, 0}, mhz = 0;
   cudaEvent_t e0, e1;
@@ -611,7 +633,7 @@ int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu, double*
     std::vector<double> s = cyc;
     std::sort(s.begin(), s.end());
     const double med = s[grid / 2];
-    const double ops_per_sm = (double)per_sm * 256.0 * iters[mode] * 32.0 * lanes_per_op[mode];
+    const double ops_per_sm = 1024.0 * iters[mode] * 32.0 * lanes_per_op[mode];
     rate[mode] = ops_per_sm / med;
     if (mode == 0) mhz = s[grid - 1] / (ms * 1e3);
   }

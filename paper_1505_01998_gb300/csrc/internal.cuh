@@ -92,6 +92,23 @@ __host__ __device__ inline void tile_coords(int64_t bx, int64_t& l, int64_t& q) 
   q = bx - L * (L + 1) / 2;
 }
 
+// Role of warp `warp` of an LSCV CTA when its item's bandwidth group has
+// cg (1..8) chunks of B bandwidths: the chunk it evaluates and the slice of
+// the tile's columns it walks.  S = kWarps / cg slices per chunk, so
+// S * cg <= kWarps; warps with slice >= S idle.
+struct WarpRole {
+  int chunk, slice, S;
+  bool active;
+};
+__host__ __device__ inline WarpRole warp_role(int warp, int cg) {
+  WarpRole r;
+  r.S = kWarps / cg;
+  r.chunk = warp % cg;
+  r.slice = warp / cg;
+  r.active = r.slice < r.S;
+  return r;
+}
+
 __host__ __device__ inline int64_t tri_tiles(int64_t n, int tile) {
   int64_t nt = (n + tile - 1) / tile;
   return nt * (nt + 1) / 2;

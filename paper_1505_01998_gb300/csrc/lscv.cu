@@ -96,9 +96,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     const int64_t tb = ds->lscv_t0 + row * ds->lscv_K;
     const int64_t te = min(tb + (int64_t)ds->lscv_K, ds->lscv_tiles);
     const int cg = min(kWarps, ds->n_chunks - hg * kWarps);
-    const int S = cg >= 8 ? 1 : cg >= 4 ? 2 : cg >= 2 ? 4 : 8;
-    const int my_chunk = warp % cg, my_slice = warp / cg;
-    const bool active = my_slice < S;
+    const WarpRole role = warp_role(warp, cg);
+    const int S = role.S, my_chunk = role.chunk, my_slice = role.slice;
+    const bool active = role.active;
     const int cols = T / S;
     const int j_lo = active ? my_slice * cols : 0;
     const int j_hi = active ? j_lo + cols : 0;

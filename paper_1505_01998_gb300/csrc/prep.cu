@@ -225,11 +225,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa) {
   }
 }
 
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeSmem = 160 * 1024;  // > half an SM's shared memory: one CTA per SM
+
 // ALU probe: `iters` rounds of 8 independent dependency chains per thread.
 // mode 0: MUFU ex2; mode 1: scalar FFMA; mode 2: packed FP32x2 FMA.
 // Each CTA records its clock64() span; out[blockIdx.x] = cycles.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_probe(double* out, int iters, float seed) {
+__global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters, float seed) {
   float a[8];
   float2 p[8];
 #pragma unroll
@@ -283,10 +286,18 @@ cudaError_t launch_prep(DsDev* ds, int n_ds, int dtype, cudaStream_t st) {
 }
 
 cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_probe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_probe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_probe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
+    attr = true;
+  }
   switch (mode) {
-    case 0: k_probe<0><<<grid, 256, 0, st>>>(out, iters, 0.5f); break;
-    case 1: k_probe<1><<<grid, 256, 0, st>>>(out, iters, 0.5f); break;
-    default: k_probe<2><<<grid, 256, 0, st>>>(out, iters, 0.5f); break;
+    case 0: k_probe<0><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
+    case 1: k_probe<1><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
+    default: k_probe<2><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
   }
   return cudaGetLastError();
 }

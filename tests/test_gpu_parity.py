@@ -85,7 +85,11 @@ def test_psi_tile_ranges_add_up(kde, n):
     cuts = [0, 1, tiles // 3, tiles - 1, tiles]
     parts = [kde.kde_psi_tile_sums(xd, 6, 3.0, cuts[k], cuts[k + 1]) for k in range(4)]
     full = kde.kde_psi_tile_sums(xd, 6, 3.0, 0, tiles)
-    assert sum(parts) == pytest.approx(full, rel=1e-11, abs=1e-9)
+    # different tile ranges group tiles into different items (different FP32
+    # runs), so the split agrees with the whole to FP32 rounding of the terms
+    mag_all = oracle.psi_abs_pair_sum(x64, 6, 3.0)
+    assert abs(sum(parts) - full) <= 1e-6 * mag_all
+    assert abs(full - oracle.psi_pair_sum(x64, 6, 3.0)) <= TOL * mag_all
     ref, mag = oracle_tile_sums_psi(x64, 6, 3.0, T, cuts[3], cuts[4], kde)
     assert abs(parts[3] - ref) <= TOL * max(abs(ref), mag)
 
@@ -208,7 +212,8 @@ def test_lscv_tile_ranges_add_up(kde):
         s1 += a
         s2 += b
     f1, f2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles)
-    assert np.allclose(s1, f1, rtol=1e-11) and np.allclose(s2, f2, rtol=1e-11)
+    # positive terms; regrouped FP32 runs agree to FP32 rounding
+    assert np.allclose(s1, f1, rtol=1e-6) and np.allclose(s2, f2, rtol=1e-6)
 
 
 def test_lscv_host_and_async_paths_match(kde):
