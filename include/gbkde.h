@@ -119,6 +119,7 @@ typedef struct kde_result {
   double g2;      /* PLUGIN: Eq. PLUGIN-g2                                      */
   double psi4;    /* PLUGIN: Eq. PLUGIN-Psi4Estimate (reading R1)               */
   double logdet_S;/* log det S                                                  */
+  double h_plugin;/* PLUGIN: h (data units), also when LSCV ran on the same data  */
 } kde_result;
 
 /* ------------------------------------------------------------- utilities */
@@ -230,6 +231,73 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double g,
 
 /* Tile edge used by the psi kernels for n samples (for kde_psi_tile_sums). */
 int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile);
+
+/* ------------------------------------------------------------- LSCV_H */
+
+/* Workspace bytes for kde_lscv_H with m bandwidth matrices. */
+int kde_lscv_H_workspace_size(int64_t n, int d, int m, const kde_opts* opts, size_t* bytes);
+
+/* The LSCV_H objective g(H) (Sec. 4.4.3, Eqs. LSCV_MULTI-gh, LSCV_MULTI-Tx,
+ * LSCV_MULTI-Kx, LSCV_MULTI-KKx, LSCV_MULTI-rk) for m symmetric positive-
+ * definite bandwidth matrices H_host[m][d][d] (row-major, host), in one
+ * batched pass over the pairs: each H whitens the samples by its Cholesky
+ * factor, so (X_i - X_j)^T H^-1 (X_i - X_j) is a squared distance.  g_host
+ * receives m values.  Errors: KDE_EINVAL (m outside [1, KDE_MAX_NH], H not
+ * finite or not symmetric), KDE_EDEGENERATE (an H not positive definite),
+ * KDE_ENOMEM, KDE_ECUDA.  Synchronises the stream. */
+int kde_lscv_H(const void* x_dev, int dtype, int64_t n, int d, const double* H_host, int m,
+               const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host);
+
+/* -------------------------------------------------------------- batches */
+
+/* One selection request of a batch (device samples) or of the server (host
+ * samples).  methods: KDE_METHOD_LSCV and/or KDE_METHOD_PLUGIN (PLUGIN needs
+ * d = 1); grid: the LSCV grid (ignored without KDE_METHOD_LSCV). */
+typedef struct kde_request {
+  const void* x;
+  int dtype;
+  int d;
+  int64_t n;
+  int methods;
+  kde_grid grid;
+} kde_request;
+
+typedef struct kde_batch_plan kde_batch_plan;
+
+/* Plans a batch: per-dataset geometry (the same as a single call would use,
+ * so results are bitwise identical alone and batched), kernel-variant groups
+ * and the workspace layout; *ws_bytes receives the workspace size.  The
+ * request array may be freed afterwards; the sample buffers must stay valid
+ * for every run. */
+int kde_batch_plan_create(const kde_request* reqs, int n_req, const kde_opts* opts,
+                          kde_batch_plan** plan, size_t* ws_bytes);
+
+/* Queues one batched selection of all requests on `stream`: one upload of
+ * descriptors, the prologue for every dataset, one persistent launch per
+ * kernel variant and phase (LSCV and psi_6 / psi_4 of the PLUGIN method), the
+ * fixed-order reductions, the scalar chains and one download of the results.
+ * The sequence is captured into a CUDA graph on the first run (and again when
+ * the workspace changes) and replayed afterwards. */
+int kde_batch_run_async(kde_batch_plan* plan, void* ws, size_t ws_bytes, void* stream);
+
+/* kde_batch_run_async + stream synchronisation + kde_batch_results. */
+int kde_batch_run(kde_batch_plan* plan, void* ws, size_t ws_bytes, void* stream, kde_result* outs);
+
+/* Results of the last completed run (outs has n_req entries). */
+int kde_batch_results(const kde_batch_plan* plan, kde_result* outs);
+
+/* The LSCV objective g[n_h] of request `req` after a completed run. */
+int kde_batch_g(const kde_batch_plan* plan, const void* ws, int req, double* g_host);
+
+int kde_batch_plan_destroy(kde_batch_plan* plan);
+
+/* Workspace bytes of a batch (same layout as kde_batch_plan_create). */
+int kde_batch_workspace_size(const kde_request* reqs, int n_req, const kde_opts* opts,
+                             size_t* bytes);
+
+/* One-shot batch: plan, run without a graph, synchronise, results, free. */
+int kde_select_batch(const kde_request* reqs, int n_req, const kde_opts* opts, void* ws,
+                     size_t ws_bytes, void* stream, kde_result* outs);
 
 /* ------------------------------------------------------- measurement aids */
 

@@ -369,14 +369,14 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, g.items, 0, 0};
   CK(launch_setup(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
-  CK(launch_prep(ds, 1, dtype, st));
-  Phase ph{ds, off, 1, 0, g.items};
+  CK(launch_prep(ds, 1, nullptr, st));
+  Phase ph{ds, off, nullptr, 1, 0, g.items};
   const int grid = (int)std::min<int64_t>(g.items, g.ctas);
   CK(mark(0, st));
   CK(launch_lscv(ph, d, g.B, g.R, g.kahan, std::max(grid, 1), st));
   CK(mark(1, st));
-  CK(launch_lscv_reduce(ds, 1, g.n_h_pad, st));
-  CK(launch_lscv_finish(ds, 1, st));
+  CK(launch_lscv_reduce(ds, 1, nullptr, g.n_h_pad, st));
+  CK(launch_lscv_finish(ds, 1, nullptr, st));
   if (gout) *gout = g;
   return KDE_OK;
 }
@@ -503,15 +503,15 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, g.prows};
   CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, dtype, st));
-  Phase ph{ds, off + 2, 1, 0, g.prows};
+  CK(launch_prep(ds, 1, nullptr, st));
+  Phase ph{ds, off + 2, nullptr, 1, 0, g.prows};
   const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));
   CK(mark(2, st));
   CK(launch_psi(ph, 6, g.Rp, g.kahan, psi_coef(6), grid, st));
   CK(mark(3, st));
-  CK(launch_psi_finish(ds, 1, 6, 6, st));
+  CK(launch_psi_finish(ds, 1, nullptr, 6, 6, st));
   CK(launch_psi(ph, 4, g.Rp, g.kahan, psi_coef(4), grid, st));
-  CK(launch_psi_finish(ds, 1, 4, 4, st));
+  CK(launch_psi_finish(ds, 1, nullptr, 4, 4, st));
   if (gout) *gout = g;
   return KDE_OK;
 }
@@ -591,11 +591,11 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpi
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, init.psi_rows};
   CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, dtype, st));
-  Phase ph{ds, off + 2, 1, 0, init.psi_rows};
+  CK(launch_prep(ds, 1, nullptr, st));
+  Phase ph{ds, off + 2, nullptr, 1, 0, init.psi_rows};
   const int grid = std::max(1, (int)std::min<int64_t>(init.psi_rows, g.ctas));
   CK(launch_psi(ph, r, g.Rp, g.kahan, psi_coef(r), grid, st));
-  CK(launch_psi_finish(ds, 1, 0, r, st));
+  CK(launch_psi_finish(ds, 1, nullptr, 0, r, st));
   kde_result res;
   CK(cudaMemcpyAsync(&res, w + g.off_ds + offsetof(DsDev, res), sizeof(res), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));

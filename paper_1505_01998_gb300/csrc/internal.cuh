@@ -67,6 +67,7 @@ struct DsDev {
 struct Phase {
   DsDev* ds;
   const int64_t* off;
+  const int64_t* base;  // optional: first local item of each dataset in this launch
   int32_t n_ds;
   int32_t pad;
   int64_t total;
@@ -158,16 +159,19 @@ __device__ __forceinline__ int find_ds(const int64_t* off, int n, int64_t it) {
 
 // ------------------------------------------------------------- launchers
 // (defined in the .cu files; return a cudaError_t)
-cudaError_t launch_prep(DsDev* ds, int n_ds, int dtype, cudaStream_t st);
+// ids: optional list of dataset indices into ds (one CTA each); NULL = ds[0..n_ds)
+cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, cudaStream_t st);
 cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
                         cudaStream_t st);
 size_t lscv_smem_bytes(int d, int B, int R, bool kahan);
-cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, int n_h_pad_max, cudaStream_t st);
-cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, cudaStream_t st);
+// sets the kernel's shared-memory attribute without launching (call before a graph capture)
+cudaError_t prepare_lscv(int d, int B, int R, bool kahan);
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, cudaStream_t st);
+cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, const int* ids, cudaStream_t st);
 cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef& cf, int grid,
                        cudaStream_t st);
 // stage: 6 -> reduce psi_6, set g2; 4 -> reduce psi_4, set h; 0 -> raw sum only (into res.g_min)
-cudaError_t launch_psi_finish(DsDev* ds, int n_ds, int stage, int r, cudaStream_t st);
+cudaError_t launch_psi_finish(DsDev* ds, int n_ds, const int* ids, int stage, int r, cudaStream_t st);
 cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
                          int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st);
 cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st);

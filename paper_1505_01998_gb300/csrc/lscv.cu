@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     const int di = find_ds(ph.off, ph.n_ds, it);
     const DsDev* ds = ph.ds + di;
     if (ds->res.status != KDE_OK) continue;
-    const int64_t li = it - ph.off[di];
+    const int64_t li = it - ph.off[di] + (ph.base ? ph.base[di] : 0);
     const int G = ds->n_groups;
     const int hg = (int)(li % G);
     const int64_t row = li / G;
@@ -206,8 +206,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
 
 // Sum of the per-item partial rows, one 32-column strip per CTA: warp w adds
 // rows w, w+8, ... ; the 8 warp sums are added in order.
-__global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa) {
-  DsDev* ds = dsa + blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   __shared__ double s[kWarps][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
@@ -229,8 +229,8 @@ __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa) {
 }
 
 // g(h) on the grid and its first-index argmin (Eqs. LSCV-gh, LSCV-finalH).
-__global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa) {
-  DsDev* ds = dsa + blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int* ids) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
   const int d = ds->d, n_h = ds->n_h;
   const double n = (double)ds->n;
@@ -270,6 +270,7 @@ cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
   k_lscv<D, B, R, KAHAN><<<grid, kThreads, smem, st>>>(ph);
   return cudaGetLastError();
 }
@@ -304,9 +305,14 @@ size_t lscv_smem_bytes(int d, int B, int R, bool kahan) {
   return (size_t)32 * R * dp * 4 + (size_t)kWarps * B * 16 + (kahan ? (size_t)kWarps * B * 32 * 16 : 0);
 }
 
+cudaError_t prepare_lscv(int d, int B, int R, bool kahan) {
+  Phase ph{nullptr, nullptr, nullptr, 0, 0, 0};
+  return launch_lscv(ph, d, B, R, kahan, 0, nullptr);
+}
+
 cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
                         cudaStream_t st) {
-  if (ph.total <= 0) return cudaSuccess;
+  if (ph.total <= 0 && grid > 0) return cudaSuccess;
   switch (d) {
     case 1: return launch_b<1>(ph, B, R, kahan, grid, st);
     case 2: return launch_b<2>(ph, B, R, kahan, grid, st);
@@ -316,14 +322,16 @@ cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int gr
   }
 }
 
-cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, int n_h_pad_max, cudaStream_t st) {
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, cudaStream_t st) {
+  if (n_ds <= 0) return cudaSuccess;
   dim3 grid(n_ds, (2 * n_h_pad_max + 31) / 32);
-  k_lscv_reduce<<<grid, kThreads, 0, st>>>(ds);
+  k_lscv_reduce<<<grid, kThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, cudaStream_t st) {
-  k_lscv_finish<<<n_ds, kThreads, 0, st>>>(ds);
+cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, const int* ids, cudaStream_t st) {
+  if (n_ds <= 0) return cudaSuccess;
+  k_lscv_finish<<<n_ds, kThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }
 

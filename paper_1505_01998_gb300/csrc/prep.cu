@@ -74,8 +74,7 @@ __device__ void block_sum(double* v, int cnt, double (*scratch)[16], double* out
 // the PLUGIN method, psi_8^NS (Eq. PLUGIN-Psi8Estimate) and g1
 // (Eq. PLUGIN-g1).  Pass 3: y = M (x - mean) and x - mean in FP32.
 template <typename TIN>
-__global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa) {
-  DsDev* ds = dsa + blockIdx.x;
+__device__ __forceinline__ void prep_body(DsDev* ds) {
   __shared__ double scratch[kPrepThreads / 32][16];
   __shared__ double sv[16];
   __shared__ float sM[KDE_MAX_D * KDE_MAX_D];
@@ -147,7 +146,11 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa) {
     for (int j = 0; j < d && pd; ++j) {
       double s = S[j][j];
       for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
-      if (!(s > 1e-300) || !(s > 1e-13 * S[j][j])) {
+      // Numerically singular for FP32 pair arithmetic: a Schur complement below
+      // 1e-6 of the variance (the whitened coordinate would be rounding noise),
+      // or a spread below 1e-5 of the magnitude of the values.
+      const double mag = ds->given_H ? 0.0 : 1e-5 * fabs(sMean[j]);
+      if (!(s > 1e-300) || !(s > 1e-6 * S[j][j]) || !(S[j][j] > mag * mag)) {
         pd = false;
         break;
       }
@@ -225,6 +228,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa) {
   }
 }
 
+// One CTA per dataset; `ids` (optional) selects the datasets of a table.
+__global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa, const int* ids) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
+  if (ds->dtype == KDE_F64)
+    prep_body<double>(ds);
+  else
+    prep_body<float>(ds);
+}
+
 constexpr int kProbeThreads = 1024;
 constexpr int kProbeSmem = 160 * 1024;  // > half an SM's shared memory: one CTA per SM
 
@@ -277,11 +289,9 @@ cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep(DsDev* ds, int n_ds, int dtype, cudaStream_t st) {
-  if (dtype == KDE_F64)
-    k_prep<double><<<n_ds, kPrepThreads, 0, st>>>(ds);
-  else
-    k_prep<float><<<n_ds, kPrepThreads, 0, st>>>(ds);
+cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, cudaStream_t st) {
+  if (n_ds <= 0) return cudaSuccess;
+  k_prep<<<n_ds, kPrepThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }
 

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
     const int di = find_ds(ph.off, ph.n_ds, it);
     const DsDev* ds = ph.ds + di;
     if (ds->res.status != KDE_OK) continue;
-    const int64_t row = it - ph.off[di];
+    const int64_t row = it - ph.off[di] + (ph.base ? ph.base[di] : 0);
     const int64_t t0 = ds->psi_t0 + row * ds->psi_K;
     const int64_t t1 = min(t0 + (int64_t)ds->psi_K, ds->psi_tiles);
     const int64_t n = ds->n;
@@ -145,8 +145,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
 //   stage 4: psi_4(g2) (Eq. PLUGIN-Psi4Estimate, reading R1), then h
 //            (Eq. PLUGIN-Final_h);
 //   stage 0: raw pair sum only (psi tile-sum entry point), into res.g_min.
-__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, int stage, int r) {
-  DsDev* ds = dsa + blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   __shared__ double sRed[kWarps];
   if (ds->res.status != KDE_OK) return;
   if (stage != 0 && !(ds->methods & KDE_METHOD_PLUGIN)) return;
@@ -192,8 +192,11 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, int stage, 
     }
     const double rk = 1.0 / (2.0 * sqrt(kPi));  // R(K), Eq. PLUGIN-Final_h
     const double h = pow(rk / (psi4 * n), 0.2);
-    res.h = h;
-    res.h_data = h;
+    res.h_plugin = h;
+    if (!(ds->methods & KDE_METHOD_LSCV)) {  // otherwise h / h_data hold the LSCV choice
+      res.h = h;
+      res.h_data = h;
+    }
   }
 }
 
@@ -229,8 +232,9 @@ cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef&
   }
 }
 
-cudaError_t launch_psi_finish(DsDev* ds, int n_ds, int stage, int r, cudaStream_t st) {
-  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, stage, r);
+cudaError_t launch_psi_finish(DsDev* ds, int n_ds, const int* ids, int stage, int r, cudaStream_t st) {
+  if (n_ds <= 0) return cudaSuccess;
+  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, ids, stage, r);
   return cudaGetLastError();
 }
 

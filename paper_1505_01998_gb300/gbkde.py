@@ -48,10 +48,15 @@ class kde_opts(ctypes.Structure):
 class kde_result(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int) for k in ("status", "method", "argmin", "flags", "n_h", "d")] + [
         (k, ctypes.c_double) for k in ("h", "h_data", "g_min", "sigma", "psi8_ns", "g1", "psi6",
-                                       "g2", "psi4", "logdet_S")]
+                                       "g2", "psi4", "logdet_S", "h_plugin")]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class kde_request(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("dtype", ctypes.c_int), ("d", ctypes.c_int),
+                ("n", ctypes.c_int64), ("methods", ctypes.c_int), ("grid", kde_grid)]
 
 
 _lock = threading.Lock()
@@ -85,6 +90,19 @@ SIGNATURES = {
     "kde_psi_tile_sums": (_I, [_P, _I, _L, _I, _D, _L, _L, ctypes.POINTER(kde_opts), _P, _S, _P, _DP]),
     "kde_psi_tile_edge": (_I, [_L, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int)]),
     "kde_probe_alu": (_I, [_P, _S, _P, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), _DP]),
+    "kde_lscv_H_workspace_size": (_I, [_L, _I, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(_S)]),
+    "kde_lscv_H": (_I, [_P, _I, _L, _I, _DP, _I, ctypes.POINTER(kde_opts), _P, _S, _P, _DP]),
+    "kde_batch_plan_create": (_I, [ctypes.POINTER(kde_request), _I, ctypes.POINTER(kde_opts),
+                                   ctypes.POINTER(_P), ctypes.POINTER(_S)]),
+    "kde_batch_run_async": (_I, [_P, _P, _S, _P]),
+    "kde_batch_run": (_I, [_P, _P, _S, _P, ctypes.POINTER(kde_result)]),
+    "kde_batch_results": (_I, [_P, ctypes.POINTER(kde_result)]),
+    "kde_batch_g": (_I, [_P, _P, _I, _DP]),
+    "kde_batch_plan_destroy": (_I, [_P]),
+    "kde_batch_workspace_size": (_I, [ctypes.POINTER(kde_request), _I, ctypes.POINTER(kde_opts),
+                                      ctypes.POINTER(_S)]),
+    "kde_select_batch": (_I, [ctypes.POINTER(kde_request), _I, ctypes.POINTER(kde_opts), _P, _S, _P,
+                              ctypes.POINTER(kde_result)]),
 }
 
 
@@ -341,3 +359,108 @@ def read_ws_result(ws, n_h: int = 0):
     if n_h:
         g = ws[goff:goff + 8 * n_h].cpu().view(torch.float64).numpy().copy()
     return res, g
+
+
+# ------------------------------------------------------------------ LSCV_H
+
+def kde_lscv_H_workspace_size(n: int, d: int, m: int, opts: kde_opts | None = None) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().kde_lscv_H_workspace_size(int(n), int(d), int(m),
+                                           ctypes.byref(opts) if opts else None, ctypes.byref(out)))
+    return out.value
+
+
+def kde_lscv_H(x, H, opts: kde_opts | None = None, ws=None, stream=None) -> np.ndarray:
+    """g(H) for each of the m bandwidth matrices H (m, d, d) on device samples x (d, n)."""
+    ptr, dt, n, d = _samples(x)
+    HH = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(-1, d, d))
+    m = HH.shape[0]
+    if ws is None:
+        ws = workspace(kde_lscv_H_workspace_size(n, d, m, opts), x.device)
+    wp, wn = _ws(ws)
+    g = np.zeros(m)
+    _check(lib().kde_lscv_H(ptr, dt, n, d, _dp(HH), m, ctypes.byref(opts) if opts else None,
+                            wp, wn, _stream_handle(stream), _dp(g)))
+    return g
+
+
+# ------------------------------------------------------------------ batches
+
+def make_request(x, methods=KDE_METHOD_LSCV | KDE_METHOD_PLUGIN, grid: kde_grid | None = None):
+    """A kde_request for device samples x (d, n) (or host numpy samples for the
+    server).  Returns (request, keepalive)."""
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x if x.ndim == 2 else x[None, :])
+        ptr, dt, n, d = a.ctypes.data, (KDE_F64 if a.dtype == np.float64 else KDE_F32), a.shape[1], a.shape[0]
+        keep = a
+    else:
+        p, dt, n, d = _samples(x)
+        ptr, keep = p.value, x
+    g = grid if grid is not None else kde_grid(KDE_GRID_DEFAULT_Z, 128, None, 0.0, 0.0)
+    return kde_request(ptr, dt, d, n, methods, g), keep
+
+
+class BatchPlan:
+    """Owner of a kde_batch_plan (destroyed with the object)."""
+
+    def __init__(self, requests, opts: kde_opts | None = None, keepalive=()):
+        self.n = len(requests)
+        self._reqs = (kde_request * self.n)(*requests)
+        self._keep = list(keepalive)
+        self.opts = opts
+        h = ctypes.c_void_p(0)
+        nb = ctypes.c_size_t(0)
+        _check(lib().kde_batch_plan_create(self._reqs, self.n, ctypes.byref(opts) if opts else None,
+                                           ctypes.byref(h), ctypes.byref(nb)))
+        self.handle = h
+        self.ws_bytes = nb.value
+
+    def run(self, ws, stream=None):
+        wp, wn = _ws(ws)
+        out = (kde_result * self.n)()
+        _check(lib().kde_batch_run(self.handle, wp, wn, _stream_handle(stream), out))
+        return [r.as_dict() for r in out]
+
+    def run_async(self, ws, stream=None):
+        wp, wn = _ws(ws)
+        _check(lib().kde_batch_run_async(self.handle, wp, wn, _stream_handle(stream)))
+
+    def results(self):
+        out = (kde_result * self.n)()
+        _check(lib().kde_batch_results(self.handle, out))
+        return [r.as_dict() for r in out]
+
+    def g(self, ws, req: int, n_h: int) -> np.ndarray:
+        out = np.zeros(n_h)
+        _check(lib().kde_batch_g(self.handle, ctypes.c_void_p(ws.data_ptr()), int(req), _dp(out)))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().kde_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kde_batch_workspace_size(requests, opts: kde_opts | None = None) -> int:
+    arr = (kde_request * len(requests))(*requests)
+    out = ctypes.c_size_t(0)
+    _check(lib().kde_batch_workspace_size(arr, len(requests), ctypes.byref(opts) if opts else None,
+                                          ctypes.byref(out)))
+    return out.value
+
+
+def kde_select_batch(requests, opts: kde_opts | None = None, ws=None, stream=None):
+    arr = (kde_request * len(requests))(*requests)
+    if ws is None:
+        ws = workspace(kde_batch_workspace_size(requests, opts))
+    wp, wn = _ws(ws)
+    out = (kde_result * len(requests))()
+    _check(lib().kde_select_batch(arr, len(requests), ctypes.byref(opts) if opts else None, wp, wn,
+                                  _stream_handle(stream), out))
+    return [r.as_dict() for r in out]

@@ -1,0 +1,193 @@
+"""Batched selection (one graph-captured launch sequence for many datasets)
+and the LSCV_H objective, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1505_01998_gb300 import datagen
+from tests._helpers import TOL, built_lib, g_err, lscv_A
+
+pytestmark = pytest.mark.gpu
+
+LSCV, PLUGIN = 1, 2
+
+
+@pytest.fixture(scope="module")
+def kde():
+    return built_lib()
+
+
+def dev(x, dtype="float32"):
+    import torch
+    a = np.ascontiguousarray(np.asarray(x))
+    if a.ndim == 1:
+        a = a[None, :]
+    return torch.from_numpy(a.astype(dtype)).cuda()
+
+
+def _mixed_requests(kde, count=24, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs, keep, meta = [], [], []
+    for k in range(count):
+        n = int(rng.integers(40, 6000))
+        d = int(rng.choice([1, 1, 2, 3, 4]))
+        if d == 1:
+            methods = int(rng.choice([LSCV, PLUGIN, LSCV | PLUGIN]))
+            x = datagen.batch_dataset(n, rng)
+        else:
+            methods = LSCV
+            x = datagen.correlated_mixture(n, d, seed=1000 + k)
+        n_h = int(rng.choice([16, 40, 64, 96, 128, 200]))
+        h = oracle.grid_default(n, d, n_h)
+        grid, hk = kde.make_grid(h=h)
+        xd = dev(x, "float64" if k % 5 == 0 else "float32")
+        req, rk = kde.make_request(xd, methods, grid)
+        reqs.append(req)
+        keep += [hk, rk, xd]
+        meta.append((xd, methods, grid, h))
+    return reqs, keep, meta
+
+
+def test_batch_equals_single_calls_bitwise(kde):
+    reqs, keep, meta = _mixed_requests(kde)
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    ws = kde.workspace(plan.ws_bytes)
+    out = plan.run(ws)
+    for k, (xd, methods, grid, h) in enumerate(meta):
+        r = out[k]
+        assert r["status"] == 0, (k, r)
+        if methods & LSCV:
+            single, g1, _ = kde.kde_lscv(xd, grid)
+            gb = plan.g(ws, k, len(h))
+            assert np.array_equal(gb, g1), k
+            for key in ("argmin", "h", "h_data", "g_min", "logdet_S"):
+                assert r[key] == single[key], (k, key)
+        if methods & PLUGIN:
+            p = kde.kde_plugin(xd)
+            for key in ("sigma", "g1", "psi6", "g2", "psi4"):
+                assert r[key] == p[key], (k, key)
+            assert r["h_plugin"] == p["h"]
+        if methods == PLUGIN:
+            assert r["h"] == r["h_plugin"]
+
+
+def test_batch_graph_replay_and_in_place_update(kde):
+    import torch
+    reqs, keep, meta = _mixed_requests(kde, count=10, seed=3)
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    ws = kde.workspace(plan.ws_bytes)
+    a = plan.run(ws)
+    b = plan.run(ws)
+    assert a == b
+    xd = meta[0][0]
+    xd.mul_(1.7).add_(0.3)  # new data behind the same pointer: the replay must see it
+    torch.cuda.synchronize()
+    c = plan.run(ws)
+    if meta[0][1] & LSCV:
+        single, _, _ = kde.kde_lscv(xd, meta[0][2])
+        assert c[0]["g_min"] == single["g_min"]
+    for k in range(1, 10):
+        assert c[k] == a[k]
+
+
+def test_select_batch_one_shot_matches_plan(kde):
+    reqs, keep, meta = _mixed_requests(kde, count=8, seed=5)
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    a = plan.run(kde.workspace(plan.ws_bytes))
+    b = kde.kde_select_batch(reqs)
+    assert a == b
+
+
+def test_batch_against_oracle(kde):
+    rng = np.random.default_rng(11)
+    reqs, keep, data = [], [], []
+    for k in range(6):
+        n = int(rng.integers(200, 1500))
+        x = datagen.batch_dataset(n, rng)
+        h = oracle.grid_default(n, 1, 64)
+        grid, hk = kde.make_grid(h=h)
+        xd = dev(x)
+        req, rk = kde.make_request(xd, LSCV | PLUGIN, grid)
+        reqs.append(req)
+        keep += [hk, rk, xd]
+        data.append((x.astype(np.float32).astype(np.float64), h))
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    ws = kde.workspace(plan.ws_bytes)
+    out = plan.run(ws)
+    for k, (x64, h) in enumerate(data):
+        ref = oracle.lscv_h(x64, h)
+        g = plan.g(ws, k, len(h))
+        err = g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, x64.shape[1], 1, lscv_A(x64))
+        assert err.max() < TOL
+        assert out[k]["argmin"] == ref["argmin"]
+        p = oracle.plugin(x64[0])
+        assert abs(out[k]["h_plugin"] - p["h"]) <= TOL * p["h"]
+
+
+def test_batch_rejects_bad_requests(kde):
+    x = dev(datagen.correlated_mixture(100, 2, seed=1))
+    req, keep = kde.make_request(x, PLUGIN)  # PLUGIN with d = 2
+    with pytest.raises(kde.KdeError) as e:
+        kde.BatchPlan([req], keepalive=[keep])
+    assert e.value.status == kde.KDE_EINVAL
+
+
+def test_batch_degenerate_member_does_not_spoil_others(kde):
+    good = dev(datagen.mixture_1d(500, seed=2))
+    const = dev(np.full((1, 300), 2.5))
+    r1, k1 = kde.make_request(good, LSCV | PLUGIN)
+    r2, k2 = kde.make_request(const, LSCV | PLUGIN)
+    plan = kde.BatchPlan([r1, r2], keepalive=[k1, k2])
+    out = plan.run(kde.workspace(plan.ws_bytes))
+    assert out[0]["status"] == 0
+    assert out[1]["status"] == kde.KDE_EDEGENERATE
+    single, _, _ = kde.kde_lscv(good, kde.make_grid(n_h=128)[0])
+    assert out[0]["g_min"] == single["g_min"]
+
+
+# ------------------------------------------------------------------ LSCV_H
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_lscv_H_general_matrices_vs_oracle(kde, d):
+    n = 900
+    x = datagen.correlated_mixture(n, d, seed=20 + d)
+    x64 = x.astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(d)
+    Hs = []
+    for k in range(5):
+        A = rng.normal(size=(d, d)) * 0.3
+        Hs.append(A @ A.T + (0.05 + 0.2 * k) * np.eye(d))
+    g = kde.kde_lscv_H(dev(x), np.array(Hs))
+    for k, H in enumerate(Hs):
+        ref = oracle.lscv_H(x64, H)
+        # magnitude scale: the same sum with every term positive
+        ckk = (4 * math.pi) ** (-d / 2) / math.sqrt(np.linalg.det(H))
+        scale = max(abs(ref), ckk / n)
+        assert abs(g[k] - ref) <= TOL * scale * 10 ** 0, (k, g[k], ref)
+
+
+def test_lscv_H_at_scaled_covariance_equals_lscv_h(kde):
+    n, d = 1200, 2
+    x = datagen.correlated_mixture(n, d, seed=4)
+    x64 = x.astype(np.float32).astype(np.float64)
+    h = np.array([0.2, 0.45, 0.9])
+    _, S = oracle.mean_cov(x64)
+    gH = kde.kde_lscv_H(dev(x), np.array([hh * hh * S for hh in h]))
+    res, gh, _ = kde.kde_lscv(dev(x), kde.make_grid(h=h)[0])
+    ref = oracle.lscv_h(x64, h)
+    err = g_err(gH, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, lscv_A(x64))
+    assert err.max() < TOL
+    err2 = g_err(gH, gh, ref["s_kk"], ref["s_k"], h, n, d, lscv_A(x64))
+    assert err2.max() < TOL
+
+
+def test_lscv_H_rejects_non_pd_and_asymmetric(kde):
+    x = dev(datagen.correlated_mixture(200, 2, seed=1))
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv_H(x, np.array([[[1.0, 2.0], [2.0, 1.0]]]))
+    assert e.value.status == kde.KDE_EDEGENERATE
+    with pytest.raises(kde.KdeError) as e:
+        kde.kde_lscv_H(x, np.array([[[1.0, 0.1], [0.2, 1.0]]]))
+    assert e.value.status == kde.KDE_EINVAL
