@@ -177,6 +177,141 @@ def run_reference(args, ws, rank):
     return 0
 
 
+# ------------------------------------------------------- batch and serving
+
+def run_batch(args):
+    """512 univariate datasets (sizes log-uniform on [256, 131072], seed 4),
+    each LSCV on 128 points over Z(h0) plus PLUGIN, as one graph-captured batch;
+    against the plain per-dataset path (one kde_lscv + kde_plugin pair of
+    calls per dataset on one stream)."""
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(0)
+    sets = datagen.batch(args.batch_count, seed=4)
+    xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in sets]
+    grid = gbkde.make_grid(n_h=128)[0]
+    reqs, keep = [], []
+    for x in xs:
+        r, k = gbkde.make_request(x, gbkde.KDE_METHOD_LSCV | gbkde.KDE_METHOD_PLUGIN, grid)
+        reqs.append(r)
+        keep.append(k)
+    evals = sum(pairs(x.shape[1]) * (128 + 2) for x in xs)
+    plan = gbkde.BatchPlan(reqs, keepalive=keep)
+    ws = gbkde.workspace(plan.ws_bytes)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(max(3, args.warmup)):
+        plan.run(ws)
+    ms = []
+    for _ in range(args.steps):
+        e0.record(stream)
+        plan.run_async(ws, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    res = plan.results()
+    # plain per-dataset path
+    wss = [gbkde.workspace(max(gbkde.kde_workspace_size(x.shape[1], 1, 128),
+                               gbkde.kde_workspace_size(x.shape[1], 1, 0))) for x in xs]
+    wsp = [gbkde.workspace(gbkde.kde_workspace_size(x.shape[1], 1, 0)) for x in xs]
+
+    def plain():
+        for x, w, wp in zip(xs, wss, wsp):
+            gbkde.kde_lscv_async(x, grid, None, w, stream)
+            gbkde.kde_plugin_async(x, None, wp, stream)
+
+    plain()
+    torch.cuda.synchronize()
+    pms = []
+    for _ in range(max(1, args.steps // 2)):
+        e0.record(stream)
+        plain()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms.append(e0.elapsed_time(e1))
+    # equal results: the plain path's last result of every dataset
+    same = all(gbkde.read_ws_result(w, 128)[0]["g_min"] == r["g_min"] for w, r in zip(wss, res))
+    t = statistics.median(ms)
+    line = {"workload": "batch", "metric": METRIC + " (batched, CUDA-graph replay)", "unit": UNIT,
+            "value": evals / (t * 1e-3), "ms_per_batch": t, "datasets": len(xs),
+            "evals_per_batch": evals, "samples": int(sum(x.shape[1] for x in xs)),
+            "plain_path": {"value": evals / (statistics.median(pms) * 1e-3),
+                           "ms_per_batch": statistics.median(pms)},
+            "speedup_vs_plain": statistics.median(pms) / t,
+            "bitwise_equal_to_plain": bool(same),
+            "statuses_ok": sum(r["status"] == 0 for r in res)}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals of selection requests (n log-uniform on [1024, 262144],
+    d = 1 : 2 at 4 : 1, LSCV or PLUGIN half and half, seed 5) at a sweep of
+    rates, served under a 40 GB arena; against the plain path (the same
+    requests, one kde_lscv / kde_plugin call at a time in arrival order)."""
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(0)
+    grid = gbkde.make_grid(n_h=128)[0]
+    arena = gbkde.workspace(args.serve_budget_gb << 30)
+    stream = torch.cuda.current_stream()
+    records = []
+    for rate in args.rates:
+        count = args.serve_count
+        reqs = datagen.serving_requests(rate, count, seed=5)
+        srv = gbkde.Server(arena, max_slots=256)
+        t0 = time.perf_counter()
+        tickets = []
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            m = gbkde.KDE_METHOD_LSCV if r.method == "lscv" else gbkde.KDE_METHOD_PLUGIN
+            tickets.append(srv.submit(r.x, m, grid))
+        for t in tickets:
+            rc, _ = srv.wait(t, 600000)
+            assert rc == 0, rc
+        st = srv.stats()
+        srv.close()
+        # plain path: arrivals at the same times, served one at a time
+        ws = gbkde.workspace(max(gbkde.kde_workspace_size(r.n, r.d, 128) for r in reqs))
+        lat = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            now = time.perf_counter() - t0
+            if r.arrival_s > now:
+                time.sleep(r.arrival_s - now)
+            xd = torch.from_numpy(r.x).cuda()
+            if r.method == "lscv":
+                gbkde.kde_lscv(xd, grid, None, ws, stream)
+            else:
+                gbkde.kde_plugin(xd, None, ws, stream)
+            lat.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
+        span = time.perf_counter() - t0
+        records.append({"rate": rate, "requests": count,
+                        "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
+                                   "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
+                                   "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],
+                                   "steps": st["steps"], "arena_peak_bytes": st["arena_peak_bytes"]},
+                        "plain": {"requests_per_s": count / span,
+                                  "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99))}})
+        print(json.dumps(records[-1]), flush=True)
+    best = max(r["served"]["requests_per_s"] for r in records)
+    best_plain = max(r["plain"]["requests_per_s"] for r in records)
+    print(json.dumps({"workload": "serve", "metric": "served selections/s", "unit": "requests/s",
+                      "value": best, "plain_path_value": best_plain,
+                      "budget_bytes": args.serve_budget_gb << 30, "rates": records}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -189,11 +324,22 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=N,
                     help="sample count (default 65536; smaller values only for profiling captures)")
+    ap.add_argument("--workload", choices=("selection", "batch", "serve"), default="selection",
+                    help="selection (default): the benchmark line; batch / serve: the batched and "
+                         "served workloads, printed as their own JSON lines")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--serve-count", type=int, default=120)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
     args = ap.parse_args()
     set_n(args.n)
     world, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, None, rank)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args, world, rank, local)
 
 

@@ -299,6 +299,68 @@ int kde_batch_workspace_size(const kde_request* reqs, int n_req, const kde_opts*
 int kde_select_batch(const kde_request* reqs, int n_req, const kde_opts* opts, void* ws,
                      size_t ws_bytes, void* stream, kde_result* outs);
 
+/* -------------------------------------------------------------- serving */
+
+/* Server configuration.  The arena is device memory owned by the caller (for
+ * example a torch tensor); its size is the HBM budget: the slot table and the
+ * step parameter blocks sit at its start, request regions (samples, prepared
+ * samples, partial sums) are carved from the rest. */
+typedef struct kde_serve_config {
+  void* arena;            /* 256-byte aligned device memory                         */
+  size_t arena_bytes;     /* HBM budget                                              */
+  int max_slots;          /* requests resident at once, 1 .. 1024                    */
+  int max_queue;          /* waiting requests before submit returns KDE_EBUSY (0 = unbounded) */
+  double quantum_evals;   /* pair evaluations per scheduling step (0 = 4e10, a few ms) */
+  int step_deadline_ms;   /* a step still running after this fails its requests with
+                             KDE_ETIMEDOUT (host-side detection; 0 = no deadline)     */
+  int device;             /* CUDA device index                                       */
+  const kde_opts* opts;   /* geometry options for every request (NULL = defaults)    */
+} kde_serve_config;
+
+typedef struct kde_serve_stats_t {
+  uint64_t submitted, completed, failed, cancelled, rejected;
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result, completed requests */
+  double p50_wait_ms, p99_wait_ms;        /* submit -> admission                   */
+  double requests_per_s;                  /* completed / (last result - first submit) */
+  double evals_per_s;                     /* pair evaluations of completed requests / same span */
+  int64_t steps;
+  int queue_depth_max, active_max;
+  size_t arena_peak_bytes;
+} kde_serve_stats_t;
+
+typedef struct kde_server kde_server;
+
+/* Starts a server: one scheduler thread, one compute and one copy stream on
+ * cfg->device.  Requests are advanced together in steps (continuous
+ * batching); a request keeps the geometry of the single-request entry points,
+ * so its result is bitwise the one kde_lscv / kde_plugin would return. */
+int kde_serve_create(const kde_serve_config* cfg, kde_server** server);
+
+/* Queues a request with HOST samples (copied at submit: the caller may reuse
+ * its buffer on return).  Admission waits for a free slot and arena space.
+ * Errors: KDE_EINVAL, KDE_EBUSY (queue full, or the request alone exceeds the
+ * arena). */
+int kde_serve_submit(kde_server* server, const kde_request* req, uint64_t* ticket);
+
+/* Result of a finished request (then forgotten): KDE_OK, or the request's
+ * failure status (KDE_EDEGENERATE, KDE_ECANCELLED, KDE_ETIMEDOUT ...);
+ * KDE_EAGAIN while it is still queued or running; KDE_ENOTFOUND. */
+int kde_serve_poll(kde_server* server, uint64_t ticket, kde_result* out);
+
+/* As kde_serve_poll, waiting up to timeout_ms (< 0: no limit); KDE_ETIMEDOUT
+ * if the request is still running then (it keeps running). */
+int kde_serve_wait(kde_server* server, uint64_t ticket, int timeout_ms, kde_result* out);
+
+/* Cancels a request: dropped at once if queued, at the next step boundary if
+ * running; its arena region is released when no launched step references it. */
+int kde_serve_cancel(kde_server* server, uint64_t ticket);
+
+int kde_serve_stats(kde_server* server, kde_serve_stats_t* out);
+
+/* Stops the scheduler after the steps in flight complete and frees host
+ * resources (the arena stays the caller's). */
+int kde_serve_destroy(kde_server* server);
+
 /* ------------------------------------------------------- measurement aids */
 
 /* Kernel timing hook for the calling thread.  When set (non-NULL cudaEvent_t

@@ -103,7 +103,33 @@ SIGNATURES = {
                                       ctypes.POINTER(_S)]),
     "kde_select_batch": (_I, [ctypes.POINTER(kde_request), _I, ctypes.POINTER(kde_opts), _P, _S, _P,
                               ctypes.POINTER(kde_result)]),
+    "kde_serve_create": (_I, [ctypes.c_void_p, ctypes.POINTER(_P)]),
+    "kde_serve_submit": (_I, [_P, ctypes.POINTER(kde_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "kde_serve_poll": (_I, [_P, ctypes.c_uint64, ctypes.POINTER(kde_result)]),
+    "kde_serve_wait": (_I, [_P, ctypes.c_uint64, _I, ctypes.POINTER(kde_result)]),
+    "kde_serve_cancel": (_I, [_P, ctypes.c_uint64]),
+    "kde_serve_stats": (_I, [_P, ctypes.c_void_p]),
+    "kde_serve_destroy": (_I, [_P]),
 }
+
+
+class kde_serve_config(ctypes.Structure):
+    _fields_ = [("arena", ctypes.c_void_p), ("arena_bytes", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int), ("max_queue", ctypes.c_int),
+                ("quantum_evals", ctypes.c_double), ("step_deadline_ms", ctypes.c_int),
+                ("device", ctypes.c_int), ("opts", ctypes.POINTER(kde_opts))]
+
+
+class kde_serve_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "failed", "cancelled",
+                                                "rejected")] + [
+        (k, ctypes.c_double) for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms", "p50_wait_ms",
+                                       "p99_wait_ms", "requests_per_s", "evals_per_s")] + [
+        ("steps", ctypes.c_int64), ("queue_depth_max", ctypes.c_int), ("active_max", ctypes.c_int),
+        ("arena_peak_bytes", ctypes.c_size_t)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def lib():
@@ -464,3 +490,65 @@ def kde_select_batch(requests, opts: kde_opts | None = None, ws=None, stream=Non
     _check(lib().kde_select_batch(arr, len(requests), ctypes.byref(opts) if opts else None, wp, wn,
                                   _stream_handle(stream), out))
     return [r.as_dict() for r in out]
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """kde_serve_*: a continuous-batching server over a caller-owned arena
+    (a torch uint8 tensor whose size is the HBM budget)."""
+
+    def __init__(self, arena, max_slots=256, max_queue=0, quantum_evals=0.0, step_deadline_ms=0,
+                 device=0, opts: kde_opts | None = None):
+        self.arena = arena
+        self._opts = opts
+        cfg = kde_serve_config(ctypes.c_void_p(arena.data_ptr()), arena.numel(), int(max_slots),
+                               int(max_queue), float(quantum_evals), int(step_deadline_ms),
+                               int(device), ctypes.pointer(opts) if opts else None)
+        h = ctypes.c_void_p(0)
+        _check(lib().kde_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, x_host: np.ndarray, methods: int, grid: kde_grid | None = None) -> int:
+        req, _keep = make_request(np.ascontiguousarray(x_host), methods, grid)
+        t = ctypes.c_uint64(0)
+        _check(lib().kde_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def submit_status(self, x_host: np.ndarray, methods: int, grid: kde_grid | None = None):
+        """(status, ticket) without raising."""
+        req, _keep = make_request(np.ascontiguousarray(x_host), methods, grid)
+        t = ctypes.c_uint64(0)
+        rc = lib().kde_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket: int):
+        """(status, result dict); status KDE_EAGAIN while not finished."""
+        res = kde_result()
+        rc = lib().kde_serve_poll(self.handle, ctypes.c_uint64(ticket), ctypes.byref(res))
+        return rc, res.as_dict()
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        res = kde_result()
+        rc = lib().kde_serve_wait(self.handle, ctypes.c_uint64(ticket), int(timeout_ms),
+                                  ctypes.byref(res))
+        return rc, res.as_dict()
+
+    def cancel(self, ticket: int) -> int:
+        return lib().kde_serve_cancel(self.handle, ctypes.c_uint64(ticket))
+
+    def stats(self) -> dict:
+        s = kde_serve_stats_t()
+        _check(lib().kde_serve_stats(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            lib().kde_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,143 @@
+"""The continuous-batching server (kde_serve_*) through the C ABI.
+
+Failure detection is exercised on the host only: a step deadline that the
+host declares missed, cancellation, a full queue, an oversized request.  No
+test faults, traps or stalls the GPU."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1505_01998_gb300 import datagen
+from tests._helpers import built_lib
+
+pytestmark = pytest.mark.gpu
+
+LSCV, PLUGIN = 1, 2
+
+
+@pytest.fixture(scope="module")
+def kde():
+    return built_lib()
+
+
+def arena(nbytes):
+    from paper_1505_01998_gb300 import gbkde
+    return gbkde.workspace(nbytes)
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _requests(count, seed, lo=800, hi=20000):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n = int(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+        d = 1 if rng.uniform() < 0.8 else 2
+        methods = LSCV if d == 2 else (PLUGIN if rng.uniform() < 0.6 else LSCV)
+        x = datagen.correlated_mixture(n, d, seed=int(rng.integers(1 << 30)))
+        out.append((x, methods))
+    return out
+
+
+def _single(kde, x, methods, grid):
+    if methods == LSCV:
+        return kde.kde_lscv(dev(x), grid)[0]
+    return kde.kde_plugin(dev(x))
+
+
+def test_results_in_the_mix_equal_single_calls_bitwise(kde):
+    grid = kde.make_grid(n_h=128)[0]
+    reqs = _requests(40, seed=1)
+    srv = kde.Server(arena(1 << 30), max_slots=64)
+    tickets = [srv.submit(x, m, grid) for x, m in reqs]
+    outs = []
+    for t in tickets:
+        rc, r = srv.wait(t, 60000)
+        assert rc == 0, (rc, r)
+        outs.append(r)
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["active_max"] > 1  # requests were on the device together
+    for (x, m), r in zip(reqs, outs):
+        s = _single(kde, x, m, grid)
+        keys = ("argmin", "h", "h_data", "g_min") if m == LSCV else ("sigma", "g1", "psi6", "g2", "psi4", "h")
+        for k in keys:
+            assert r[k] == s[k], (m, k, r[k], s[k])
+
+
+def test_admission_under_a_small_budget(kde):
+    grid = kde.make_grid(n_h=64)[0]
+    reqs = _requests(30, seed=2, lo=2000, hi=30000)
+    budget = 24 << 20
+    srv = kde.Server(arena(budget), max_slots=32)
+    tickets = [srv.submit(x, m, grid) for x, m in reqs]
+    for t in tickets:
+        rc, r = srv.wait(t, 120000)
+        assert rc == 0
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == 30
+    assert st["arena_peak_bytes"] <= budget
+    assert st["queue_depth_max"] > 0 and st["p99_wait_ms"] > 0  # some had to wait for memory
+
+
+def test_cancel_queued_and_running(kde):
+    grid = kde.make_grid(n_h=256)[0]
+    big = datagen.skewed_column(65536, seed=9)
+    small = datagen.mixture_1d(3000, seed=3).astype(np.float32)
+    srv = kde.Server(arena(1 << 30), max_slots=1)  # one slot: the second request queues
+    t_big = srv.submit(big, LSCV, grid)
+    t_q = srv.submit(small, LSCV, grid)
+    t_ok = srv.submit(small, PLUGIN)
+    assert srv.cancel(t_q) == 0
+    assert srv.cancel(t_big) == 0
+    rc, r = srv.wait(t_q, 10000)
+    assert rc == kde.KDE_ECANCELLED
+    rc, r = srv.wait(t_big, 60000)
+    assert rc == kde.KDE_ECANCELLED
+    rc, r = srv.wait(t_ok, 60000)
+    assert rc == 0
+    assert r["h"] == kde.kde_plugin(dev(small))["h"]
+    st = srv.stats()
+    srv.close()
+    assert st["cancelled"] == 2 and st["completed"] == 1
+
+
+def test_step_deadline_fails_requests_on_the_host_and_server_recovers(kde):
+    grid = kde.make_grid(n_h=256)[0]
+    big = datagen.skewed_column(65536, seed=4)
+    # one step of this request is ~tens of ms; a 1 ms deadline is missed
+    srv = kde.Server(arena(1 << 30), max_slots=4, quantum_evals=5e11, step_deadline_ms=1)
+    t = srv.submit(big, LSCV, grid)
+    rc, r = srv.wait(t, 60000)
+    assert rc == kde.KDE_ETIMEDOUT
+    srv.close()
+    # a fresh server on the same device keeps serving correctly
+    srv = kde.Server(arena(256 << 20), max_slots=4)
+    x = datagen.mixture_1d(5000, seed=5).astype(np.float32)
+    rc, r = srv.wait(srv.submit(x, PLUGIN), 60000)
+    srv.close()
+    assert rc == 0 and r["h"] == kde.kde_plugin(dev(x))["h"]
+
+
+def test_busy_and_wait_timeout(kde):
+    grid = kde.make_grid(n_h=128)[0]
+    srv = kde.Server(arena(8 << 20), max_slots=2, max_queue=1)
+    huge = datagen.skewed_column(262144, seed=1)
+    rc, _ = srv.submit_status(huge, LSCV, grid)
+    assert rc == kde.KDE_EBUSY  # alone larger than the arena
+    x = datagen.mixture_1d(20000, seed=2).astype(np.float32)
+    t1 = srv.submit(x, LSCV, grid)
+    rc, _ = srv.wait(t1, 0)
+    assert rc in (0, kde.KDE_ETIMEDOUT)
+    for t in [t1]:
+        rc, r = srv.wait(t, 60000)
+        assert rc == 0
+    rc, r = srv.poll(123456)
+    assert rc == kde.KDE_ENOTFOUND
+    srv.close()
