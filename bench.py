@@ -66,6 +66,24 @@ def set_n(n):
 LAUNCHES_PER_STEP = 5 + 6  # LSCV: setup, prep, pairs, reduce, finish; PLUGIN: setup, prep, 2 x (pairs, finish)
 
 
+def profiled_lscv_traffic():
+    """DRAM bytes per full-size launch of the LSCV kernel from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", "k_lscv_skewed_column.md")
+    src = os.path.join(ROOT, "paper_1505_01998_gb300", "csrc", "lscv.cu")
+    try:
+        text = open(prof).read()
+        want = re.search(r"sha256 prefix `([0-9a-f]{16})`", text).group(1)
+        have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if want != have or N != 65536:
+            return None
+        return int(re.search(r"traffic = ([0-9,]+) bytes", text).group(1).replace(",", ""))
+    except Exception:
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -445,7 +463,7 @@ def run_gpu(args, world, rank, local):
     achieved = EVALS_LSCV / (lscv_ms * 1e-3) / 1e9
     peak_max = per_clk * probe["sm_count"] * 2070.0 * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Geval/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": profiled_lscv_traffic(),
                 "kernel": "k_lscv (all-pairs, all-bandwidths LSCV)",
                 "kernel_ms": lscv_ms, "evals_per_launch": EVALS_LSCV,
                 "peak_basis": (f"min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM, FP32 lanes "

@@ -202,6 +202,20 @@ int kde_lscv_tile_sums(const void* x_dev, int dtype, int64_t n, int d, const dou
                        void* ws, size_t ws_bytes, void* stream, double* s1_host,
                        double* s2_host);
 
+/* log det S of the samples (the prologue of kde_lscv, FP64 on the device):
+ * what kde_lscv_merge needs besides the summed exponential sums. */
+int kde_lscv_logdet(const void* x_dev, int dtype, int64_t n, int d, void* ws, size_t ws_bytes,
+                    void* stream, double* logdet_S);
+
+/* Finishes a sharded LSCV_h selection on the host in FP64: from the full
+ * exponential sums s1, s2 (the element-wise sum of kde_lscv_tile_sums over
+ * shards that cover the tile range exactly once) computes
+ * g(h) = h^-d A [2 n^-2 (s1 - 2^(1+d/2) s2) + n^-1], A = (4 pi)^(-d/2) exp(-logdet_S/2)
+ * (Eq. LSCV-gh) and the first-index argmin (Eq. LSCV-finalH).  g_out may be
+ * NULL; out receives argmin, h, g_min, flags. */
+int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, const double* s1,
+                   const double* s2, double* g_out, kde_result* out);
+
 /* ------------------------------------------------------------- PLUGIN */
 
 /* PLUGIN bandwidth selection for univariate data (Sec. 4.4.1, steps 1-8; GPU

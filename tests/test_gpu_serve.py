@@ -127,8 +127,8 @@ def test_step_deadline_fails_requests_on_the_host_and_server_recovers(kde):
 
 def test_busy_and_wait_timeout(kde):
     grid = kde.make_grid(n_h=128)[0]
-    srv = kde.Server(arena(8 << 20), max_slots=2, max_queue=1)
-    huge = datagen.skewed_column(262144, seed=1)
+    srv = kde.Server(arena(4 << 20), max_slots=2, max_queue=1)
+    huge = datagen.correlated_mixture(262144, 4, seed=1)  # 8 MB of staged samples alone
     rc, _ = srv.submit_status(huge, LSCV, grid)
     assert rc == kde.KDE_EBUSY  # alone larger than the arena
     x = datagen.mixture_1d(20000, seed=2).astype(np.float32)
