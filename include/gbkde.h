@@ -375,6 +375,30 @@ int kde_serve_stats(kde_server* server, kde_serve_stats_t* out);
  * resources (the arena stays the caller's). */
 int kde_serve_destroy(kde_server* server);
 
+/* ------------------------------------------------ no-allocation variant */
+
+/* Size of the scratch buffer built into the library for kde_lscv_noalloc. */
+#define KDE_NOALLOC_MAX_BYTES (16 << 20)
+
+/* kde_lscv without a caller workspace, for callers that cannot allocate
+ * device memory: code inside an application whose allocator owns the whole
+ * device heap, latency-critical code that must not take cudaMalloc's implicit
+ * synchronisation, plain C callers without a tensor library.  The paper has no
+ * counterpart; this is a convenience of this library.
+ * Arguments and results are those of kde_lscv.  Scratch comes from one
+ * KDE_NOALLOC_MAX_BYTES (16 MiB) buffer compiled into the library; every GPU
+ * that loads the library holds it until the process exits.  Problems whose
+ * workspace (kde_workspace_size) exceeds it are rejected with KDE_ENOMEM
+ * before anything is queued.  The first call on each device looks up the
+ * buffer's device address (with that device current); make it before any
+ * stream capture.  Every call shares the buffer, which keeps the previous
+ * call's contents (nothing in it needs to start at zero); calls that overlap
+ * on the GPU race on it and must be serialised by the caller.  Allocates no
+ * device memory; synchronises the stream like kde_lscv. */
+int kde_lscv_noalloc(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
+                     const kde_opts* opts, void* stream, double* g_host, double* h_host,
+                     kde_result* out);
+
 /* ------------------------------------------------------- measurement aids */
 
 /* Kernel timing hook for the calling thread.  When set (non-NULL cudaEvent_t

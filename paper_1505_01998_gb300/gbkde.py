@@ -110,29 +110,12 @@ SIGNATURES = {
     "kde_serve_cancel": (_I, [_P, ctypes.c_uint64]),
     "kde_serve_stats": (_I, [_P, ctypes.c_void_p]),
     "kde_serve_destroy": (_I, [_P]),
+    "kde_lscv_noalloc": (_I, [_P, _I, _L, _I, ctypes.POINTER(kde_grid), ctypes.POINTER(kde_opts), _P,
+                              _DP, _DP, ctypes.POINTER(kde_result)]),
     "kde_lscv_logdet": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
 }
 
-
-def kde_lscv_logdet(x, ws=None, stream=None) -> float:
-    ptr, dt, n, d = _samples(x)
-    if ws is None:
-        ws = workspace(kde_workspace_size(n, d, 1), x.device)
-    wp, wn = _ws(ws)
-    out = np.zeros(1)
-    _check(lib().kde_lscv_logdet(ptr, dt, n, d, wp, wn, _stream_handle(stream), _dp(out)))
-    return float(out[0])
-
-
-def kde_lscv_merge(n: int, d: int, logdet_S: float, h, s1, s2):
-    """g(h) and the argmin from summed shard sums (host FP64)."""
-    hh, a, b = (np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel()) for v in (h, s1, s2))
-    g = np.zeros(hh.size)
-    res = kde_result()
-    _check(lib().kde_lscv_merge(int(n), int(d), float(logdet_S), _dp(hh), hh.size, _dp(a), _dp(b),
-                                _dp(g), ctypes.byref(res)))
-    return res.as_dict(), g
 
 def kde_lscv_logdet(x, ws=None, stream=None) -> float:
     ptr, dt, n, d = _samples(x)
