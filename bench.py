@@ -217,6 +217,22 @@ def run_batch(args):
         reqs.append(r)
         keep.append(k)
     evals = sum(pairs(x.shape[1]) * (128 + 2) for x in xs)
+    tuned = {}
+    if args.autotune:
+        # tune the size buckets where geometry matters (n <= 16384); larger
+        # datasets fill the GPU on their own and keep the default rules
+        by_bucket = {}
+        for x in xs:
+            n = x.shape[1]
+            b = int(math.ceil(math.log2(n)))
+            if n <= 16384 and (b not in by_bucket or n > by_bucket[b].shape[1]):
+                by_bucket[b] = x
+        tws = gbkde.workspace(2 << 30)
+        for b, x in sorted(by_bucket.items()):
+            o, rate = gbkde.kde_autotune(x, 128, gbkde.KDE_TUNE_THROUGHPUT, tws)
+            tuned[b] = {"tile": o.tile, "bw_per_thread": o.bw_per_thread, "ctas_per_sm": o.ctas_per_sm,
+                        "tiles_per_item": o.tiles_per_item, "evals_per_s": rate}
+        del tws
     plan = gbkde.BatchPlan(reqs, keepalive=keep)
     ws = gbkde.workspace(plan.ws_bytes)
     stream = torch.cuda.current_stream()
@@ -260,7 +276,8 @@ def run_batch(args):
                            "ms_per_batch": statistics.median(pms)},
             "speedup_vs_plain": statistics.median(pms) / t,
             "bitwise_equal_to_plain": bool(same),
-            "statuses_ok": sum(r["status"] == 0 for r in res)}
+            "statuses_ok": sum(r["status"] == 0 for r in res),
+            "autotuned_buckets": tuned}
     print(json.dumps(line), flush=True)
     plan.close()
     return 0
@@ -293,27 +310,37 @@ def run_serve(args):
                 time.sleep(r.arrival_s - now)
             m = gbkde.KDE_METHOD_LSCV if r.method == "lscv" else gbkde.KDE_METHOD_PLUGIN
             tickets.append(srv.submit(r.x, m, grid))
-        for t in tickets:
+        failures = []
+        for k, t in enumerate(tickets):
             rc, _ = srv.wait(t, 600000)
-            assert rc == 0, rc
+            if rc != 0:
+                r = reqs[k]
+                failures.append({"index": k, "status": rc, "n": r.n, "d": r.d, "method": r.method,
+                                 "seed": r.seed})
         st = srv.stats()
         srv.close()
         # plain path: arrivals at the same times, served one at a time
         ws = gbkde.workspace(max(gbkde.kde_workspace_size(r.n, r.d, 128) for r in reqs))
         lat = []
+        plain_fail = {}
         t0 = time.perf_counter()
-        for r in reqs:
+        for k, r in enumerate(reqs):
             now = time.perf_counter() - t0
             if r.arrival_s > now:
                 time.sleep(r.arrival_s - now)
             xd = torch.from_numpy(r.x).cuda()
-            if r.method == "lscv":
-                gbkde.kde_lscv(xd, grid, None, ws, stream)
-            else:
-                gbkde.kde_plugin(xd, None, ws, stream)
+            try:
+                if r.method == "lscv":
+                    gbkde.kde_lscv(xd, grid, None, ws, stream)
+                else:
+                    gbkde.kde_plugin(xd, None, ws, stream)
+            except gbkde.KdeError as e:
+                plain_fail[k] = e.status
             lat.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
         span = time.perf_counter() - t0
-        records.append({"rate": rate, "requests": count,
+        for f in failures:  # the same request through the single-call path
+            f["plain_status"] = plain_fail.get(f["index"], 0)
+        records.append({"rate": rate, "requests": count, "failures": failures,
                         "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
                                    "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
                                    "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],
@@ -346,6 +373,8 @@ def main():
                     help="selection (default): the benchmark line; batch / serve: the batched and "
                          "served workloads, printed as their own JSON lines")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch workload: tune the small-size buckets before planning")
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])

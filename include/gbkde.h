@@ -399,6 +399,33 @@ int kde_lscv_noalloc(const void* x_dev, int dtype, int64_t n, int d, const kde_g
                      const kde_opts* opts, void* stream, double* g_host, double* h_host,
                      kde_result* out);
 
+/* ------------------------------------------------------------ autotuner */
+
+#define KDE_TUNE_LATENCY 0    /* one dataset alone on the GPU                    */
+#define KDE_TUNE_THROUGHPUT 1 /* the dataset replicated until a launch fills the GPU */
+
+/* Times the LSCV pair kernel for every candidate geometry -- tile edge T in
+ * {32, 128}, bandwidths per thread B in {8, 16}, CTAs per SM in {1, 2}, tiles
+ * per item at 1x or 2x the default rule -- on the caller's samples and an
+ * n_h-point grid (CUDA events around the kernel, best of two runs), and
+ * caches the fastest per (device, mode, d, n_h bucket, n bucket; buckets are
+ * ceil(log2)).  From then on every entry point of this process uses the
+ * cached geometry for options the caller leaves at 0 (throughput entries
+ * first).  best receives the winner, best_evals_per_s its rate.  Needs a
+ * workspace large enough for the candidates (kde_batch_workspace_size of the
+ * replicated dataset); candidates that do not fit are skipped.  Synchronises
+ * the stream.  Errors: KDE_EINVAL, KDE_ENOMEM (no candidate fits), KDE_ECUDA. */
+int kde_autotune(const void* x_dev, int dtype, int64_t n, int d, int n_h, int mode, void* ws,
+                 size_t ws_bytes, void* stream, kde_opts* best, double* best_evals_per_s);
+
+/* Forget every cached tuning of this process. */
+int kde_autotune_clear(void);
+
+/* Write / read the tuning cache as text, one line per entry:
+ * device mode d nh_bucket n_bucket tile bw ctas_per_sm k_scale evals_per_s. */
+int kde_autotune_save(const char* path);
+int kde_autotune_load(const char* path);
+
 /* ------------------------------------------------------- measurement aids */
 
 /* Kernel timing hook for the calling thread.  When set (non-NULL cudaEvent_t

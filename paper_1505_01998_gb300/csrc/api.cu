@@ -23,6 +23,8 @@ static cudaError_t mark(int k, cudaStream_t st) {
   return t_ev[k] ? cudaEventRecord(t_ev[k], st) : cudaSuccess;
 }
 
+cudaError_t mark_event(int k, cudaStream_t st) { return mark(k, st); }
+
 int fail(int status, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -83,6 +85,20 @@ int check_warp_roles(int T) {
 
 // Geometry of one selection.  Deterministic in (n, d, n_h, opts, SM count).
 int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g) {
+  // Options left at 0 take the autotuner's cached choice for this device,
+  // dimension and size bucket (throughput tuning first), else the fixed rules.
+  kde_opts eff{};
+  if (o) eff = *o;
+  int kscale = 1;
+  kde_opts t;
+  if (n_h > 0 && (!eff.tile || !eff.bw_per_thread || !eff.ctas_per_sm || !eff.tiles_per_item) &&
+      (tuned_lookup(1, d, n_h, n, &t) || tuned_lookup(0, d, n_h, n, &t))) {
+    if (!eff.tile) eff.tile = t.tile;
+    if (!eff.bw_per_thread) eff.bw_per_thread = t.bw_per_thread;
+    if (!eff.ctas_per_sm) eff.ctas_per_sm = t.ctas_per_sm;
+    if (!eff.tiles_per_item) kscale = -t.tiles_per_item;
+  }
+  o = &eff;
   memset(g, 0, sizeof(*g));
   g->n = n;
   g->d = d;
@@ -105,7 +121,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
     g->K = o->tiles_per_item;
   } else {
     const int64_t target = 4 * (int64_t)g->ctas;
-    g->K = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
+    g->K = (int)std::min<int64_t>(4096, kscale * std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
   }
   g->rows = (g->tiles + g->K - 1) / g->K;
   g->items = g->rows * g->G;

@@ -241,11 +241,13 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
   BK(cudaMemcpyAsync(ws, p->pin_in, p->staged, cudaMemcpyHostToDevice, st));
   BK(launch_prep(ds, n, nullptr, st));
   size_t k = 0;
+  BK(mark_event(0, st));
   for (auto& G : p->lscv_groups) {
     Phase ph{ds, offs + k * (n + 1), nullptr, n, 0, G.total};
     BK(launch_lscv(ph, G.d, G.B, G.R, G.kahan, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, ctas)), st));
     ++k;
   }
+  BK(mark_event(1, st));
   const size_t k_psi = k;
   const PsiCoef c6 = psi_coef(6), c4 = psi_coef(4);
   for (size_t i = 0; i < p->psi_groups.size(); ++i) {

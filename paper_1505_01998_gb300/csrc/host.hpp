@@ -38,4 +38,15 @@ int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h);
 DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsigned char* ws);
 PsiCoef psi_coef(int r);
 
+// Records the caller's timing event k (kde_set_kernel_events) on `st`, if set.
+cudaError_t mark_event(int k, cudaStream_t st);
+
+// Cached autotuning of the LSCV geometry (mode 0 latency, 1 throughput);
+// out->tiles_per_item holds minus the multiple of the default K rule.
+bool tuned_lookup(int mode, int d, int n_h, int64_t n, kde_opts* out);
+
+// Batch machinery shared with the autotuner (batch.cu).
+int batch_run(kde_batch_plan* p, void* ws, size_t ws_bytes, cudaStream_t st, bool use_graph);
+void batch_free(kde_batch_plan* p);
+
 }  // namespace gbkde

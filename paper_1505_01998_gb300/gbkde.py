@@ -113,8 +113,41 @@ SIGNATURES = {
     "kde_lscv_noalloc": (_I, [_P, _I, _L, _I, ctypes.POINTER(kde_grid), ctypes.POINTER(kde_opts), _P,
                               _DP, _DP, ctypes.POINTER(kde_result)]),
     "kde_lscv_logdet": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
+    "kde_autotune": (_I, [_P, _I, _L, _I, _I, _I, _P, _S, _P, ctypes.POINTER(kde_opts), _DP]),
+    "kde_autotune_clear": (_I, []),
+    "kde_autotune_save": (_I, [ctypes.c_char_p]),
+    "kde_autotune_load": (_I, [ctypes.c_char_p]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
 }
+
+
+KDE_TUNE_LATENCY, KDE_TUNE_THROUGHPUT = 0, 1
+
+
+def kde_autotune(x, n_h: int, mode: int = KDE_TUNE_THROUGHPUT, ws=None, stream=None):
+    """Tune the LSCV geometry on device samples x; returns (kde_opts, evals/s).
+    The winner is cached and used by later calls that leave options at 0."""
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        ws = workspace(1 << 30, x.device)
+    wp, wn = _ws(ws)
+    best = kde_opts()
+    rate = np.zeros(1)
+    _check(lib().kde_autotune(ptr, dt, n, d, int(n_h), int(mode), wp, wn, _stream_handle(stream),
+                              ctypes.byref(best), _dp(rate)))
+    return best, float(rate[0])
+
+
+def kde_autotune_clear():
+    _check(lib().kde_autotune_clear())
+
+
+def kde_autotune_save(path: str):
+    _check(lib().kde_autotune_save(str(path).encode()))
+
+
+def kde_autotune_load(path: str):
+    _check(lib().kde_autotune_load(str(path).encode()))
 
 
 def kde_lscv_logdet(x, ws=None, stream=None) -> float:

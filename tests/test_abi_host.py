@@ -161,3 +161,17 @@ def test_oracle_and_library_share_no_code():
                 src = open(os.path.join(dp, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "kde_oracle" not in src, f
+
+
+def test_autotune_cache_text_roundtrip(kde, tmp_path):
+    p = tmp_path / "cache.txt"
+    p.write_text("# header\nSomeGPU/152 1 1 7 14 128 16 2 1 9.1e12\nbad line\nSomeGPU/152 0 2 8 16 32 8 1 2 1e12\n")
+    kde.kde_autotune_clear()
+    kde.kde_autotune_load(p)
+    q = tmp_path / "out.txt"
+    kde.kde_autotune_save(q)
+    lines = [l for l in q.read_text().splitlines() if not l.startswith("#")]
+    assert len(lines) == 2 and any(l.startswith("SomeGPU/152 1 1 7 14 128 16 2 1") for l in lines)
+    kde.kde_autotune_clear()
+    with pytest.raises(kde.KdeError):
+        kde.kde_autotune_load(tmp_path / "missing.txt")
