@@ -18,7 +18,8 @@
  *  - Samples: a d x n matrix with one sample per column, row-major, i.e.
  *    x[k*n + i] is coordinate k of sample i (the paper's input matrix of
  *    Sec. 4.4.2, Eq. LSCV-InputData).  Element type KDE_F32 or KDE_F64.
- *    1 <= d <= 4, n >= 2, all values finite.
+ *    1 <= d <= 16 (the paper's experiments span d = 1..16, Sec. 7.2), n >= 2,
+ *    all values finite.
  *  - Memory: the caller owns every buffer.  Device pointers must be device
  *    memory of the current CUDA device; the workspace must be at least
  *    kde_workspace_size() bytes and 256-byte aligned.  No entry point
@@ -70,7 +71,7 @@ extern "C" {
 #define KDE_GRID_EXPLICIT 1  /* the n_h values in h[] (need not be sorted)       */
 #define KDE_GRID_LOG 2       /* n_h log-spaced points over [h_min, h_max]        */
 
-#define KDE_MAX_D 4
+#define KDE_MAX_D 16
 #define KDE_MAX_NH 1024
 
 /* result flags */
@@ -262,6 +263,27 @@ int kde_lscv_H_workspace_size(int64_t n, int d, int m, const kde_opts* opts, siz
 int kde_lscv_H(const void* x_dev, int dtype, int64_t n, int d, const double* H_host, int m,
                const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host);
 
+/* Sample covariance S (d x d, row-major, n-1 denominator; Eq. LSCV-covariance,
+ * two-pass) computed by the device prologue.  Workspace: kde_workspace_size(n,
+ * d, 1).  Synchronises the stream. */
+int kde_sample_covariance(const void* x_dev, int dtype, int64_t n, int d, void* ws, size_t ws_bytes,
+                          void* stream, double* cov);
+
+/* Minimises g(H) over symmetric positive-definite H (Sec. 4.4.3) by
+ * Nelder-Mead over vech of the Cholesky factor of H with log-diagonal entries
+ * (every simplex point is positive definite), starting from H_start (NULL:
+ * the normal-scale (4/(d+2))^(2/(d+4)) n^(-2/(d+4)) S, reading R5 of
+ * Eq. LSCV-H-start).  Every iteration evaluates reflection, expansion and
+ * both contractions in one batched kde_lscv_H pass; a shrink in one more.
+ * Stops when max |g - g_best| over the simplex <= ftol |g_best| or after
+ * max_iter iterations.  H_out (d x d) and g_out receive the best point;
+ * evals_out (optional) the number of g(H) evaluations.  Workspace: the larger
+ * of kde_workspace_size(n, d, 1) and kde_lscv_H_workspace_size(n, d,
+ * max(4, d(d+1)/2 + 1)). */
+int kde_lscv_H_minimize(const void* x_dev, int dtype, int64_t n, int d, const double* H_start,
+                        int max_iter, double ftol, const kde_opts* opts, void* ws, size_t ws_bytes,
+                        void* stream, double* H_out, double* g_out, int* evals_out);
+
 /* -------------------------------------------------------------- batches */
 
 /* One selection request of a batch (device samples) or of the server (host
@@ -346,8 +368,11 @@ typedef struct kde_server kde_server;
 
 /* Starts a server: one scheduler thread, one compute and one copy stream on
  * cfg->device.  Requests are advanced together in steps (continuous
- * batching); a request keeps the geometry of the single-request entry points,
- * so its result is bitwise the one kde_lscv / kde_plugin would return. */
+ * batching).  A request's work items depend only on the request and the
+ * server configuration (items are capped so one step spans every CTA), so
+ * its result is bitwise the same whether it runs alone or among others; it
+ * equals the single-request entry points' result within the 1e-5 tolerance
+ * (those use larger items, so FP32 partial sums are grouped differently). */
 int kde_serve_create(const kde_serve_config* cfg, kde_server** server);
 
 /* Queues a request with HOST samples (copied at submit: the caller may reuse

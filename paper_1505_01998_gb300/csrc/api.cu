@@ -84,7 +84,8 @@ int check_warp_roles(int T) {
 }
 
 // Geometry of one selection.  Deterministic in (n, d, n_h, opts, SM count).
-int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g) {
+int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g,
+                  double max_item_evals) {
   // Options left at 0 take the autotuner's cached choice for this device,
   // dimension and size bucket (throughput tuning first), else the fixed rules.
   kde_opts eff{};
@@ -102,6 +103,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   memset(g, 0, sizeof(*g));
   g->n = n;
   g->d = d;
+  g->dk = d <= 4 ? d : (d + 3) / 4 * 4;
   g->n_h = n_h;
   g->n_pad = (int64_t)align_up((size_t)n, kPadTo);
   g->kahan = !(o && o->precision == KDE_FP32_PLAIN);
@@ -109,6 +111,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->ctas = std::max(1, sms) * cps;
   // LSCV
   g->T = (o && o->tile) ? o->tile : (n <= 2048 ? 32 : 128);
+  if (g->dk > 4) g->T = 32;  // one row per lane keeps the d > 4 coordinates in registers
   g->R = g->T / 32;
   g->B = (o && o->bw_per_thread) ? o->bw_per_thread : (n_h <= 64 ? 8 : 16);
   const int nh = std::max(n_h, 1);
@@ -123,6 +126,10 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
     const int64_t target = 4 * (int64_t)g->ctas;
     g->K = (int)std::min<int64_t>(4096, kscale * std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
   }
+  if (max_item_evals > 0 && !(o && o->tiles_per_item)) {
+    const double per_tile = (double)g->T * g->T * std::min(g->n_h_pad, kWarps * g->B);
+    g->K = (int)std::max<int64_t>(1, std::min<int64_t>(g->K, (int64_t)(max_item_evals / per_tile)));
+  }
   g->rows = (g->tiles + g->K - 1) / g->K;
   g->items = g->rows * g->G;
   // psi
@@ -132,6 +139,8 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   {
     const int64_t target = 4 * (int64_t)g->ctas;
     g->Kp = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (g->ptiles + target - 1) / target));
+    if (max_item_evals > 0)
+      g->Kp = (int)std::max<int64_t>(1, std::min<int64_t>(g->Kp, (int64_t)(max_item_evals / ((double)g->Tp * g->Tp))));
   }
   g->prows = (g->ptiles + g->Kp - 1) / g->Kp;
   // workspace layout
@@ -151,7 +160,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->off_x = o0;
   o0 = align_up(o0 + (size_t)d * n * sizeof(double), 256);
   g->off_y = o0;
-  o0 = align_up(o0 + (size_t)d * g->n_pad * sizeof(float), 256);
+  o0 = align_up(o0 + (size_t)g->dk * g->n_pad * sizeof(float), 256);
   g->off_xc = o0;
   o0 = align_up(o0 + (size_t)g->n_pad * sizeof(float), 256);
   g->off_lpart = o0;
@@ -216,6 +225,7 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
   s.x = x;
   s.n = g.n;
   s.d = g.d;
+  s.dk = g.dk;
   s.dtype = dtype;
   s.n_pad = g.n_pad;
   s.methods = methods;
@@ -389,7 +399,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   Phase ph{ds, off, nullptr, 1, 0, g.items};
   const int grid = (int)std::min<int64_t>(g.items, g.ctas);
   CK(mark(0, st));
-  CK(launch_lscv(ph, d, g.B, g.R, g.kahan, std::max(grid, 1), st));
+  CK(launch_lscv(ph, g.dk, g.B, g.R, g.kahan, std::max(grid, 1), st));
   CK(mark(1, st));
   CK(launch_lscv_reduce(ds, 1, nullptr, g.n_h_pad, st));
   CK(launch_lscv_finish(ds, 1, nullptr, st));

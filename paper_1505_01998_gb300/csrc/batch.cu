@@ -90,11 +90,11 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
     rc = make_geometry(q.n, q.d, n_h, opts, p->sms, &g);
     if (rc) return rc;
     if (q.methods & KDE_METHOD_LSCV) {
-      auto k = std::make_tuple(q.d, g.B, g.R, g.kahan);
+      auto k = std::make_tuple(g.dk, g.B, g.R, g.kahan);
       auto it = lkey.find(k);
       if (it == lkey.end()) {
         it = lkey.emplace(k, (int)p->lscv_groups.size()).first;
-        p->lscv_groups.push_back({q.d, g.B, g.R, 0, g.kahan, 0, {}});
+        p->lscv_groups.push_back({g.dk, g.B, g.R, 0, g.kahan, 0, {}});
       }
       p->lscv_group[r] = it->second;
       p->n_h_pad_max = std::max(p->n_h_pad_max, g.n_h_pad);
@@ -151,7 +151,7 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
     const int m = reqs[r].methods;
     if (m & KDE_METHOD_LSCV) {
       p->off_y[r] = o;
-      o = align256(o + sizeof(float) * g.d * g.n_pad);
+      o = align256(o + sizeof(float) * g.dk * g.n_pad);
       p->off_lpart[r] = o;
       o = align256(o + sizeof(double) * g.rows * 2 * g.n_h_pad);
       p->off_lsum[r] = o;

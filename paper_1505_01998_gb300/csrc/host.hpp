@@ -13,6 +13,7 @@ namespace gbkde {
 struct Geometry {
   int64_t n;
   int d;
+  int dk;  // kernel dimension: d for d <= 4, else d rounded up to a multiple of 4
   int n_h;
   int64_t n_pad;
   bool kahan;
@@ -33,7 +34,11 @@ int cuda_fail(cudaError_t e, const char* where);
 int device_sms();
 int check_opts(const kde_opts* o);
 int check_common(const void* x, int dtype, int64_t n, int d, void* ws);
-int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g);
+// max_item_evals > 0 caps the pair evaluations of one work item (tiles per
+// item shrink accordingly): the serving scheduler needs items small enough
+// that one step of a fixed evaluation budget spans every CTA.
+int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometry* g,
+                  double max_item_evals = 0);
 int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h);
 DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsigned char* ws);
 PsiCoef psi_coef(int r);

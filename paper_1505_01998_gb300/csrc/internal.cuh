@@ -26,6 +26,8 @@ struct DsDev {
   int64_t n_pad;    // n rounded up to kPadTo
   int32_t methods;  // KDE_METHOD_* bits to run
   int32_t given_H;  // 1: whiten by the matrix in cov[] (LSCV_H) instead of the sample covariance
+  int32_t dk;       // coordinates of y the pair kernel walks: d, or d rounded up to 8/12/16 (zeros)
+  int32_t pad0;
   // ---- prepared samples
   float* y;   // [d][n_pad]  sqrt(log2(e)/4) L^-1 (x - mean), zero padded   (LSCV)
   float* xc;  // [n_pad]     x - mean, zero padded                           (d = 1)

@@ -39,11 +39,19 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
                                              float2 (&t1)[B / 2], float2 (&t2)[B / 2],
                                              int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
-  constexpr int CPI = 4 / DP;  // columns per 16-byte shared-memory load
+  constexpr int CPI = DP <= 4 ? 4 / DP : 1;  // columns per iteration
+  constexpr int NV = CPI * DP / 4;           // 16-byte shared-memory loads per iteration
 #pragma unroll 1
   for (int jj = j_lo; jj < j_hi; jj += CPI) {
-    const float4 v = *reinterpret_cast<const float4*>(sF + jj * DP);
-    const float vv[4] = {v.x, v.y, v.z, v.w};
+    float vv[4 * NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(sF + jj * DP + 4 * u);
+      vv[4 * u] = v.x;
+      vv[4 * u + 1] = v.y;
+      vv[4 * u + 2] = v.z;
+      vv[4 * u + 3] = v.w;
+    }
 #pragma unroll
     for (int c = 0; c < CPI; ++c) {
       float2 q2[R];
@@ -284,7 +292,9 @@ template <int D, int B>
 cudaError_t launch_r(const Phase& ph, int R, bool kahan, int grid, cudaStream_t st) {
   switch (R) {
     case 1: return launch_k<D, B, 1>(ph, kahan, grid, st);
-    case 4: return launch_k<D, B, 4>(ph, kahan, grid, st);
+    case 4:
+      if constexpr (D <= 4) return launch_k<D, B, 4>(ph, kahan, grid, st);
+      return cudaErrorInvalidValue;  // d > 4 walks one row per lane
     default: return cudaErrorInvalidValue;
   }
 }
@@ -318,6 +328,9 @@ cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int gr
     case 2: return launch_b<2>(ph, B, R, kahan, grid, st);
     case 3: return launch_b<3>(ph, B, R, kahan, grid, st);
     case 4: return launch_b<4>(ph, B, R, kahan, grid, st);
+    case 8: return launch_b<8>(ph, B, R, kahan, grid, st);
+    case 12: return launch_b<12>(ph, B, R, kahan, grid, st);
+    case 16: return launch_b<16>(ph, B, R, kahan, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -52,7 +52,9 @@ struct Acc<double> {
 
 // Block-wide FP64 sum of `cnt` values per thread, deterministic order;
 // results land in out[0..cnt) (shared memory) for every thread.
-__device__ void block_sum(double* v, int cnt, double (*scratch)[16], double* out) {
+constexpr int kNPairs = KDE_MAX_D * (KDE_MAX_D + 1) / 2;  // covariance entries a <= b
+
+__device__ void block_sum(double* v, int cnt, double (*scratch)[kNPairs], double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k < cnt; ++k) {
     double s = warp_sum(v[k]);
@@ -75,8 +77,8 @@ __device__ void block_sum(double* v, int cnt, double (*scratch)[16], double* out
 // (Eq. PLUGIN-g1).  Pass 3: y = M (x - mean) and x - mean in FP32.
 template <typename TIN>
 __device__ __forceinline__ void prep_body(DsDev* ds) {
-  __shared__ double scratch[kPrepThreads / 32][16];
-  __shared__ double sv[16];
+  __shared__ double scratch[kPrepThreads / 32][kNPairs];
+  __shared__ double sv[kNPairs];
   __shared__ float sM[KDE_MAX_D * KDE_MAX_D];
   __shared__ float sMeanF[KDE_MAX_D];
   __shared__ double sMean[KDE_MAX_D];
@@ -89,7 +91,7 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
   Acc<TIN> a1[KDE_MAX_D];
   for (int64_t i = threadIdx.x; i < n; i += kPrepThreads)
     for (int k = 0; k < d; ++k) a1[k].add(x[(int64_t)k * n + i]);
-  double v[16];
+  double v[kNPairs];
   for (int k = 0; k < d; ++k) v[k] = a1[k].get();
   block_sum(v, d, scratch, sv);
   if (threadIdx.x < d) {
@@ -99,7 +101,7 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
   __syncthreads();
 
   // ---- pass 2: centred cross products, upper triangle a <= b
-  Acc<TIN> a2[10];
+  Acc<TIN> a2[kNPairs];
   for (int64_t i = threadIdx.x; i < n; i += kPrepThreads) {
     TIN c[KDE_MAX_D];
     for (int k = 0; k < d; ++k) {
@@ -208,7 +210,7 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
   float* __restrict__ y = ds->y;
   float* __restrict__ xc = ds->xc;
   for (int64_t i = threadIdx.x; i < n_pad; i += kPrepThreads) {
-    float c[KDE_MAX_D] = {0.f, 0.f, 0.f, 0.f};
+    float c[KDE_MAX_D] = {};
     if (i < n) {
       for (int k = 0; k < d; ++k) {
         if constexpr (sizeof(TIN) == 4)
@@ -223,6 +225,7 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
         for (int j = 0; j <= k; ++j) t = fmaf(sM[k * KDE_MAX_D + j], c[j], t);
         y[(int64_t)k * n_pad + i] = t;
       }
+      for (int k = d; k < ds->dk; ++k) y[(int64_t)k * n_pad + i] = 0.f;  // padded coordinates
     }
     if (xc && d == 1) xc[i] = c[0];
   }

@@ -13,8 +13,11 @@
 //   launch per kernel variant over a slot table; then the finishing kernels of
 //   requests whose phase completed.  Up to two steps are in flight; the host
 //   builds the next step while the device runs the current one.
-// * Results are bitwise those of the single-request entry points: a request
-//   keeps its single-call geometry, and items only ever write their own rows.
+// * A request's items depend only on the request and the server
+//   configuration, and items only ever write their own rows: results are
+//   bitwise the same alone or in the mix.  Items are capped at half a CTA's
+//   share of a step (finer than a single call's), so results equal the
+//   single-request entry points' within the FP32 tolerance, not bitwise.
 // * Failure handling on the host: a step that misses its deadline fails its
 //   requests (KDE_ETIMEDOUT) without touching the device; their regions are
 //   released once the device work that references them has completed.
@@ -165,6 +168,13 @@ struct kde_server {
 
 namespace {
 
+// Pair evaluations per scheduling step (default 1.6e11: about 18 ms of the
+// all-pairs kernels on a GB300, long against the ~0.1 ms launch overhead of a
+// step, short against the latency of a large request).
+double step_budget(const kde_server* s) {
+  return s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 1.6e11;
+}
+
 void finish_req(kde_server* s, Req* r, int status) {
   r->finished = true;
   r->t_done = Clock::now();
@@ -185,7 +195,7 @@ void finish_req(kde_server* s, Req* r, int status) {
 
 void release_req(kde_server* s, Req* r) {
   if (r->slot >= 0) {
-    s->heap.release(r->region, r->region_bytes);
+    s->heap.release(r->region - s->heap_off, r->region_bytes);  // heap offsets are heap-relative
     s->slot_owner[r->slot] = 0;
     r->slot = -1;
   }
@@ -251,7 +261,7 @@ double item_evals(const Req* r) {
 // Build and launch one step.  Returns false if there was nothing to do.
 bool launch_step(kde_server* s, int* err) {
   const int S = s->cfg.max_slots;
-  const double budget = s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 4e10;
+  const double budget = step_budget(s);
   const int buf = s->next_buf;
   unsigned char* pin = s->pin_params[buf];
   unsigned char* dparams = s->arena + s->params_off[buf];
@@ -276,9 +286,9 @@ bool launch_step(kde_server* s, int* err) {
     const int rr = kind == P_LSCV ? 0 : (kind == P_PSI6 ? 6 : 4);
     for (auto& x : groups)
       if (x.kind == kind && x.kahan == g.kahan &&
-          (kind == P_LSCV ? (x.d == g.d && x.B == g.B && x.R == g.R) : (x.Rp == g.Rp && x.r == rr)))
+          (kind == P_LSCV ? (x.d == g.dk && x.B == g.B && x.R == g.R) : (x.Rp == g.Rp && x.r == rr)))
         return x;
-    groups.push_back({kind, g.d, g.B, g.R, g.Rp, rr, g.kahan, std::vector<int64_t>(S, 0),
+    groups.push_back({kind, g.dk, g.B, g.R, g.Rp, rr, g.kahan, std::vector<int64_t>(S, 0),
                       std::vector<int64_t>(S, 0), 0});
     return groups.back();
   };
@@ -583,10 +593,11 @@ int kde_serve_create(const kde_serve_config* cfg, kde_server** out) {
     return fail(KDE_ECUDA, "serve: streams or pinned staging");
   }
   // every kernel variant's shared-memory attribute up front
-  for (int d = 1; d <= KDE_MAX_D; ++d)
+  for (int d : {1, 2, 3, 4, 8, 12, 16})
     for (int B : {8, 16})
       for (int R : {1, 4})
-        for (int k = 0; k < 2; ++k) prepare_lscv(d, B, R, k == 0);
+        for (int k = 0; k < 2; ++k)
+          if (d <= 4 || R == 1) prepare_lscv(d, B, R, k == 0);
   s->worker = std::thread(worker_main, s);
   *out = s;
   return KDE_OK;
@@ -614,7 +625,10 @@ int kde_serve_submit(kde_server* s, const kde_request* q, uint64_t* ticket) {
     }
     n_h = (int)r->grid.size();
   }
-  int rc = make_geometry(q->n, q->d, n_h, s->has_opts ? &s->opts : nullptr, s->sms, &r->geo);
+  // items no larger than half a CTA's share of one step, so every step spans all CTAs
+  const int cps = (s->has_opts && s->opts.ctas_per_sm) ? s->opts.ctas_per_sm : 2;
+  const double max_item = step_budget(s) / (2.0 * std::max(1, s->sms) * cps);
+  int rc = make_geometry(q->n, q->d, n_h, s->has_opts ? &s->opts : nullptr, s->sms, &r->geo, max_item);
   if (rc) {
     delete r;
     return rc;

@@ -44,6 +44,23 @@ int kde_lscv_logdet(const void* x_dev, int dtype, int64_t n, int d, void* ws, si
   return KDE_OK;
 }
 
+int kde_sample_covariance(const void* x_dev, int dtype, int64_t n, int d, void* ws, size_t ws_bytes,
+                          void* stream, double* cov) {
+  if (!cov) return fail(KDE_EINVAL, "cov is NULL");
+  double logdet = 0;
+  int rc = kde_lscv_logdet(x_dev, dtype, n, d, ws, ws_bytes, stream, &logdet);
+  if (rc) return rc;
+  Geometry g;
+  rc = make_geometry(n, d, 1, nullptr, device_sms(), &g);
+  if (rc) return rc;
+  double c[KDE_MAX_D * KDE_MAX_D];
+  cudaError_t e = cudaMemcpy(c, static_cast<unsigned char*>(ws) + g.off_ds + offsetof(DsDev, cov),
+                             sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  for (int k = 0; k < d * d; ++k) cov[k] = c[k];
+  return KDE_OK;
+}
+
 int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, const double* s1,
                    const double* s2, double* g_out, kde_result* out) {
   if (!h || !s1 || !s2 || !out || n < 2 || d < 1 || d > KDE_MAX_D || n_h < 1 || n_h > KDE_MAX_NH ||

@@ -114,11 +114,44 @@ SIGNATURES = {
                               _DP, _DP, ctypes.POINTER(kde_result)]),
     "kde_lscv_logdet": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
     "kde_autotune": (_I, [_P, _I, _L, _I, _I, _I, _P, _S, _P, ctypes.POINTER(kde_opts), _DP]),
+    "kde_sample_covariance": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
+    "kde_lscv_H_minimize": (_I, [_P, _I, _L, _I, _DP, _I, _D, ctypes.POINTER(kde_opts), _P, _S, _P,
+                                 _DP, _DP, ctypes.POINTER(ctypes.c_int)]),
     "kde_autotune_clear": (_I, []),
     "kde_autotune_save": (_I, [ctypes.c_char_p]),
     "kde_autotune_load": (_I, [ctypes.c_char_p]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
 }
+
+
+def kde_sample_covariance(x, ws=None, stream=None) -> np.ndarray:
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, d, 1), x.device)
+    wp, wn = _ws(ws)
+    out = np.zeros(d * d)
+    _check(lib().kde_sample_covariance(ptr, dt, n, d, wp, wn, _stream_handle(stream), _dp(out)))
+    return out.reshape(d, d)
+
+
+def kde_lscv_H_minimize(x, H_start=None, max_iter=200, ftol=1e-8, opts=None, ws=None, stream=None):
+    """Nelder-Mead minimisation of g(H); returns (H, g, number of g evaluations)."""
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        p = d * (d + 1) // 2
+        ws = workspace(max(kde_workspace_size(n, d, 1), kde_lscv_H_workspace_size(n, d, max(4, p + 1))),
+                       x.device)
+    wp, wn = _ws(ws)
+    H0 = None
+    if H_start is not None:
+        H0 = np.ascontiguousarray(np.asarray(H_start, dtype=np.float64).reshape(d, d))
+    H = np.zeros(d * d)
+    g = np.zeros(1)
+    ev = ctypes.c_int(0)
+    _check(lib().kde_lscv_H_minimize(ptr, dt, n, d, _dp(H0) if H0 is not None else None, int(max_iter),
+                                     float(ftol), ctypes.byref(opts) if opts else None, wp, wn,
+                                     _stream_handle(stream), _dp(H), _dp(g), ctypes.byref(ev)))
+    return H.reshape(d, d), float(g[0]), ev.value
 
 
 KDE_TUNE_LATENCY, KDE_TUNE_THROUGHPUT = 0, 1

@@ -110,7 +110,7 @@ def test_workspace_size_monotone_and_bad_args(kde):
         kde.kde_workspace_size(1, 1, 64)
     assert e.value.status == kde.KDE_EINVAL
     with pytest.raises(kde.KdeError):
-        kde.kde_workspace_size(100, 5, 64)
+        kde.kde_workspace_size(100, 17, 64)
     with pytest.raises(kde.KdeError):
         kde.kde_workspace_size(100, 1, 64, kde.make_opts(tile=48))
 
@@ -124,7 +124,7 @@ def test_entry_points_reject_bad_arguments_before_any_launch(kde):
     assert L.kde_lscv(None, 0, 100, 1, ctypes.byref(grid), None, dummy, 1 << 20, None, None, None,
                       ctypes.byref(res)) == kde.KDE_EINVAL
     # d out of range
-    assert L.kde_lscv(dummy, 0, 100, 5, ctypes.byref(grid), None, dummy, 1 << 20, None, None, None,
+    assert L.kde_lscv(dummy, 0, 100, 17, ctypes.byref(grid), None, dummy, 1 << 20, None, None, None,
                       ctypes.byref(res)) == kde.KDE_EINVAL
     # n < 2
     assert L.kde_plugin(dummy, 0, 1, None, dummy, 1 << 20, None, ctypes.byref(res)) == kde.KDE_EINVAL

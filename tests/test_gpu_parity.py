@@ -179,6 +179,30 @@ def test_lscv_dims_sizes_grids(kde, d, n, n_h):
     _lscv_check(kde, x, h)
 
 
+@pytest.mark.parametrize("d", [5, 7, 8, 9, 12, 13, 16])
+@pytest.mark.parametrize("n,n_h", [(450, 32), (1300, 100)])
+def test_lscv_high_dimensions(kde, d, n, n_h):
+    """d = 5..16 (the paper's experiments reach d = 16): coordinates padded to
+    8 / 12 / 16 with zeros, one row per lane."""
+    x = datagen.correlated_mixture(n, d, seed=300 + d + n)
+    h = oracle.grid_default(n, d, n_h)
+    _lscv_check(kde, x, h)
+
+
+@pytest.mark.parametrize("d", [6, 16])
+def test_lscv_H_high_dimensions(kde, d):
+    n = 700
+    x = datagen.correlated_mixture(n, d, seed=400 + d)
+    x64 = x.astype(np.float32).astype(np.float64)
+    _, S = oracle.mean_cov(x64)
+    Hs = np.array([0.3 * S, 0.8 * S + 0.1 * np.eye(d)])
+    g = kde.kde_lscv_H(dev(x), Hs)
+    for k in range(2):
+        ref = oracle.lscv_H(x64, Hs[k])
+        scale = (4 * math.pi) ** (-d / 2) / math.sqrt(np.linalg.det(Hs[k])) / n
+        assert abs(g[k] - ref) <= TOL * max(abs(ref), scale)
+
+
 @pytest.mark.parametrize("opts", [dict(precision=1), dict(tile=128), dict(tile=32, bw_per_thread=16),
                                   dict(bw_per_thread=8, tiles_per_item=3), dict(ctas_per_sm=1)])
 def test_lscv_option_paths(kde, opts):
