@@ -357,6 +357,75 @@ def run_serve(args):
     return 0
 
 
+def run_paper(args):
+    """The largest instances of the paper's experiments (Sec. 7.2, Table 1),
+    timed end to end (host samples in, results out, as the paper timed its
+    GPU runs) and with samples resident; the paper's GTX 480 times are quoted
+    as context."""
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    out = []
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return 1e3 * statistics.median(ts)
+
+    # PLUGIN, n = 32768, d = 1 (paper: 87.9 ms)
+    x = datagen.mixture_1d(32768, seed=7).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    ws = gbkde.workspace(gbkde.kde_workspace_size(32768, 1, 0))
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    e2e = timed(lambda: gbkde.kde_plugin_host(xh, None, ws, stream), args.steps)
+    res = timed(lambda: gbkde.kde_plugin(xd, None, ws, stream), args.steps)
+    out.append({"instance": "PLUGIN n=32768 d=1", "e2e_ms": e2e, "resident_ms": res,
+                "paper_gpu_ms": 87.9, "paper_sse_ms": 1442.3, "paper_seq_ms": 47435.3,
+                "speedup_vs_paper_gpu_e2e": 87.9 / e2e})
+    # LSCV_h, n = 1024, d = 16, 150 bandwidths (paper: 14.7 ms)
+    x = datagen.correlated_mixture(1024, 16, seed=8)
+    xd = torch.from_numpy(x).cuda()
+    grid = gbkde.make_grid(n_h=150)[0]
+    ws = gbkde.workspace(gbkde.kde_workspace_size(1024, 16, 150))
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    e2e = timed(lambda: gbkde.kde_lscv_host(xh, grid, None, ws, stream), args.steps)
+    res = timed(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), args.steps)
+    out.append({"instance": "LSCV_h n=1024 d=16 n_h=150", "e2e_ms": e2e, "resident_ms": res,
+                "paper_gpu_ms": 14.7, "paper_sse_ms": 344.1, "paper_seq_ms": 8283.6,
+                "speedup_vs_paper_gpu_e2e": 14.7 / e2e})
+    # LSCV_H, one g(H), n = 16384, d = 16 (paper: 184.2 ms)
+    x = datagen.correlated_mixture(16384, 16, seed=9)
+    xd = torch.from_numpy(x).cuda()
+    S = gbkde.kde_sample_covariance(xd)
+    H = (0.5 * S)[None]
+    ws = gbkde.workspace(gbkde.kde_lscv_H_workspace_size(16384, 16, 1))
+    xh = torch.from_numpy(x).pin_memory()
+
+    def lscv_H_e2e():
+        xd2 = xh.cuda(non_blocking=True)
+        gbkde.kde_lscv_H(xd2, H, None, ws, stream)
+
+    e2e = timed(lscv_H_e2e, args.steps)
+    res = timed(lambda: gbkde.kde_lscv_H(xd, H, None, ws, stream), args.steps)
+    out.append({"instance": "LSCV_H g(H) n=16384 d=16", "e2e_ms": e2e, "resident_ms": res,
+                "paper_gpu_ms": 184.2, "paper_sse_ms": 2320.0, "paper_seq_ms": 53258.8,
+                "speedup_vs_paper_gpu_e2e": 184.2 / e2e})
+    print(json.dumps({"workload": "paper_table1", "note": "paper times: GTX 480 / Core i7 SSE / "
+                      "sequential C, FP32, transfers included (Sec. 7.1-7.3, Table 1)",
+                      "instances": out}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -369,7 +438,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=N,
                     help="sample count (default 65536; smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=("selection", "batch", "serve"), default="selection",
+    ap.add_argument("--workload", choices=("selection", "batch", "serve", "paper"), default="selection",
                     help="selection (default): the benchmark line; batch / serve: the batched and "
                          "served workloads, printed as their own JSON lines")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -387,6 +456,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "paper":
+        return run_paper(args)
     return run_gpu(args, world, rank, local)
 
 

@@ -15,9 +15,10 @@
 //   builds the next step while the device runs the current one.
 // * A request's items depend only on the request and the server
 //   configuration, and items only ever write their own rows: results are
-//   bitwise the same alone or in the mix.  Items are capped at half a CTA's
-//   share of a step (finer than a single call's), so results equal the
+//   bitwise the same alone or in the mix.  Items are capped at a sixth of a
+//   CTA's share of a step (finer than a single call's), so results equal the
 //   single-request entry points' within the FP32 tolerance, not bitwise.
+//   The variant launches of a step run on side streams, so their tails overlap.
 // * Failure handling on the host: a step that misses its deadline fails its
 //   requests (KDE_ETIMEDOUT) without touching the device; their regions are
 //   released once the device work that references them has completed.
@@ -122,6 +123,7 @@ struct Req {
 };
 
 constexpr int kMaxSlots = 1024;
+constexpr int kSideStreams = 4;  // concurrent variant launches within a step
 
 struct Step {
   cudaEvent_t done = nullptr;
@@ -143,6 +145,8 @@ struct kde_server {
   size_t table_off = 0, params_off[2] = {0, 0}, params_bytes = 0, heap_off = 0;
   Arena heap;
   cudaStream_t comp = nullptr, copy = nullptr;
+  cudaStream_t side[kSideStreams] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
   unsigned char* pin_params[2] = {nullptr, nullptr};
   unsigned char* pin_table[2] = {nullptr, nullptr};
   std::mutex mu;
@@ -209,7 +213,7 @@ void release_req(kde_server* s, Req* r) {
 
 // Bytes of the step parameter block: ids lists + per-group (off, base) arrays.
 size_t params_block_bytes(int slots) {
-  const size_t groups = 16;  // LSCV variants (d x B x R x precision) + psi variants, bounded
+  const size_t groups = 64;  // LSCV variants (d x B x R x precision) + psi variants, bounded
   return (size_t)(4 + 2 * groups) * (slots + 1) * sizeof(int64_t) + 4 * slots * sizeof(int) + 4096;
 }
 
@@ -420,17 +424,31 @@ bool launch_step(kde_server* s, int* err) {
   ck(launch_prep(table, n_prep, d_prep, cs), "prep");
   const int ctas = std::max(1, s->sms) * ((s->has_opts && s->opts.ctas_per_sm) ? s->opts.ctas_per_sm : 2);
   const PsiCoef c6 = psi_coef(6), c4 = psi_coef(4);
+  // One persistent launch per kernel variant, forked over side streams so
+  // that the tail of one launch overlaps the work of the others; joined back
+  // before the finishing kernels.
+  ck(cudaEventRecord(s->ev_fork, cs), "fork");
+  bool forked[kSideStreams] = {};
   for (size_t i = 0; i < groups.size(); ++i) {
     const G& g = groups[i];
     if (!g.total) continue;
+    const int k = (int)(i % kSideStreams);
+    cudaStream_t ss = s->side[k];
+    if (!forked[k]) ck(cudaStreamWaitEvent(ss, s->ev_fork, 0), "fork wait");
+    forked[k] = true;
     Phase ph{table, reinterpret_cast<const int64_t*>(dparams + goff[i].first),
              reinterpret_cast<const int64_t*>(dparams + goff[i].second), S, 0, g.total};
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total, ctas));
     if (g.kind == P_LSCV)
-      ck(launch_lscv(ph, g.d, g.B, g.R, g.kahan, grid, cs), "lscv");
+      ck(launch_lscv(ph, g.d, g.B, g.R, g.kahan, grid, ss), "lscv");
     else
-      ck(launch_psi(ph, g.r, g.Rp, g.kahan, g.r == 6 ? c6 : c4, grid, cs), "psi");
+      ck(launch_psi(ph, g.r, g.Rp, g.kahan, g.r == 6 ? c6 : c4, grid, ss), "psi");
   }
+  for (int k = 0; k < kSideStreams; ++k)
+    if (forked[k]) {
+      ck(cudaEventRecord(s->ev_join[k], s->side[k]), "join");
+      ck(cudaStreamWaitEvent(cs, s->ev_join[k], 0), "join wait");
+    }
   int nh_max = 0;
   for (int k = 0; k < n_lfin; ++k) nh_max = std::max(nh_max, s->reqs[s->slot_owner[lfin_ids[k]]]->geo.n_h_pad);
   ck(launch_lscv_reduce(table, n_lfin, d_lfin, nh_max, cs), "lscv reduce");
@@ -588,6 +606,10 @@ int kde_serve_create(const kde_serve_config* cfg, kde_server** out) {
   for (int b = 0; b < 2 && ok; ++b)
     ok = cudaMallocHost(&s->pin_params[b], s->params_bytes) == cudaSuccess &&
          cudaMallocHost(&s->pin_table[b], sizeof(DsDev) * S) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < kSideStreams && ok; ++k)
+    ok = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     kde_serve_destroy(s);
     return fail(KDE_ECUDA, "serve: streams or pinned staging");
@@ -625,9 +647,10 @@ int kde_serve_submit(kde_server* s, const kde_request* q, uint64_t* ticket) {
     }
     n_h = (int)r->grid.size();
   }
-  // items no larger than half a CTA's share of one step, so every step spans all CTAs
+  // items of at most a sixth of a CTA's share of one step: every step spans all
+  // CTAs and launch tails stay short
   const int cps = (s->has_opts && s->opts.ctas_per_sm) ? s->opts.ctas_per_sm : 2;
-  const double max_item = step_budget(s) / (2.0 * std::max(1, s->sms) * cps);
+  const double max_item = step_budget(s) / (6.0 * std::max(1, s->sms) * cps);
   int rc = make_geometry(q->n, q->d, n_h, s->has_opts ? &s->opts : nullptr, s->sms, &r->geo, max_item);
   if (rc) {
     delete r;
@@ -775,6 +798,11 @@ int kde_serve_destroy(kde_server* s) {
   }
   if (s->comp) cudaStreamDestroy(s->comp);
   if (s->copy) cudaStreamDestroy(s->copy);
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (s->side[k]) cudaStreamDestroy(s->side[k]);
+    if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   delete s;
   return KDE_OK;
 }
