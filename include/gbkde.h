@@ -100,7 +100,14 @@ typedef struct kde_opts {
   int bw_per_thread;  /* LSCV bandwidths per thread B: 8 or 16                  */
   int tiles_per_item; /* tiles per work item K (1 .. 4096)                      */
   int ctas_per_sm;    /* resident CTAs per SM of the persistent pair kernels    */
+  int cv;             /* LSCV weights: KDE_CV_PAPER (0) or KDE_CV_LOO           */
 } kde_opts;
+
+/* LSCV objective weights.  KDE_CV_PAPER: n^-2 on the pair sum as printed in
+ * Eq. LSCV-gh (reading R2).  KDE_CV_LOO: exact leave-one-out cross-validation,
+ * g = h^-d A [n^-1 + 2 n^-2 S1 - 2^(2+d/2) S2 / (n (n-1))]. */
+#define KDE_CV_PAPER 0
+#define KDE_CV_LOO 1
 
 /* Result of one selection.  Fields that do not apply are 0. */
 typedef struct kde_result {
@@ -216,6 +223,18 @@ int kde_lscv_logdet(const void* x_dev, int dtype, int64_t n, int d, void* ws, si
  * NULL; out receives argmin, h, g_min, flags. */
 int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, const double* s1,
                    const double* s2, double* g_out, kde_result* out);
+
+/* Bracketing search for argmin g(h) over [h_lo, h_hi] (<= 0: Z(h0), Eq.
+ * LSCV-Zh0): the golden-section alternative to the dense grid named in
+ * Sec. 4.4.2, evaluated 8 interior points per round (log-spaced) in one pass;
+ * the bracket becomes the neighbours of the best point (log-width x 2/9 per
+ * round) until it is within 2 rel_tol (log) or after max_rounds.  out->h and
+ * out->g_min hold the best evaluated point (a local minimum if g is not
+ * unimodal); rounds_out (optional) the rounds taken.  Workspace:
+ * kde_workspace_size(n, d, 8).  Synchronises the stream every round. */
+int kde_lscv_search(const void* x_dev, int dtype, int64_t n, int d, double h_lo, double h_hi,
+                    double rel_tol, int max_rounds, const kde_opts* opts, void* ws, size_t ws_bytes,
+                    void* stream, kde_result* out, int* rounds_out);
 
 /* ------------------------------------------------------------- PLUGIN */
 

@@ -79,6 +79,8 @@ def _load():
             "kdeo_lscv_sums_block": (I, [P, L, I, P, I, L, L, L, L, P, P, P, I]),
             "kdeo_lscv_h": (I, [P, L, I, P, I, P, P, P, P, I]),
             "kdeo_lscv_H": (I, [P, L, I, P, P, I]),
+            "kdeo_lscv_h_loo": (I, [P, L, I, P, I, P, I]),
+            "kdeo_lscv_search": (I, [P, L, I, D, D, I, D, I, I, P, P, P, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -229,6 +231,33 @@ def lscv_h(x, h, threads: int = 0):
     if rc:
         raise ValueError(f"oracle lscv_h status {rc}")
     return {"g": g, "argmin": am.value, "s_kk": skk, "s_k": sk}
+
+
+def lscv_h_loo(x, h, threads: int = 0) -> np.ndarray:
+    """Exact leave-one-out g(h) on the grid."""
+    a = _as2d(x)
+    d, n = a.shape
+    hh = np.ascontiguousarray(np.asarray(h, dtype=np.float64).ravel())
+    g = np.zeros(hh.size)
+    rc = _load().kdeo_lscv_h_loo(_p(a), n, d, _p(hh), hh.size, _p(g), threads)
+    if rc:
+        raise ValueError(f"oracle lscv_h_loo status {rc}")
+    return g
+
+
+def lscv_search(x, a: float, b: float, P: int = 8, rel_tol: float = 1e-4, max_rounds: int = 30,
+                loo: bool = False, threads: int = 0):
+    """Bracketing search for argmin g(h) over [a, b]: (h, g, rounds)."""
+    arr = _as2d(x)
+    d, n = arr.shape
+    hb, gb = np.zeros(1), np.zeros(1)
+    rounds = ctypes.c_int(0)
+    rc = _load().kdeo_lscv_search(_p(arr), n, d, float(a), float(b), int(P), float(rel_tol),
+                                  int(max_rounds), int(bool(loo)), _p(hb), _p(gb),
+                                  ctypes.byref(rounds), threads)
+    if rc:
+        raise ValueError(f"oracle lscv_search status {rc}")
+    return float(hb[0]), float(gb[0]), rounds.value
 
 
 def lscv_H(x, H, threads: int = 0) -> float:

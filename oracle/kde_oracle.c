@@ -417,6 +417,79 @@ int kdeo_lscv_h(const double *x, long n, int d, const double *h, int n_h, double
   return KDEO_OK;
 }
 
+/* Exact leave-one-out variant of the objective (the paper's Eq. LSCV-gh uses
+ * n^-2 on the pair sum, reading R2; exact leave-one-out cross-validation uses
+ * 1/(n(n-1)) on the K term):
+ *   g_loo(h) = int fhat^2 - (2/n) sum_i fhat_{-i}(X_i)
+ *            = n^-2 [n (K*K)_H(0) + 2 sum_{i<j} (K*K)_H(v)] - 4/(n(n-1)) sum_{i<j} K_H(v)
+ * with H = h^2 Sigma, (K*K)_H(v) = h^-d (K*K)(v/h) and K_H(v) = h^-d K(v/h). */
+int kdeo_lscv_h_loo(const double *x, long n, int d, const double *h, int n_h, double *g,
+                    int threads) {
+  double *skk = (double *)malloc(sizeof(double) * (size_t)n_h);
+  double *sk = (double *)malloc(sizeof(double) * (size_t)n_h);
+  double *mean = (double *)malloc(sizeof(double) * (size_t)d);
+  double *cov = (double *)malloc(sizeof(double) * (size_t)(d * d));
+  double *icov = (double *)malloc(sizeof(double) * (size_t)(d * d));
+  if (!skk || !sk || !mean || !cov || !icov) return KDEO_ENOMEM;
+  int rc = kdeo_lscv_sums_block(x, n, d, h, n_h, 0, n, 0, n, skk, sk, NULL, threads);
+  if (rc == KDEO_OK) {
+    kdeo_mean_cov(x, n, d, mean, cov);
+    double det;
+    kdeo_invert(cov, d, icov, &det);
+    double ckk = pow(4.0 * KDEO_PI, -0.5 * d) / sqrt(det);
+    double ck = pow(2.0 * KDEO_PI, -0.5 * d) / sqrt(det);
+    double dn = (double)n;
+    for (int k = 0; k < n_h; ++k) {
+      double hd = pow(h[k], -(double)d);
+      double intf2 = (dn * hd * ckk + 2.0 * hd * ckk * skk[k]) / (dn * dn);
+      double loo = 4.0 / (dn * (dn - 1.0)) * hd * ck * sk[k];
+      g[k] = intf2 - loo;
+    }
+  }
+  free(skk), free(sk), free(mean), free(cov), free(icov);
+  return rc;
+}
+
+/* Bracketing search for the minimum of g(h) (the golden-section alternative
+ * to the dense grid named in Sec. 4.4.2 and Sec. 6.2, evaluated P points at a
+ * time): in round t the bracket [a, b] holds P interior points log-spaced at
+ * a (b/a)^(k/(P+1)), k = 1..P; the bracket becomes the neighbours of the
+ * first-index minimum among them (a and b stand for k = 0 and k = P+1).
+ * Stops when log(b/a) <= 2 rel_tol or after max_rounds.  Returns the best
+ * evaluated h (and g there); loo selects the exact leave-one-out objective. */
+int kdeo_lscv_search(const double *x, long n, int d, double a, double b, int P, double rel_tol,
+                     int max_rounds, int loo, double *h_best, double *g_best, int *rounds,
+                     int threads) {
+  double *u = (double *)malloc(sizeof(double) * (size_t)(P + 2));
+  double *gu = (double *)malloc(sizeof(double) * (size_t)P);
+  if (!u || !gu) return KDEO_ENOMEM;
+  double hb = 0.0, gb = INFINITY;
+  int t = 0;
+  for (; t < max_rounds && log(b / a) > 2.0 * rel_tol; ++t) {
+    for (int k = 0; k <= P + 1; ++k) u[k] = a * exp(log(b / a) * (double)k / (double)(P + 1));
+    int rc = loo ? kdeo_lscv_h_loo(x, n, d, u + 1, P, gu, threads)
+                 : kdeo_lscv_h(x, n, d, u + 1, P, gu, NULL, NULL, NULL, threads);
+    if (rc != KDEO_OK) {
+      free(u), free(gu);
+      return rc;
+    }
+    int km = 0;
+    for (int k = 1; k < P; ++k)
+      if (gu[k] < gu[km]) km = k;
+    if (gu[km] < gb) {
+      gb = gu[km];
+      hb = u[km + 1];
+    }
+    a = u[km];
+    b = u[km + 2];
+  }
+  *h_best = hb;
+  *g_best = gb;
+  if (rounds) *rounds = t;
+  free(u), free(gu);
+  return KDEO_OK;
+}
+
 /* ------------------------------------------------------------- LSCV_H */
 
 /* The LSCV_H objective g(H) for one symmetric positive-definite bandwidth

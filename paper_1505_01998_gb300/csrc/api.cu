@@ -59,6 +59,7 @@ int check_opts(const kde_opts* o) {
     return fail(KDE_EINVAL, "opts.tiles_per_item %d invalid", o->tiles_per_item);
   if (o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
     return fail(KDE_EINVAL, "opts.ctas_per_sm %d invalid", o->ctas_per_sm);
+  if (o->cv != KDE_CV_PAPER && o->cv != KDE_CV_LOO) return fail(KDE_EINVAL, "opts.cv %d invalid", o->cv);
   return KDE_OK;
 }
 
@@ -107,6 +108,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->n_h = n_h;
   g->n_pad = (int64_t)align_up((size_t)n, kPadTo);
   g->kahan = !(o && o->precision == KDE_FP32_PLAIN);
+  g->cv_loo = (o && o->cv == KDE_CV_LOO) ? 1 : 0;
   const int cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : 2;
   g->ctas = std::max(1, sms) * cps;
   // LSCV
@@ -226,6 +228,7 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
   s.n = g.n;
   s.d = g.d;
   s.dk = g.dk;
+  s.cv_loo = g.cv_loo;
   s.dtype = dtype;
   s.n_pad = g.n_pad;
   s.methods = methods;

@@ -17,6 +17,7 @@ struct Geometry {
   int n_h;
   int64_t n_pad;
   bool kahan;
+  int cv_loo;  // KDE_CV_LOO requested
   int ctas;  // persistent CTAs of the pair kernels
   // LSCV: tile T = 32 R, B bandwidths per thread, K tiles per item
   int T, R, B, n_h_pad, n_chunks, G, K;

@@ -27,7 +27,7 @@ struct DsDev {
   int32_t methods;  // KDE_METHOD_* bits to run
   int32_t given_H;  // 1: whiten by the matrix in cov[] (LSCV_H) instead of the sample covariance
   int32_t dk;       // coordinates of y the pair kernel walks: d, or d rounded up to 8/12/16 (zeros)
-  int32_t pad0;
+  int32_t cv_loo;   // 1: exact leave-one-out weights in g(h) (KDE_CV_LOO)
   // ---- prepared samples
   float* y;   // [d][n_pad]  sqrt(log2(e)/4) L^-1 (x - mean), zero padded   (LSCV)
   float* xc;  // [n_pad]     x - mean, zero padded                           (d = 1)

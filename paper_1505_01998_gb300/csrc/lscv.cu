@@ -243,9 +243,11 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
   const int d = ds->d, n_h = ds->n_h;
   const double n = (double)ds->n;
   const double c2 = exp2(1.0 + 0.5 * d);
+  // K-term weight: the paper's n^-2 (Eq. LSCV-gh) or exact leave-one-out 1/(n(n-1))
+  const double wk = ds->cv_loo ? 2.0 / (n * (n - 1.0)) : 2.0 / (n * n);
   for (int k = threadIdx.x; k < n_h; k += blockDim.x) {
     const double s1 = ds->lscv_sum[2 * k], s2 = ds->lscv_sum[2 * k + 1];
-    ds->g[k] = pow(ds->h[k], -(double)d) * ds->A * (2.0 / (n * n) * (s1 - c2 * s2) + 1.0 / n);
+    ds->g[k] = pow(ds->h[k], -(double)d) * ds->A * (2.0 / (n * n) * s1 - wk * c2 * s2 + 1.0 / n);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

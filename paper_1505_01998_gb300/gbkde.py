@@ -42,7 +42,10 @@ class kde_grid(ctypes.Structure):
 class kde_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tile", ctypes.c_int),
                 ("bw_per_thread", ctypes.c_int), ("tiles_per_item", ctypes.c_int),
-                ("ctas_per_sm", ctypes.c_int)]
+                ("ctas_per_sm", ctypes.c_int), ("cv", ctypes.c_int)]
+
+
+KDE_CV_PAPER, KDE_CV_LOO = 0, 1
 
 
 class kde_result(ctypes.Structure):
@@ -115,6 +118,8 @@ SIGNATURES = {
     "kde_lscv_logdet": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
     "kde_autotune": (_I, [_P, _I, _L, _I, _I, _I, _P, _S, _P, ctypes.POINTER(kde_opts), _DP]),
     "kde_sample_covariance": (_I, [_P, _I, _L, _I, _P, _S, _P, _DP]),
+    "kde_lscv_search": (_I, [_P, _I, _L, _I, _D, _D, _D, _I, ctypes.POINTER(kde_opts), _P, _S, _P,
+                             ctypes.POINTER(kde_result), ctypes.POINTER(ctypes.c_int)]),
     "kde_lscv_H_minimize": (_I, [_P, _I, _L, _I, _DP, _I, _D, ctypes.POINTER(kde_opts), _P, _S, _P,
                                  _DP, _DP, ctypes.POINTER(ctypes.c_int)]),
     "kde_autotune_clear": (_I, []),
@@ -122,6 +127,21 @@ SIGNATURES = {
     "kde_autotune_load": (_I, [ctypes.c_char_p]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
 }
+
+
+def kde_lscv_search(x, h_lo=0.0, h_hi=0.0, rel_tol=1e-4, max_rounds=30, opts=None, ws=None,
+                    stream=None):
+    """Bracketing search (8 points per round); returns (result dict, rounds)."""
+    ptr, dt, n, d = _samples(x)
+    if ws is None:
+        ws = workspace(kde_workspace_size(n, d, 8, opts), x.device)
+    wp, wn = _ws(ws)
+    res = kde_result()
+    rounds = ctypes.c_int(0)
+    _check(lib().kde_lscv_search(ptr, dt, n, d, float(h_lo), float(h_hi), float(rel_tol),
+                                 int(max_rounds), ctypes.byref(opts) if opts else None, wp, wn,
+                                 _stream_handle(stream), ctypes.byref(res), ctypes.byref(rounds)))
+    return res.as_dict(), rounds.value
 
 
 def kde_sample_covariance(x, ws=None, stream=None) -> np.ndarray:
@@ -269,8 +289,9 @@ def _dp(a: np.ndarray):
 
 # ------------------------------------------------------------------ helpers
 
-def make_opts(precision=KDE_FP32_KAHAN, tile=0, bw_per_thread=0, tiles_per_item=0, ctas_per_sm=0):
-    return kde_opts(precision, tile, bw_per_thread, tiles_per_item, ctas_per_sm)
+def make_opts(precision=KDE_FP32_KAHAN, tile=0, bw_per_thread=0, tiles_per_item=0, ctas_per_sm=0,
+              cv=KDE_CV_PAPER):
+    return kde_opts(precision, tile, bw_per_thread, tiles_per_item, ctas_per_sm, cv)
 
 
 def make_grid(h=None, n_h=None, h_min=None, h_max=None):

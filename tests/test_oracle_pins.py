@@ -387,3 +387,68 @@ def test_toy8_regression_fixture():
     p = oracle.plugin(x)
     for k in ("sigma", "g1", "psi6", "g2", "psi4", "h"):
         assert p[k] == pytest.approx(ref["plugin"][k], rel=1e-13)
+
+
+# ------------------------------------------- exact leave-one-out, search
+
+def _lscv_loo_d1_by_quadrature(x, h):
+    """g_loo(h) = int fhat^2 - (2/n) sum_i fhat_{-i}(X_i), the integral by
+    quadrature, the leave-one-out sum by library normal densities."""
+    x = np.asarray(x, dtype=np.float64).ravel()
+    n = x.size
+    bw = h * np.std(x, ddof=1)
+    fhat = lambda t: np.sum(stats.norm.pdf(t, loc=x, scale=bw)) / n
+    pts = np.sort(x)
+    val, _ = integrate.quad(lambda t: fhat(t) ** 2, pts[0] - 12 * bw, pts[-1] + 12 * bw, points=pts,
+                            limit=2000, epsabs=0, epsrel=1e-12)
+    loo = 0.0
+    for i in range(n):
+        loo += (np.sum(stats.norm.pdf(x[i] - x, scale=bw)) - stats.norm.pdf(0.0, scale=bw)) / (n - 1)
+    return val - 2.0 * loo / n
+
+
+def test_lscv_loo_matches_quadrature():
+    x = datagen.mixture_1d(11, seed=4)[0]
+    h = np.array([0.08, 0.3, 0.9])
+    g = oracle.lscv_h_loo(x, h)
+    for k in range(h.size):
+        assert g[k] == pytest.approx(_lscv_loo_d1_by_quadrature(x, h[k]), rel=1e-8, abs=1e-12)
+
+
+def test_lscv_loo_multivariate_library_densities():
+    x = datagen.correlated_mixture(25, 3, seed=8).astype(np.float64)
+    d, n = x.shape
+    S = np.cov(x)
+    for hh in (0.3, 1.1):
+        H = hh * hh * S
+        k2 = stats.multivariate_normal(mean=np.zeros(d), cov=2 * H)
+        k1 = stats.multivariate_normal(mean=np.zeros(d), cov=H)
+        v = np.array([x[:, i] - x[:, j] for i in range(n) for j in range(i + 1, n)])
+        expect = (n * k2.pdf(np.zeros(d)) + 2 * np.sum(k2.pdf(v))) / n ** 2 - \
+            4.0 / (n * (n - 1)) * np.sum(k1.pdf(v))
+        assert oracle.lscv_h_loo(x, [hh])[0] == pytest.approx(expect, rel=1e-10)
+
+
+def test_search_finds_the_dense_grid_minimum_of_a_unimodal_objective():
+    x = datagen.rng(12).normal(0.0, 1.0, 400)
+    z = oracle.h0(400, 1)
+    a, b = z / 4, 4 * z
+    dense = oracle.grid_log(a, b, 3000)
+    gd = oracle.lscv_h(x, dense)["g"]
+    hs, gs, rounds = oracle.lscv_search(x, a, b, P=8, rel_tol=1e-4)
+    k = int(np.argmin(gd))
+    step = dense[1] / dense[0]
+    assert dense[k] / step ** 2 <= hs <= dense[k] * step ** 2
+    assert gs <= gd[k] + 1e-12 * abs(gd[k])
+    # each round keeps 2/(P+1) of the log-width
+    expect = int(np.ceil(np.log(np.log(b / a) / 2e-4) / np.log(9 / 2)))
+    assert rounds == expect
+
+
+def test_search_loo_flag_uses_the_loo_objective():
+    x = datagen.mixture_1d(300, seed=6)[0]
+    z = oracle.h0(300, 1)
+    h1, g1, _ = oracle.lscv_search(x, z / 4, 4 * z, loo=True)
+    assert g1 == pytest.approx(oracle.lscv_h_loo(x, [h1])[0], rel=1e-14)
+    h2, g2, _ = oracle.lscv_search(x, z / 4, 4 * z, loo=False)
+    assert g2 == pytest.approx(oracle.lscv_h(x, [h2])["g"][0], rel=1e-14)
