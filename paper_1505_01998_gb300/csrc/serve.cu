@@ -15,7 +15,7 @@
 //   builds the next step while the device runs the current one.
 // * A request's items depend only on the request and the server
 //   configuration, and items only ever write their own rows: results are
-//   bitwise the same alone or in the mix.  Items are capped at a sixth of a
+//   bitwise the same alone or in the mix.  Items are capped at a twelfth of a
 //   CTA's share of a step (finer than a single call's), so results equal the
 //   single-request entry points' within the FP32 tolerance, not bitwise.
 //   The variant launches of a step run on side streams, so their tails overlap.
@@ -172,11 +172,11 @@ struct kde_server {
 
 namespace {
 
-// Pair evaluations per scheduling step (default 1.6e11: about 18 ms of the
-// all-pairs kernels on a GB300, long against the ~0.1 ms launch overhead of a
-// step, short against the latency of a large request).
+// Pair evaluations per scheduling step (default 2.4e11: about 27 ms of the
+// all-pairs kernels on a GB300, long against the ~0.1 ms launch overhead and
+// the item tails of a step, short against the latency of a large request).
 double step_budget(const kde_server* s) {
-  return s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 1.6e11;
+  return s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 2.4e11;
 }
 
 void finish_req(kde_server* s, Req* r, int status) {
@@ -647,10 +647,10 @@ int kde_serve_submit(kde_server* s, const kde_request* q, uint64_t* ticket) {
     }
     n_h = (int)r->grid.size();
   }
-  // items of at most a sixth of a CTA's share of one step: every step spans all
-  // CTAs and launch tails stay short
+  // items of at most a twelfth of a CTA's share of one step: every step spans
+  // all CTAs and launch tails stay short
   const int cps = (s->has_opts && s->opts.ctas_per_sm) ? s->opts.ctas_per_sm : 2;
-  const double max_item = step_budget(s) / (6.0 * std::max(1, s->sms) * cps);
+  const double max_item = step_budget(s) / (12.0 * std::max(1, s->sms) * cps);
   int rc = make_geometry(q->n, q->d, n_h, s->has_opts ? &s->opts : nullptr, s->sms, &r->geo, max_item);
   if (rc) {
     delete r;
