@@ -80,6 +80,8 @@ def _load():
             "kdeo_lscv_h": (I, [P, L, I, P, I, P, P, P, P, I]),
             "kdeo_lscv_H": (I, [P, L, I, P, P, I]),
             "kdeo_lscv_h_loo": (I, [P, L, I, P, I, P, I]),
+            "kdeo_kde_eval": (I, [P, L, I, P, P, L, P, I]),
+            "kdeo_aqp": (I, [P, L, D, P, P, L, P, P, I]),
             "kdeo_lscv_search": (I, [P, L, I, D, D, I, D, I, I, P, P, P, I]),
         }
         for name, (res, args) in sig.items():
@@ -258,6 +260,29 @@ def lscv_search(x, a: float, b: float, P: int = 8, rel_tol: float = 1e-4, max_ro
     if rc:
         raise ValueError(f"oracle lscv_search status {rc}")
     return float(hb[0]), float(gb[0]), rounds.value
+
+
+def kde_eval(x, H, q, threads: int = 0) -> np.ndarray:
+    """fhat at the points q (d, m) with bandwidth matrix H."""
+    a = _as2d(x)
+    d, n = a.shape
+    qq = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(d, -1))
+    HH = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(d, d))
+    f = np.zeros(qq.shape[1])
+    rc = _load().kdeo_kde_eval(_p(a), n, d, _p(HH), _p(qq), qq.shape[1], _p(f), threads)
+    if rc:
+        raise ValueError(f"oracle kde_eval status {rc}")
+    return f
+
+
+def aqp(x, h: float, lo, hi, threads: int = 0):
+    """(count, sum) over the ranges [lo_k, hi_k] of a univariate column."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    l = np.ascontiguousarray(np.asarray(lo, dtype=np.float64).ravel())
+    u = np.ascontiguousarray(np.asarray(hi, dtype=np.float64).ravel())
+    c, s = np.zeros(l.size), np.zeros(l.size)
+    _load().kdeo_aqp(_p(a), a.size, float(h), _p(l), _p(u), l.size, _p(c), _p(s), threads)
+    return c, s
 
 
 def lscv_H(x, H, threads: int = 0) -> float:

@@ -490,6 +490,68 @@ int kdeo_lscv_search(const double *x, long n, int d, double a, double b, int P, 
   return KDEO_OK;
 }
 
+/* ------------------------------------------- consumers of the bandwidth */
+
+/* Density estimate fhat(q) = n^-1 sum_i K_H(q - X_i) at m points q (d x m,
+ * one point per column) with K_H(u) = (2 pi)^(-d/2) |H|^(-1/2)
+ * exp(-u^T H^-1 u / 2) (Sec. 4.2, Eqs. kde-def-H, K_H, gaussian). */
+int kdeo_kde_eval(const double *x, long n, int d, const double *H, const double *q, long m,
+                  double *f, int threads) {
+  double *Hi = (double *)malloc(sizeof(double) * (size_t)(d * d));
+  if (!Hi) return KDEO_ENOMEM;
+  double det;
+  if (kdeo_invert(H, d, Hi, &det) != KDEO_OK || !(det > 0.0)) {
+    free(Hi);
+    return KDEO_EDEGENERATE;
+  }
+  double c = pow(2.0 * KDEO_PI, -0.5 * d) / sqrt(det) / (double)n;
+  int nt = pick_threads(threads);
+#pragma omp parallel num_threads(nt)
+  {
+    double *v = (double *)malloc(sizeof(double) * (size_t)d);
+#pragma omp for schedule(dynamic, 4)
+    for (long k = 0; k < m; ++k) {
+      nsum_t s = {0, 0};
+      for (long i = 0; i < n; ++i) {
+        for (int a = 0; a < d; ++a) v[a] = q[(long)a * m + k] - x[(long)a * n + i];
+        double qf = 0.0;
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) qf += v[a] * Hi[a * d + b] * v[b];
+        nsum_add(&s, exp(-0.5 * qf));
+      }
+      f[k] = c * nsum_get(&s);
+    }
+    free(v);
+  }
+  free(Hi);
+  return KDEO_OK;
+}
+
+/* Approximate Count and Sum of a numeric column over ranges [lo_k, hi_k]
+ * from its univariate estimate with bandwidth h (Sec. 4.3, Eqs. count, sum):
+ *   count = n int_lo^hi fhat(x) dx = sum_i [Phi(b_i) - Phi(a_i)],
+ *   sum   = n int_lo^hi x fhat(x) dx = sum_i [x_i (Phi(b_i) - Phi(a_i)) + h (phi(a_i) - phi(b_i))],
+ * with a_i = (lo - x_i)/h, b_i = (hi - x_i)/h: the integrals of each Gaussian
+ * term done exactly (Phi by the complementary error function). */
+int kdeo_aqp(const double *x, long n, double h, const double *lo, const double *hi, long m,
+             double *count, double *sum, int threads) {
+  int nt = pick_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+  for (long k = 0; k < m; ++k) {
+    nsum_t sc = {0, 0}, ss = {0, 0};
+    for (long i = 0; i < n; ++i) {
+      double a = (lo[k] - x[i]) / h, b = (hi[k] - x[i]) / h;
+      double Pa = 0.5 * erfc(-a / sqrt(2.0)), Pb = 0.5 * erfc(-b / sqrt(2.0));
+      double pa = exp(-0.5 * a * a) / sqrt(2.0 * KDEO_PI), pb = exp(-0.5 * b * b) / sqrt(2.0 * KDEO_PI);
+      nsum_add(&sc, Pb - Pa);
+      nsum_add(&ss, x[i] * (Pb - Pa) + h * (pa - pb));
+    }
+    count[k] = nsum_get(&sc);
+    sum[k] = nsum_get(&ss);
+  }
+  return KDEO_OK;
+}
+
 /* ------------------------------------------------------------- LSCV_H */
 
 /* The LSCV_H objective g(H) for one symmetric positive-definite bandwidth

@@ -452,3 +452,43 @@ def test_search_loo_flag_uses_the_loo_objective():
     assert g1 == pytest.approx(oracle.lscv_h_loo(x, [h1])[0], rel=1e-14)
     h2, g2, _ = oracle.lscv_search(x, z / 4, 4 * z, loo=False)
     assert g2 == pytest.approx(oracle.lscv_h(x, [h2])["g"][0], rel=1e-14)
+
+
+# ------------------------------------------- density evaluation and AQP
+
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_kde_eval_matches_library_densities(d):
+    x = datagen.correlated_mixture(60, d, seed=120 + d).astype(np.float64)
+    rng = datagen.rng(d)
+    A = rng.normal(size=(d, d)) * 0.4
+    H = A @ A.T + 0.3 * np.eye(d)
+    q = rng.normal(size=(d, 9)) * 2
+    f = oracle.kde_eval(x, H, q)
+    mvn = stats.multivariate_normal(mean=np.zeros(d), cov=H)
+    for k in range(q.shape[1]):
+        expect = np.mean([mvn.pdf(q[:, k] - x[:, i]) for i in range(x.shape[1])])
+        assert f[k] == pytest.approx(expect, rel=1e-11)
+
+
+def test_kde_eval_integrates_to_one():
+    x = datagen.mixture_1d(40, seed=3)
+    H = np.array([[0.09]])
+    val, _ = integrate.quad(lambda t: oracle.kde_eval(x, H, np.array([[t]]))[0], -20, 20, limit=400)
+    assert val == pytest.approx(1.0, rel=1e-9)
+
+
+def test_aqp_count_and_sum_match_quadrature():
+    x = datagen.mixture_1d(30, seed=5)[0]
+    n, h = x.size, 0.4
+    lo = np.array([-3.0, -0.5, 1.0])
+    hi = np.array([-1.0, 2.5, 1.2])
+    c, s = oracle.aqp(x, h, lo, hi)
+    fh = lambda t: np.sum(stats.norm.pdf(t, loc=x, scale=h)) / n
+    for k in range(3):
+        ce, _ = integrate.quad(lambda t: n * fh(t), lo[k], hi[k], epsabs=0, epsrel=1e-12, limit=200)
+        se, _ = integrate.quad(lambda t: n * t * fh(t), lo[k], hi[k], epsabs=0, epsrel=1e-12, limit=200)
+        assert c[k] == pytest.approx(ce, rel=1e-9)
+        assert s[k] == pytest.approx(se, rel=1e-9, abs=1e-12)
+    call, sall = oracle.aqp(x, h, [-1e3], [1e3])
+    assert call[0] == pytest.approx(n, rel=1e-14)
+    assert sall[0] == pytest.approx(np.sum(x), rel=1e-12)
