@@ -230,7 +230,9 @@ int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, 
  * the bracket becomes the neighbours of the best point (log-width x 2/9 per
  * round) until it is within 2 rel_tol (log) or after max_rounds.  out->h and
  * out->g_min hold the best evaluated point (a local minimum if g is not
- * unimodal); rounds_out (optional) the rounds taken.  Workspace:
+ * unimodal); out->flags has KDE_FLAG_MIN_AT_LOWER_EDGE (UPPER_EDGE) when every
+ * round kept the bracket's lower (upper) end, i.e. g still falls towards that
+ * end of [h_lo, h_hi]; rounds_out (optional) the rounds taken.  Workspace:
  * kde_workspace_size(n, d, 8).  Synchronises the stream every round. */
 int kde_lscv_search(const void* x_dev, int dtype, int64_t n, int d, double h_lo, double h_hi,
                     double rel_tol, int max_rounds, const kde_opts* opts, void* ws, size_t ws_bytes,
@@ -442,6 +444,48 @@ int kde_serve_destroy(kde_server* server);
 int kde_lscv_noalloc(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* grid,
                      const kde_opts* opts, void* stream, double* g_host, double* h_host,
                      kde_result* out);
+
+/* ------------------------------------------- consumers of a bandwidth */
+
+/* Workspace for kde_eval of n samples in d dimensions at m query points. */
+int kde_eval_workspace_size(int64_t n, int d, int64_t m, size_t* bytes);
+
+/* Density estimate at query points (Sec. 4.2, the kernel estimator with a
+ * bandwidth matrix H and the Gaussian K_H): for every query q_j,
+ *   f(q_j) = n^-1 sum_i (2 pi)^-d/2 |H|^-1/2 exp(-(q_j - x_i)^T H^-1 (q_j - x_i) / 2).
+ * x_dev: d x n samples (x[k*n + i], as everywhere), KDE_F32 or KDE_F64.
+ * H_host: d x d symmetric positive definite bandwidth matrix, row-major host
+ * array (for d = 1, h^2; from kde_lscv with H = h^2 S, or kde_lscv_H).
+ * q_dev: d x m queries (q[k*m + j]), same dtype as x.  f_host: m doubles.
+ * Pairs are evaluated in FP32 (one exp2 per pair) with FP32 Kahan runs per
+ * thread and FP64 sums across threads; the result is deterministic.
+ * Synchronises the stream.  Errors: KDE_EINVAL (arguments, H not finite or
+ * not symmetric), KDE_ENOMEM (workspace too small), KDE_EDEGENERATE (H not
+ * positive definite), KDE_ECUDA. */
+int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_host,
+             const void* q_dev, int64_t m, void* ws, size_t ws_bytes, void* stream,
+             double* f_host);
+
+/* Workspace for kde_aqp of n samples and m ranges. */
+int kde_aqp_workspace_size(int64_t n, int m, size_t* bytes);
+
+/* Approximate range aggregates of one numeric column from its sample and a
+ * bandwidth h (Sec. 4.3, the Count and Sum estimators over the density
+ * estimate).  For every range [lo_k, hi_k], with a = (lo_k - x_i)/h,
+ * b = (hi_k - x_i)/h and Phi, phi the standard normal cdf and pdf:
+ *   count_k = sum_i [Phi(b) - Phi(a)],
+ *   sum_k   = sum_i [x_i (Phi(b) - Phi(a)) + h (phi(a) - phi(b))],
+ * i.e. the sample's share of the range and of its total; multiply by
+ * N / n for a table of N rows.  x_dev: n samples (KDE_F32 / KDE_F64) in device
+ * memory; lo_host, hi_host: m <= KDE_MAX_NH bounds with lo <= hi (either may
+ * be infinite; NaN is rejected), rounded to FP32.
+ * count_host / sum_host: m doubles each, either may be NULL.  Arithmetic per
+ * sample in FP32 (cdf differences taken from the smaller tails), FP32 Kahan
+ * sums per thread, FP64 across threads; deterministic.  Synchronises the
+ * stream.  Errors: KDE_EINVAL, KDE_ENOMEM, KDE_ECUDA. */
+int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_host,
+            const double* hi_host, int m, void* ws, size_t ws_bytes, void* stream,
+            double* count_host, double* sum_host);
 
 /* ------------------------------------------------------------ autotuner */
 

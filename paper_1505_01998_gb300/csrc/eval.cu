@@ -1,0 +1,353 @@
+// Consumers of a selected bandwidth: the density estimate at query points
+// (Sec. 4.2, Eqs. kde-def-H, K_H) and the approximate Count / Sum of a
+// numeric column over ranges (Sec. 4.3, Eqs. count, sum).
+//
+// kde_eval: samples and queries are whitened by the Cholesky factor of H (the
+// prologue with a given H), scaled so that K_H(q - x) is proportional to
+// 2^-|y_q - y_x|^2; one CTA item is a tile of 128 queries (4 per lane) against
+// a chunk of samples staged in shared memory; per-query FP32 runs fold into
+// Kahan pairs, item totals go to per-item FP64 rows reduced in fixed order.
+// kde_aqp: for every sample and range, the exact integral of its Gaussian
+// term over the range (normal cdf differences, tails taken from the nearer
+// side); per-thread Kahan sums, FP64 across threads and items.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "host.hpp"
+#include "internal.cuh"
+
+using namespace gbkde;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kQT = 128;          // queries per item (4 per lane)
+constexpr int kSampleStage = 512; // samples staged per pass
+
+// Whitened, sqrt(2)-scaled queries: yq[k][j] = sqrt(2) (M (q_j - mean))_k.
+template <typename TIN>
+__global__ void k_whiten_queries(const DsDev* ds, const TIN* __restrict__ q, int64_t m, int64_t m_pad,
+                                 float* __restrict__ yq) {
+  const int d = ds->d, dk = ds->dk;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m_pad; j += (int64_t)gridDim.x * blockDim.x) {
+    float c[KDE_MAX_D] = {};
+    if (j < m)
+      for (int k = 0; k < d; ++k) c[k] = (float)((double)q[(int64_t)k * m + j] - ds->mean[k]);
+    for (int k = 0; k < dk; ++k) {
+      float t = 0.f;
+      if (k < d)
+        for (int i = 0; i <= k; ++i) t = fmaf(ds->M[k * KDE_MAX_D + i], c[i], t);
+      yq[(int64_t)k * m_pad + j] = 1.41421356237309505f * t;
+    }
+  }
+}
+
+// items: (query tile, sample chunk); part[chunk][m_pad] FP64.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_eval(const DsDev* ds, const float* __restrict__ yq, int64_t m_pad,
+                                                   int64_t q_tiles, int64_t chunk, int64_t n_chunks,
+                                                   double* __restrict__ part) {
+  __shared__ __align__(16) float sS[kSampleStage * D];
+  __shared__ double sRed[kWarps][kQT];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n = ds->n, n_pad = ds->n_pad;
+  const float* __restrict__ Y = ds->y;
+  const int64_t items = q_tiles * n_chunks;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t qt = it % q_tiles, c = it / q_tiles;
+    float yqr[4][D];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int k = 0; k < D; ++k) yqr[r][k] = yq[(int64_t)k * m_pad + qt * kQT + lane + 32 * r];
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int64_t j0 = c * chunk, j1 = min(j0 + chunk, n);
+    for (int64_t jb = j0; jb < j1; jb += kSampleStage) {
+      const int cnt = (int)min((int64_t)kSampleStage, j1 - jb);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < kSampleStage * D; idx += kThreads) {
+        const int jj = idx / D, k = idx - jj * D;
+        sS[idx] = jj < cnt ? 1.41421356237309505f * Y[(int64_t)k * n_pad + jb + jj] : 0.f;
+      }
+      __syncthreads();
+      float run[4] = {0.f, 0.f, 0.f, 0.f};
+      // warp w walks samples w, w + 8, ... of the staged block
+      for (int jj = warp; jj < cnt; jj += kWarps) {
+        float f[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) f[k] = sS[jj * D + k];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          float Q = 0.f;
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float dl = yqr[r][k] - f[k];
+            Q = fmaf(dl, dl, Q);
+          }
+          run[r] += ex2(-Q);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) kahan_add(s[r], cc[r], run[r]);
+    }
+    // combine the 8 warps (each saw every query of the tile) in fixed order
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) sRed[warp][lane + 32 * r] = (double)s[r] - (double)cc[r];
+    __syncthreads();
+    for (int qq = threadIdx.x; qq < kQT; qq += kThreads) {
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += sRed[w][qq];
+      part[c * m_pad + qt * kQT + qq] = t;
+    }
+  }
+}
+
+__global__ void k_eval_finish(const DsDev* ds, const double* __restrict__ part, int64_t m, int64_t m_pad,
+                              int64_t n_chunks, double* __restrict__ f) {
+  const int d = ds->d;
+  const double C = pow(2.0 * kPi, -0.5 * d) * exp(-0.5 * ds->logdet) / (double)ds->n;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+    double t = 0.0;
+    for (int64_t c = 0; c < n_chunks; ++c) t += part[c * m_pad + j];
+    f[j] = C * t;
+  }
+}
+
+// Phi(b) - Phi(a) for a <= b, taken from the side with the smaller tails.
+__device__ __forceinline__ float cdf_diff(float a, float b) {
+  const float r = 0.70710678118654752f;
+  if (a >= 0.f) return 0.5f * (erfcf(a * r) - erfcf(b * r));
+  if (b <= 0.f) return 0.5f * (erfcf(-b * r) - erfcf(-a * r));
+  return 1.f - 0.5f * (erfcf(b * r) + erfcf(-a * r));
+}
+
+constexpr int kRG = 8;  // ranges per pass of a thread
+
+template <typename TIN>
+__global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int64_t n, float h,
+                                                  const float* __restrict__ rng /* [m][2] */, int m,
+                                                  int64_t chunk, double* __restrict__ part /* [chunks][m][2] */) {
+  __shared__ double sRed[kWarps][kRG][2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i0 = blockIdx.x * chunk, i1 = min(i0 + chunk, n);
+  const float inv_h = 1.f / h, inv_sqrt_2pi = 0.39894228040143268f;
+  for (int k0 = 0; k0 < m; k0 += kRG) {
+    float sc[kRG], cc[kRG], ss[kRG], cs[kRG];
+#pragma unroll
+    for (int g = 0; g < kRG; ++g) sc[g] = cc[g] = ss[g] = cs[g] = 0.f;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
+      const float xi = (float)x[i];
+#pragma unroll
+      for (int g = 0; g < kRG; ++g) {
+        if (k0 + g >= m) break;
+        const float a = (rng[2 * (k0 + g)] - xi) * inv_h, b = (rng[2 * (k0 + g) + 1] - xi) * inv_h;
+        const float P = cdf_diff(a, b);
+        const float pa = inv_sqrt_2pi * expf(-0.5f * a * a), pb = inv_sqrt_2pi * expf(-0.5f * b * b);
+        kahan_add(sc[g], cc[g], P);
+        kahan_add(ss[g], cs[g], fmaf(xi, P, h * (pa - pb)));
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kRG; ++g) {
+      double vc = warp_sum((double)sc[g] - (double)cc[g]);
+      double vs = warp_sum((double)ss[g] - (double)cs[g]);
+      if (lane == 0) {
+        sRed[warp][g][0] = vc;
+        sRed[warp][g][1] = vs;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kRG) {
+      const int g = threadIdx.x >> 1, w2 = threadIdx.x & 1;
+      double t = 0.0;
+      for (int w = 0; w < kWarps; ++w) t += sRed[w][g][w2];
+      if (k0 + g < m) part[((int64_t)blockIdx.x * m + k0 + g) * 2 + w2] = t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_aqp_finish(const double* __restrict__ part, int m, int64_t chunks, double* __restrict__ out) {
+  for (int j = threadIdx.x; j < 2 * m; j += blockDim.x) {
+    double t = 0.0;
+    for (int64_t c = 0; c < chunks; ++c) t += part[c * 2 * m + j];
+    out[j] = t;
+  }
+}
+
+struct EvalLayout {
+  Geometry g;
+  int64_t m_pad, q_tiles, chunk, n_chunks;
+  size_t off_yq, off_part, off_f, total;
+};
+
+int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
+  int rc = make_geometry(n, d, 1, nullptr, sms, &L->g);
+  if (rc) return rc;
+  L->m_pad = (m + kQT - 1) / kQT * kQT;
+  L->q_tiles = L->m_pad / kQT;
+  // sample chunks: about 4 items per CTA over the whole launch, whole stage blocks
+  const int64_t ctas = (int64_t)std::max(1, sms) * 2;
+  int64_t want = std::max<int64_t>(1, (4 * ctas + L->q_tiles - 1) / L->q_tiles);
+  L->chunk = std::max<int64_t>(kSampleStage, (n + want - 1) / want / kSampleStage * kSampleStage);
+  L->n_chunks = (n + L->chunk - 1) / L->chunk;
+  size_t o = (L->g.total + 255) / 256 * 256;
+  L->off_yq = o;
+  o += ((size_t)L->g.dk * L->m_pad * 4 + 255) / 256 * 256;
+  L->off_part = o;
+  o += ((size_t)L->n_chunks * L->m_pad * 8 + 255) / 256 * 256;
+  L->off_f = o;
+  o += ((size_t)m * 8 + 255) / 256 * 256;
+  L->total = o;
+  return KDE_OK;
+}
+
+struct AqpLayout {
+  int64_t chunk, chunks;
+  size_t off_part, off_out, total;
+};
+
+// One CTA per sample chunk, about 4 CTAs per SM.
+AqpLayout aqp_layout(int64_t n, int m, int sms) {
+  AqpLayout L;
+  const int64_t ctas = (int64_t)std::max(1, sms) * 4;
+  L.chunk = std::max<int64_t>(kThreads, (n + ctas - 1) / ctas);
+  L.chunks = (n + L.chunk - 1) / L.chunk;
+  L.off_part = ((size_t)m * 2 * sizeof(float) + 255) / 256 * 256;
+  L.off_out = L.off_part + ((size_t)L.chunks * m * 2 * sizeof(double) + 255) / 256 * 256;
+  L.total = L.off_out + ((size_t)m * 2 * sizeof(double) + 255) / 256 * 256;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kde_eval_workspace_size(int64_t n, int d, int64_t m, size_t* bytes) {
+  if (!bytes || n < 2 || d < 1 || d > KDE_MAX_D || m < 1) return fail(KDE_EINVAL, "kde_eval_workspace_size: bad arguments");
+  EvalLayout L;
+  int rc = eval_layout(n, d, m, device_sms(), &L);
+  if (rc) return rc;
+  *bytes = L.total;
+  return KDE_OK;
+}
+
+int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_host, const void* q_dev,
+             int64_t m, void* ws, size_t ws_bytes, void* stream, double* f_host) {
+  int rc = check_common(x_dev, dtype, n, d, ws);
+  if (rc) return rc;
+  if (!H_host || !q_dev || !f_host || m < 1) return fail(KDE_EINVAL, "kde_eval: H, q, f or m");
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b)
+      if (!std::isfinite(H_host[a * d + b]) || H_host[a * d + b] != H_host[b * d + a])
+        return fail(KDE_EINVAL, "kde_eval: H not finite and symmetric");
+  EvalLayout L;
+  rc = eval_layout(n, d, m, device_sms(), &L);
+  if (rc) return rc;
+  if (ws_bytes < L.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  DsDev init = make_desc(L.g, x_dev, dtype, KDE_METHOD_LSCV, w);
+  init.given_H = 1;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) init.cov[a * d + b] = H_host[a * d + b];
+  DsDev* ds = reinterpret_cast<DsDev*>(w + L.g.off_ds);
+  int64_t* off = reinterpret_cast<int64_t*>(w + L.g.off_off);
+  const double one = 1.0;
+  const int64_t offs[4] = {0, 0, 0, 0};
+  float* yq = reinterpret_cast<float*>(w + L.off_yq);
+  double* part = reinterpret_cast<double*>(w + L.off_part);
+  double* f = reinterpret_cast<double*>(w + L.off_f);
+  cudaError_t e = launch_setup(ds, init, &one, 1, off, offs, 4, st);
+  if (e == cudaSuccess) e = launch_prep(ds, 1, nullptr, st);
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<int64_t>(1024, (L.m_pad + 255) / 256);
+    if (dtype == KDE_F64)
+      k_whiten_queries<double><<<blocks, 256, 0, st>>>(ds, static_cast<const double*>(q_dev), m, L.m_pad, yq);
+    else
+      k_whiten_queries<float><<<blocks, 256, 0, st>>>(ds, static_cast<const float*>(q_dev), m, L.m_pad, yq);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int64_t items = L.q_tiles * L.n_chunks;
+    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * 2);
+    switch (L.g.dk) {
+      case 1: k_eval<1><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      case 2: k_eval<2><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      case 3: k_eval<3><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      case 4: k_eval<4><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      case 8: k_eval<8><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      case 12: k_eval<12><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+      default: k_eval<16><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_eval_finish<<<(int)std::min<int64_t>(1024, (m + 255) / 256), 256, 0, st>>>(ds, part, m, L.m_pad, L.n_chunks, f);
+    e = cudaGetLastError();
+  }
+  kde_result r;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&r, w + L.g.off_ds + offsetof(DsDev, res), sizeof(r), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f_host, f, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "kde_eval");
+  if (r.status != KDE_OK) return fail(r.status, "kde_eval: %s", kde_status_string(r.status));
+  return KDE_OK;
+}
+
+int kde_aqp_workspace_size(int64_t n, int m, size_t* bytes) {
+  if (!bytes || n < 2 || m < 1 || m > KDE_MAX_NH) return fail(KDE_EINVAL, "kde_aqp_workspace_size: bad arguments");
+  *bytes = aqp_layout(n, m, device_sms()).total;
+  return KDE_OK;
+}
+
+int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_host,
+            const double* hi_host, int m, void* ws, size_t ws_bytes, void* stream, double* count_host,
+            double* sum_host) {
+  int rc = check_common(x_dev, dtype, n, 1, ws);
+  if (rc) return rc;
+  if (!lo_host || !hi_host || m < 1 || m > KDE_MAX_NH || !(h > 0) || !std::isfinite(h))
+    return fail(KDE_EINVAL, "kde_aqp: ranges, m or h");
+  for (int k = 0; k < m; ++k)
+    if (!(lo_host[k] <= hi_host[k])) return fail(KDE_EINVAL, "kde_aqp: range %d has lo > hi or a NaN bound", k);
+  const AqpLayout L = aqp_layout(n, m, device_sms());
+  const int64_t chunk = L.chunk, chunks = L.chunks;
+  if (ws_bytes < L.total) return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, L.total);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  float* rng = reinterpret_cast<float*>(w);
+  double* part = reinterpret_cast<double*>(w + L.off_part);
+  double* out = reinterpret_cast<double*>(w + L.off_out);
+  std::vector<float> r2(2 * m);
+  for (int k = 0; k < m; ++k) {
+    r2[2 * k] = (float)lo_host[k];
+    r2[2 * k + 1] = (float)hi_host[k];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(rng, r2.data(), sizeof(float) * 2 * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    if (dtype == KDE_F64)
+      k_aqp<double><<<(int)chunks, kThreads, 0, st>>>(static_cast<const double*>(x_dev), n, (float)h, rng, m, chunk, part);
+    else
+      k_aqp<float><<<(int)chunks, kThreads, 0, st>>>(static_cast<const float*>(x_dev), n, (float)h, rng, m, chunk, part);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_aqp_finish<<<1, 256, 0, st>>>(part, m, chunks, out);
+    e = cudaGetLastError();
+  }
+  std::vector<double> res(2 * m);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(res.data(), out, sizeof(double) * 2 * m, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "kde_aqp");
+  for (int k = 0; k < m; ++k) {
+    if (count_host) count_host[k] = res[2 * k];
+    if (sum_host) sum_host[k] = res[2 * k + 1];
+  }
+  return KDE_OK;
+}
+
+}  // extern "C"

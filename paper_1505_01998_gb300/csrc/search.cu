@@ -29,6 +29,7 @@ extern "C" int kde_lscv_search(const void* x_dev, int dtype, int64_t n, int d, d
     b = h0 * 4.0;
   }
   if (!(b > a) || !std::isfinite(b)) return fail(KDE_EINVAL, "bracket [%g, %g] invalid", a, b);
+  const double a0 = a, b0 = b;
   double hb = 0.0, gb = INFINITY;
   kde_result best{};
   int t = 0;
@@ -53,7 +54,8 @@ extern "C" int kde_lscv_search(const void* x_dev, int dtype, int64_t n, int d, d
   best.h_data = (d == 1) ? hb * best.sigma : 0.0;
   best.argmin = 0;
   best.n_h = 0;
-  best.flags = 0;
+  // the bracket never left an end of the range: the minimum is at (or beyond) it
+  best.flags = (a == a0 ? KDE_FLAG_MIN_AT_LOWER_EDGE : 0) | (b == b0 ? KDE_FLAG_MIN_AT_UPPER_EDGE : 0);
   *out = best;
   if (rounds_out) *rounds_out = t;
   return KDE_OK;

@@ -122,6 +122,10 @@ SIGNATURES = {
                              ctypes.POINTER(kde_result), ctypes.POINTER(ctypes.c_int)]),
     "kde_lscv_H_minimize": (_I, [_P, _I, _L, _I, _DP, _I, _D, ctypes.POINTER(kde_opts), _P, _S, _P,
                                  _DP, _DP, ctypes.POINTER(ctypes.c_int)]),
+    "kde_eval_workspace_size": (_I, [_L, _I, _L, ctypes.POINTER(ctypes.c_size_t)]),
+    "kde_eval": (_I, [_P, _I, _L, _I, _DP, _P, _L, _P, _S, _P, _DP]),
+    "kde_aqp_workspace_size": (_I, [_L, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "kde_aqp": (_I, [_P, _I, _L, _D, _DP, _DP, _I, _P, _S, _P, _DP, _DP]),
     "kde_autotune_clear": (_I, []),
     "kde_autotune_save": (_I, [ctypes.c_char_p]),
     "kde_autotune_load": (_I, [ctypes.c_char_p]),
@@ -237,6 +241,55 @@ def kde_lscv_noalloc(x, grid, opts=None, stream=None):
                                   ctypes.byref(opts) if opts else None, _stream_handle(stream),
                                   _dp(g), _dp(h), ctypes.byref(res)))
     return res.as_dict(), g, h
+
+
+def kde_eval_workspace_size(n: int, d: int, m: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().kde_eval_workspace_size(n, d, m, ctypes.byref(out)))
+    return out.value
+
+
+def kde_eval(x, H, q, ws=None, stream=None) -> np.ndarray:
+    """Density estimate with bandwidth matrix H (d x d, or a scalar h^2 for
+    d = 1) at the device query points q (d, m), from device samples x (d, n)."""
+    ptr, dt, n, d = _samples(x)
+    qp, qdt, m, qd = _samples(q)
+    if qd != d or qdt != dt:
+        raise ValueError("queries must have the samples' dimension and dtype")
+    Hm = np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(d, d))
+    if ws is None:
+        ws = workspace(kde_eval_workspace_size(n, d, m), x.device)
+    wp, wn = _ws(ws)
+    f = np.zeros(m)
+    _check(lib().kde_eval(ptr, dt, n, d, _dp(Hm), qp, m, wp, wn, _stream_handle(stream), _dp(f)))
+    return f
+
+
+def kde_aqp_workspace_size(n: int, m: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().kde_aqp_workspace_size(n, m, ctypes.byref(out)))
+    return out.value
+
+
+def kde_aqp(x, h: float, lo, hi, ws=None, stream=None):
+    """Approximate Count and Sum over the ranges [lo_k, hi_k] from device
+    samples x (n,) and bandwidth h.  Returns (count, sum) arrays."""
+    ptr, dt, n, d = _samples(x)
+    if d != 1:
+        raise ValueError("range aggregates take one column")
+    a = np.ascontiguousarray(np.asarray(lo, dtype=np.float64).ravel())
+    b = np.ascontiguousarray(np.asarray(hi, dtype=np.float64).ravel())
+    if a.size != b.size:
+        raise ValueError("lo and hi differ in length")
+    m = a.size
+    if ws is None:
+        ws = workspace(kde_aqp_workspace_size(n, m), x.device)
+    wp, wn = _ws(ws)
+    cnt = np.zeros(m)
+    sm = np.zeros(m)
+    _check(lib().kde_aqp(ptr, dt, n, float(h), _dp(a), _dp(b), m, wp, wn, _stream_handle(stream),
+                         _dp(cnt), _dp(sm)))
+    return cnt, sm
 
 
 class kde_serve_config(ctypes.Structure):

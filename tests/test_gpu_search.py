@@ -46,11 +46,27 @@ def test_search_matches_oracle_search(d, n, loo):
 
 
 def test_search_is_no_worse_than_the_dense_grid():
+    """Interior minimum (three-component mixture): the search ends at or below
+    the best point of a 256-point grid over the same range, without edge flags."""
+    kde = built_lib()
+    n = 20000
+    x = datagen.mixture_1d(n, seed=17)
+    res, rounds = kde.kde_lscv_search(_dev(x), rel_tol=1e-4)
+    grid_res, g, h = kde.kde_lscv(_dev(x), kde.make_grid(n_h=256)[0])
+    assert 0 < grid_res["argmin"] < 255
+    assert res["g_min"] <= grid_res["g_min"] + 1e-6 * abs(grid_res["g_min"])
+    assert res["flags"] == 0
+    assert rounds <= 10
+
+
+def test_search_flags_a_minimum_at_the_range_end():
+    """The skewed column's g(h) still falls at h0/4 (the dense grid's argmin is
+    its first point): the search walks down to the lower end and flags it."""
     kde = built_lib()
     n = 20000
     x = datagen.skewed_column(n, seed=17)
-    x64 = x.astype(np.float32).astype(np.float64)
     res, rounds = kde.kde_lscv_search(_dev(x), rel_tol=1e-4)
     grid_res, g, h = kde.kde_lscv(_dev(x), kde.make_grid(n_h=256)[0])
-    assert res["g_min"] <= grid_res["g_min"] + 1e-5 * abs(grid_res["g_min"])
-    assert rounds <= 10
+    assert grid_res["argmin"] == 0
+    assert res["flags"] == kde.KDE_FLAG_MIN_AT_LOWER_EDGE
+    assert abs(np.log(res["h"] / h[0])) <= 2e-4
