@@ -2,11 +2,12 @@
 // (Sec. 4.2, Eqs. kde-def-H, K_H) and the approximate Count / Sum of a
 // numeric column over ranges (Sec. 4.3, Eqs. count, sum).
 //
-// kde_eval: samples and queries are whitened by the Cholesky factor of H (the
-// prologue with a given H), scaled so that K_H(q - x) is proportional to
-// 2^-|y_q - y_x|^2; one CTA item is a tile of 128 queries (4 per lane) against
-// a chunk of samples staged in shared memory; per-query FP32 runs fold into
-// Kahan pairs, item totals go to per-item FP64 rows reduced in fixed order.
+// kde_eval: the prologue (with a given H) checks and factors H = L L^T; one CTA
+// item is a tile of 128 queries (4 per lane) against a chunk of samples staged
+// in shared memory, both whitened by L^-1 relative to the tile's first query
+// and scaled so that K_H(q - x) is proportional to 2^-|y_q - y_x|^2; per-query
+// FP32 runs fold into Kahan pairs, item totals go to per-chunk FP64 rows
+// reduced in fixed order.
 // kde_aqp: for every sample and range, the exact integral of its Gaussian
 // term over the range (normal cdf differences, tails taken from the nearer
 // side); per-thread Kahan sums, FP64 across threads and items.
@@ -26,54 +27,89 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kQT = 128;          // queries per item (4 per lane)
 constexpr int kSampleStage = 512; // samples staged per pass
 
-// Whitened, sqrt(2)-scaled queries: yq[k][j] = sqrt(2) (M (q_j - mean))_k.
+// Every query tile t has a centre c_t (its first query).  Queries and samples
+// are whitened relative to the centre of the tile they meet, so the FP32
+// coordinates the pair loop subtracts are small near the query and the
+// rounding of a squared distance is relative to the local, not the global,
+// spread of the data.  Scale: sqrt(2) M, so that K_H(q - x) is proportional
+// to 2^-|y_q - y_x|^2 (M = sqrt(log2(e)/4) L^-1, H = L L^T).
 template <typename TIN>
-__global__ void k_whiten_queries(const DsDev* ds, const TIN* __restrict__ q, int64_t m, int64_t m_pad,
-                                 float* __restrict__ yq) {
+__global__ void k_eval_queries(const DsDev* ds, const TIN* __restrict__ q, int64_t m, int64_t m_pad,
+                               double* __restrict__ cent /* [q_tiles][KDE_MAX_D] */,
+                               float* __restrict__ yq /* [dk][m_pad] */) {
   const int d = ds->d, dk = ds->dk;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m_pad; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = j / kQT, j0 = t * kQT;
     float c[KDE_MAX_D] = {};
-    if (j < m)
-      for (int k = 0; k < d; ++k) c[k] = (float)((double)q[(int64_t)k * m + j] - ds->mean[k]);
+    for (int k = 0; k < d; ++k) {
+      const double ck = (double)q[(int64_t)k * m + j0];  // j0 < m: every tile starts with a query
+      if (j == j0) cent[t * KDE_MAX_D + k] = ck;
+      if (j < m) c[k] = (float)((double)q[(int64_t)k * m + j] - ck);
+    }
     for (int k = 0; k < dk; ++k) {
-      float t = 0.f;
+      float v = 0.f;
       if (k < d)
-        for (int i = 0; i <= k; ++i) t = fmaf(ds->M[k * KDE_MAX_D + i], c[i], t);
-      yq[(int64_t)k * m_pad + j] = 1.41421356237309505f * t;
+        for (int i = 0; i <= k; ++i) v = fmaf(ds->M[k * KDE_MAX_D + i], c[i], v);
+      yq[(int64_t)k * m_pad + j] = 1.41421356237309505f * v;
     }
   }
 }
 
-// items: (query tile, sample chunk); part[chunk][m_pad] FP64.
-template <int D>
+// items: (query tile, sample chunk); part[chunk][m_pad] FP64.  Each staged
+// sample is whitened against the tile's centre by the thread that loads it.
+template <typename TIN, int D>
 __global__ void __launch_bounds__(kThreads) k_eval(const DsDev* ds, const float* __restrict__ yq, int64_t m_pad,
                                                    int64_t q_tiles, int64_t chunk, int64_t n_chunks,
+                                                   const double* __restrict__ cent,
                                                    double* __restrict__ part) {
   __shared__ __align__(16) float sS[kSampleStage * D];
   __shared__ double sRed[kWarps][kQT];
+  __shared__ float sM[D * D];
+  __shared__ TIN sC[D];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t n = ds->n, n_pad = ds->n_pad;
-  const float* __restrict__ Y = ds->y;
+  const int64_t n = ds->n;
+  const int d = ds->d;
+  const TIN* __restrict__ X = static_cast<const TIN*>(ds->x);
+  for (int idx = threadIdx.x; idx < D * D; idx += kThreads) {
+    const int k = idx / D, i = idx - k * D;
+    sM[idx] = (k < d && i <= k) ? 1.41421356237309505f * ds->M[k * KDE_MAX_D + i] : 0.f;
+  }
   const int64_t items = q_tiles * n_chunks;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t qt = it % q_tiles, c = it / q_tiles;
-    float yqr[4][D];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int k = 0; k < D; ++k) yqr[r][k] = yq[(int64_t)k * m_pad + qt * kQT + lane + 32 * r];
+    if (threadIdx.x < D) sC[threadIdx.x] = threadIdx.x < d ? (TIN)cent[qt * KDE_MAX_D + threadIdx.x] : TIN(0);
     float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
     const int64_t j0 = c * chunk, j1 = min(j0 + chunk, n);
     for (int64_t jb = j0; jb < j1; jb += kSampleStage) {
       const int cnt = (int)min((int64_t)kSampleStage, j1 - jb);
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < kSampleStage * D; idx += kThreads) {
-        const int jj = idx / D, k = idx - jj * D;
-        sS[idx] = jj < cnt ? 1.41421356237309505f * Y[(int64_t)k * n_pad + jb + jj] : 0.f;
+      __syncthreads();  // previous readers of sS done; sC, sM visible
+#pragma unroll 1
+      for (int jj = threadIdx.x; jj < cnt; jj += kThreads) {
+        float u[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) u[k] = k < d ? (float)(X[(int64_t)k * n + jb + jj] - sC[k]) : 0.f;
+        // M is re-read from shared memory per sample (volatile): hoisting its
+        // D(D+1)/2 entries out of the loop would exhaust the registers at D = 16
+        const volatile float* vM = sM;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float v = 0.f;
+#pragma unroll
+          for (int i = 0; i <= k; ++i) v = fmaf(vM[k * D + i], u[i], v);
+          sS[jj * D + k] = v;
+        }
       }
       __syncthreads();
+      // the tile's queries (reloaded per stage: not live while samples are whitened)
+      float yqr[4][D];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) yqr[r][k] = yq[(int64_t)k * m_pad + qt * kQT + lane + 32 * r];
       float run[4] = {0.f, 0.f, 0.f, 0.f};
       // warp w walks samples w, w + 8, ... of the staged block
+      constexpr int kUnroll = D > 4 ? 1 : 4;  // wide samples carry enough independent work
+#pragma unroll kUnroll
       for (int jj = warp; jj < cnt; jj += kWarps) {
         float f[D];
 #pragma unroll
@@ -133,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
   __shared__ double sRed[kWarps][kRG][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = blockIdx.x * chunk, i1 = min(i0 + chunk, n);
-  const float inv_h = 1.f / h, inv_sqrt_2pi = 0.39894228040143268f;
+  const float inv_h = 1.f / h, h_phi = h * 0.39894228040143268f;  // h / sqrt(2 pi)
   for (int k0 = 0; k0 < m; k0 += kRG) {
     float sc[kRG], cc[kRG], ss[kRG], cs[kRG];
 #pragma unroll
@@ -145,9 +181,10 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
         if (k0 + g >= m) break;
         const float a = (rng[2 * (k0 + g)] - xi) * inv_h, b = (rng[2 * (k0 + g) + 1] - xi) * inv_h;
         const float P = cdf_diff(a, b);
-        const float pa = inv_sqrt_2pi * expf(-0.5f * a * a), pb = inv_sqrt_2pi * expf(-0.5f * b * b);
+        // phi(a) - phi(b) as one difference of exponentials: exactly 0 when a == b
+        const float ea = expf(-0.5f * a * a), eb = expf(-0.5f * b * b);
         kahan_add(sc[g], cc[g], P);
-        kahan_add(ss[g], cs[g], fmaf(xi, P, h * (pa - pb)));
+        kahan_add(ss[g], cs[g], fmaf(xi, P, h_phi * (ea - eb)));
       }
     }
 #pragma unroll
@@ -181,7 +218,7 @@ __global__ void k_aqp_finish(const double* __restrict__ part, int m, int64_t chu
 struct EvalLayout {
   Geometry g;
   int64_t m_pad, q_tiles, chunk, n_chunks;
-  size_t off_yq, off_part, off_f, total;
+  size_t off_yq, off_cent, off_part, off_f, total;
 };
 
 int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
@@ -197,12 +234,34 @@ int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
   size_t o = (L->g.total + 255) / 256 * 256;
   L->off_yq = o;
   o += ((size_t)L->g.dk * L->m_pad * 4 + 255) / 256 * 256;
+  L->off_cent = o;
+  o += ((size_t)L->q_tiles * KDE_MAX_D * 8 + 255) / 256 * 256;
   L->off_part = o;
   o += ((size_t)L->n_chunks * L->m_pad * 8 + 255) / 256 * 256;
   L->off_f = o;
   o += ((size_t)m * 8 + 255) / 256 * 256;
   L->total = o;
   return KDE_OK;
+}
+
+template <typename TIN, int D>
+void eval_launch(int grid, cudaStream_t st, const DsDev* ds, const float* yq, const EvalLayout& L,
+                 const double* cent, double* part) {
+  k_eval<TIN, D><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, cent, part);
+}
+
+template <typename TIN>
+void eval_dispatch(int dk, int grid, cudaStream_t st, const DsDev* ds, const float* yq,
+                   const EvalLayout& L, const double* cent, double* part) {
+  switch (dk) {
+    case 1: eval_launch<TIN, 1>(grid, st, ds, yq, L, cent, part); break;
+    case 2: eval_launch<TIN, 2>(grid, st, ds, yq, L, cent, part); break;
+    case 3: eval_launch<TIN, 3>(grid, st, ds, yq, L, cent, part); break;
+    case 4: eval_launch<TIN, 4>(grid, st, ds, yq, L, cent, part); break;
+    case 8: eval_launch<TIN, 8>(grid, st, ds, yq, L, cent, part); break;
+    case 12: eval_launch<TIN, 12>(grid, st, ds, yq, L, cent, part); break;
+    default: eval_launch<TIN, 16>(grid, st, ds, yq, L, cent, part); break;
+  }
 }
 
 struct AqpLayout {
@@ -252,6 +311,8 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
   unsigned char* w = static_cast<unsigned char*>(ws);
   DsDev init = make_desc(L.g, x_dev, dtype, KDE_METHOD_LSCV, w);
   init.given_H = 1;
+  init.y = nullptr;  // the prologue only checks and factors H; k_eval whitens per query tile
+  init.xc = nullptr;
   for (int a = 0; a < d; ++a)
     for (int b = 0; b < d; ++b) init.cov[a * d + b] = H_host[a * d + b];
   DsDev* ds = reinterpret_cast<DsDev*>(w + L.g.off_ds);
@@ -259,6 +320,7 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
   const double one = 1.0;
   const int64_t offs[4] = {0, 0, 0, 0};
   float* yq = reinterpret_cast<float*>(w + L.off_yq);
+  double* cent = reinterpret_cast<double*>(w + L.off_cent);
   double* part = reinterpret_cast<double*>(w + L.off_part);
   double* f = reinterpret_cast<double*>(w + L.off_f);
   cudaError_t e = launch_setup(ds, init, &one, 1, off, offs, 4, st);
@@ -266,23 +328,18 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
   if (e == cudaSuccess) {
     const int blocks = (int)std::min<int64_t>(1024, (L.m_pad + 255) / 256);
     if (dtype == KDE_F64)
-      k_whiten_queries<double><<<blocks, 256, 0, st>>>(ds, static_cast<const double*>(q_dev), m, L.m_pad, yq);
+      k_eval_queries<double><<<blocks, 256, 0, st>>>(ds, static_cast<const double*>(q_dev), m, L.m_pad, cent, yq);
     else
-      k_whiten_queries<float><<<blocks, 256, 0, st>>>(ds, static_cast<const float*>(q_dev), m, L.m_pad, yq);
+      k_eval_queries<float><<<blocks, 256, 0, st>>>(ds, static_cast<const float*>(q_dev), m, L.m_pad, cent, yq);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
     const int64_t items = L.q_tiles * L.n_chunks;
     const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * 2);
-    switch (L.g.dk) {
-      case 1: k_eval<1><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      case 2: k_eval<2><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      case 3: k_eval<3><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      case 4: k_eval<4><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      case 8: k_eval<8><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      case 12: k_eval<12><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-      default: k_eval<16><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, part); break;
-    }
+    if (dtype == KDE_F64)
+      eval_dispatch<double>(L.g.dk, grid, st, ds, yq, L, cent, part);
+    else
+      eval_dispatch<float>(L.g.dk, grid, st, ds, yq, L, cent, part);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {

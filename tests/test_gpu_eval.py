@@ -88,6 +88,7 @@ def test_eval_general_H_and_edge_sizes(kde):
     g = datagen.rng(7)
     d = 3
     H = datagen.random_spd(d, g, cond=20.0) * 0.05
+    H = 0.5 * (H + H.T)  # exactly symmetric, as the entry point requires
     x = datagen.correlated_mixture(700, d, seed=8)
     x64 = same(x)
     for q in (x[:, :1], x, np.concatenate([x, x + 0.01], axis=1)):
