@@ -426,6 +426,187 @@ def run_paper(args):
     return 0
 
 
+def run_configs(args):
+    """The n = 1,024 FP64 mixture (64-point grid on [0.01, 2] + plug-in) and
+    the d = 2, 3, 4, n = 16,384 correlated mixtures (128-point grid over
+    Z(h0)): GPU rate with samples resident (CUDA events around the LSCV
+    kernel, and around the whole selection), end to end from host samples,
+    and the FP64 oracle on the host cores (in full for n = 1,024, on rows of
+    the pair triangle for the d > 1 sets)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probe = gbkde.kde_probe_alu()
+    per_clk = min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
+    peak = per_clk * probe["sm_count"] * 2070.0 * 1e6
+    cores = oracle.openmp_threads() or 1
+    K = max(3, args.steps)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    out = []
+
+    def median_ms(fn, kernel_events=False):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        call, kern = [], []
+        for _ in range(K):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e1.record(stream)
+            if kernel_events:
+                gbkde.kde_set_kernel_events(e0, e1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            call.append(time.perf_counter() - t0)
+            gbkde.kde_set_kernel_events()
+            kern.append(e0.elapsed_time(e1) if kernel_events else 0.0)
+        return 1e3 * statistics.median(call), statistics.median(kern)
+
+    # n = 1,024 FP64 mixture
+    n = 1024
+    x = datagen.mixture_1d(n, seed=1)
+    xd = torch.from_numpy(x).cuda()
+    h = oracle.grid_log(0.01, 2.0, 64)
+    grid, _keep = gbkde.make_grid(h=h)
+    ws = gbkde.workspace(max(gbkde.kde_workspace_size(n, 1, 64), gbkde.kde_workspace_size(n, 1, 0)))
+    P = n * (n - 1) // 2
+    evals = P * (64 + 2)
+    sel_ms, _ = median_ms(lambda: (gbkde.kde_lscv(xd, grid, None, ws, stream), gbkde.kde_plugin(xd, None, ws, stream)))
+    _, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True)
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    e2e_ms, _ = median_ms(lambda: (gbkde.kde_lscv_host(xh, grid, None, ws, stream),
+                                   gbkde.kde_plugin_host(xh, None, ws, stream)))
+    t0 = time.perf_counter()
+    oracle.lscv_h(x, h)
+    oracle.plugin(x)
+    o_s = time.perf_counter() - t0
+    out.append({"config": "n=1024 FP64 mixture, 64-point LSCV on [0.01, 2] + plug-in", "evals": evals,
+                "selection_ms": sel_ms, "evals_per_s": evals / (sel_ms * 1e-3),
+                "lscv_kernel_ms": kern_ms, "lscv_kernel_evals_per_s": P * 64 / (kern_ms * 1e-3),
+                "lscv_kernel_frac": P * 64 / (kern_ms * 1e-3) / peak, "e2e_ms": e2e_ms,
+                "oracle_full_s": o_s, "oracle_evals_per_s": evals / o_s, "oracle_cores": cores})
+    # d = 2, 3, 4, n = 16,384
+    n = 16384
+    P = n * (n - 1) // 2
+    for d in (2, 3, 4):
+        x = datagen.correlated_mixture(n, d, seed=3 + d)
+        xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        grid, _keep = gbkde.make_grid(n_h=128)
+        ws = gbkde.workspace(gbkde.kde_workspace_size(n, d, 128))
+        sel_ms, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True)
+        xh = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory().numpy()
+        e2e_ms, _ = median_ms(lambda: gbkde.kde_lscv_host(xh, grid, None, ws, stream))
+        x64 = np.asarray(x, dtype=np.float32).astype(np.float64)
+        hh = oracle.grid_default(n, d, 128)
+        rows = 8 * cores
+        t0 = time.perf_counter()
+        oracle.lscv_sums(x64, hh, block=(0, rows, 0, n))
+        o_s = time.perf_counter() - t0
+        o_pairs = sum(n - 1 - i for i in range(rows))
+        out.append({"config": f"d={d} n=16384 correlated mixture, 128-point LSCV over Z(h0)",
+                    "evals": P * 128, "selection_ms": sel_ms, "evals_per_s": P * 128 / (sel_ms * 1e-3),
+                    "lscv_kernel_ms": kern_ms, "lscv_kernel_evals_per_s": P * 128 / (kern_ms * 1e-3),
+                    "lscv_kernel_frac": P * 128 / (kern_ms * 1e-3) / peak, "e2e_ms": e2e_ms,
+                    "oracle_evals_per_s": o_pairs * 128 / o_s, "oracle_cores": cores,
+                    "oracle_sample": f"rows 0..{rows - 1} of the pair triangle ({o_pairs} pairs, {o_s:.1f} s)"})
+    clocks = sampler.stop()
+    print(json.dumps({"workload": "configs", "peak_evals_per_s_2070mhz": peak, "results": out,
+                      "clocks": clocks}), flush=True)
+    return 0
+
+
+def run_consumers(args):
+    """Consumers of a selected bandwidth (Sec. 4.2, 4.3): the density estimate
+    at query points (query x sample pairs, one exp2 each) and the range
+    Count / Sum of one column (sample x range terms).  Per instance: the call
+    end to end (perf_counter, results on the host), the pair kernel alone
+    (CUDA events on the launching stream) and its ALU roofline."""
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    probe = gbkde.kde_probe_alu()
+    K = max(1, args.steps)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    out = []
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        call, kern = [], []
+        for _ in range(K):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)  # torch creates the CUDA event at its first record
+            e1.record(stream)
+            gbkde.kde_set_kernel_events(e0, e1)
+            t0 = time.perf_counter()
+            fn()
+            call.append(time.perf_counter() - t0)
+            gbkde.kde_set_kernel_events()
+            kern.append(e0.elapsed_time(e1))
+        return 1e3 * statistics.median(call), statistics.median(kern)
+
+    def alu_peak(fp32_per_eval, mufu_per_eval):
+        per_clk = min(probe["mufu_ex2_per_clk_sm"] / mufu_per_eval,
+                      probe["ffma_lanes_per_clk_sm"] / fp32_per_eval)
+        return per_clk * probe["sm_count"] * 2070.0 * 1e6
+
+    for d, n, m in ((1, 65536, 65536), (4, 65536, 16384), (16, 16384, 16384)):
+        x = (datagen.skewed_column(n, seed=2) if d == 1 else datagen.correlated_mixture(n, d, seed=30 + d))
+        xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        S = np.atleast_2d(np.cov(x.astype(np.float64)))
+        H = (0.25 if d > 1 else 0.01) * 0.5 * (S + S.T)
+        g = datagen.rng(50 + d)
+        lo, hi = x.min(axis=1), x.max(axis=1)
+        q = (lo[:, None] + (hi - lo)[:, None] * g.uniform(size=(d, m))).astype(np.float32)
+        if d == 1:
+            q = np.linspace(lo[0], hi[0], m, dtype=np.float32)[None, :]
+        qd = torch.from_numpy(np.ascontiguousarray(q)).cuda()
+        ws = gbkde.workspace(gbkde.kde_eval_workspace_size(n, d, m))
+        call_ms, kern_ms = timed(lambda: gbkde.kde_eval(xd, H, qd, ws, stream))
+        evals = float(n) * m
+        fp32 = 2 * d + 1  # per pair: d differences, d squared-distance FMAs, the running add
+        peak = alu_peak(fp32, 1.0)
+        out.append({"instance": f"kde_eval d={d} n={n} m={m}", "evals": evals,
+                    "call_ms": call_ms, "kernel_ms": kern_ms,
+                    "kernel_evals_per_s": evals / (kern_ms * 1e-3),
+                    "call_evals_per_s": evals / (call_ms * 1e-3),
+                    "roofline": {"bound": "alu", "peak_evals_per_s": peak,
+                                 "frac": evals / (kern_ms * 1e-3) / peak,
+                                 "basis": f"min(MUFU 1 ex2, FP32 {fp32} lanes) per pair at 2070 MHz"}})
+    n, m = 1 << 24, 64
+    x = datagen.skewed_column(n, seed=3)
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+    g = datagen.rng(60)
+    lo = np.quantile(x[0][:: 64], g.uniform(0, 0.9, m))
+    hi = lo + g.uniform(0, 1.0, m) * float(x.std())
+    ws = gbkde.workspace(gbkde.kde_aqp_workspace_size(n, m))
+    call_ms, kern_ms = timed(lambda: gbkde.kde_aqp(xd, 0.3, lo, hi, ws, stream))
+    terms = float(n) * m
+    out.append({"instance": f"kde_aqp n={n} ranges={m}", "terms": terms, "call_ms": call_ms,
+                "kernel_ms": kern_ms, "kernel_terms_per_s": terms / (kern_ms * 1e-3),
+                "call_terms_per_s": terms / (call_ms * 1e-3)})
+    clocks = sampler.stop()
+    print(json.dumps({"workload": "consumers", "instances": out, "clocks": clocks,
+                      "alu_probe": probe}), flush=True)
+    return 0
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def main():
@@ -438,9 +619,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--n", type=int, default=N,
                     help="sample count (default 65536; smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=("selection", "batch", "serve", "paper"), default="selection",
+    ap.add_argument("--workload", choices=("selection", "batch", "serve", "paper", "consumers", "configs"),
+                    default="selection",
                     help="selection (default): the benchmark line; batch / serve: the batched and "
                          "served workloads, printed as their own JSON lines")
+    ap.add_argument("--precision", choices=("kahan", "plain"), default="kahan",
+                    help="per-thread summation of the pair kernels (selection workload)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--autotune", action="store_true",
                     help="batch workload: tune the small-size buckets before planning")
@@ -458,6 +642,10 @@ def main():
         return run_serve(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "consumers":
+        return run_consumers(args)
+    if args.workload == "configs":
+        return run_configs(args)
     return run_gpu(args, world, rank, local)
 
 
@@ -478,15 +666,16 @@ def run_gpu(args, world, rank, local):
     x = datagen.skewed_column(N, seed=SEED + rank)
     xd = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
     grid, _keep = gbkde.make_grid(n_h=N_H)
-    ws_l = gbkde.workspace(gbkde.kde_workspace_size(N, 1, N_H), dev)
-    ws_p = gbkde.workspace(gbkde.kde_workspace_size(N, 1, 0), dev)
+    opts = gbkde.make_opts(precision=gbkde.KDE_FP32_PLAIN if args.precision == "plain" else gbkde.KDE_FP32_KAHAN)
+    ws_l = gbkde.workspace(gbkde.kde_workspace_size(N, 1, N_H, opts), dev)
+    ws_p = gbkde.workspace(gbkde.kde_workspace_size(N, 1, 0, opts), dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     probe = gbkde.kde_probe_alu()
 
     def step():
-        gbkde.kde_lscv_async(xd, grid, None, ws_l, stream)
-        gbkde.kde_plugin_async(xd, None, ws_p, stream)
+        gbkde.kde_lscv_async(xd, grid, opts, ws_l, stream)
+        gbkde.kde_plugin_async(xd, opts, ws_p, stream)
 
     W, K = max(3, args.warmup), args.steps
     for _ in range(W):
@@ -535,8 +724,8 @@ def run_gpu(args, world, rank, local):
     x_pin = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     xh = x_pin.numpy()
     for _ in range(W):
-        gbkde.kde_lscv_host(xh, grid, None, ws_l, stream)
-        gbkde.kde_plugin_host(xh, None, ws_p, stream)
+        gbkde.kde_lscv_host(xh, grid, opts, ws_l, stream)
+        gbkde.kde_plugin_host(xh, opts, ws_p, stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -545,8 +734,8 @@ def run_gpu(args, world, rank, local):
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        gbkde.kde_lscv_host(xh, grid, None, ws_l, stream)
-        gbkde.kde_plugin_host(xh, None, ws_p, stream)
+        gbkde.kde_lscv_host(xh, grid, opts, ws_l, stream)
+        gbkde.kde_plugin_host(xh, opts, ws_p, stream)
         e2e_s += time.perf_counter() - t1
     if dist:
         t = torch.tensor([e2e_s], device=dev)
@@ -579,7 +768,9 @@ def run_gpu(args, world, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": N, "d": 1, "n_h": N_H,
                        "evals_per_step": EVALS_STEP, "seed": SEED,
-                       "precision": "fp32 terms, Kahan fp32 per-thread sums, fp64 reductions",
+                       "precision": ("fp32 terms, plain fp32 per-thread sums, fp64 reductions"
+                                     if args.precision == "plain" else
+                                     "fp32 terms, Kahan fp32 per-thread sums, fp64 reductions"),
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

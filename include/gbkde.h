@@ -520,7 +520,8 @@ int kde_autotune_load(const char* path);
  * handles created by the caller), the next LSCV_h / PLUGIN calls of this
  * thread record lscv_begin / lscv_end on their stream immediately around the
  * launch of the all-pairs LSCV kernel, and psi_begin / psi_end around the
- * first all-pairs psi kernel.  Pass NULLs to clear.  Never fails. */
+ * first all-pairs psi kernel; kde_eval and kde_aqp record lscv_begin /
+ * lscv_end around their query x sample (range x sample) kernel.  Pass NULLs to clear.  Never fails. */
 int kde_set_kernel_events(void* lscv_begin, void* lscv_end, void* psi_begin, void* psi_end);
 
 /* Sustained per-SM throughput of the units the pair kernels are bound by,

@@ -336,11 +336,13 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
   if (e == cudaSuccess) {
     const int64_t items = L.q_tiles * L.n_chunks;
     const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * 2);
+    e = mark_event(0, st);
     if (dtype == KDE_F64)
       eval_dispatch<double>(L.g.dk, grid, st, ds, yq, L, cent, part);
     else
       eval_dispatch<float>(L.g.dk, grid, st, ds, yq, L, cent, part);
-    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = mark_event(1, st);
   }
   if (e == cudaSuccess) {
     k_eval_finish<<<(int)std::min<int64_t>(1024, (m + 255) / 256), 256, 0, st>>>(ds, part, m, L.m_pad, L.n_chunks, f);
@@ -385,6 +387,7 @@ int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(rng, r2.data(), sizeof(float) * 2 * m, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = mark_event(0, st);
   if (e == cudaSuccess) {
     if (dtype == KDE_F64)
       k_aqp<double><<<(int)chunks, kThreads, 0, st>>>(static_cast<const double*>(x_dev), n, (float)h, rng, m, chunk, part);
@@ -392,6 +395,7 @@ int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_
       k_aqp<float><<<(int)chunks, kThreads, 0, st>>>(static_cast<const float*>(x_dev), n, (float)h, rng, m, chunk, part);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = mark_event(1, st);
   if (e == cudaSuccess) {
     k_aqp_finish<<<1, 256, 0, st>>>(part, m, chunks, out);
     e = cudaGetLastError();
