@@ -24,8 +24,18 @@ using namespace gbkde;
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kQT = 128;          // queries per item (4 per lane)
-constexpr int kSampleStage = 512; // samples staged per pass
+// Queries per lane: 8 for narrow samples (the per-sample shared-memory load
+// and loop overhead spread over more evaluations), 4 for wide ones
+// (registers).  A query tile is the 32 lanes' queries.
+__host__ __device__ constexpr int qpl_of(int dk) { return dk <= 4 ? 8 : 4; }
+__host__ __device__ constexpr int qtile_of(int dk) { return 32 * qpl_of(dk); }
+
+// 2^-a (the negation folded into the exponential's operand).
+__device__ __forceinline__ float ex2_neg(float a) {
+  float r;
+  asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "=f"(r) : "f"(a));
+  return r;
+}
 
 // Every query tile t has a centre c_t (its first query).  Queries and samples
 // are whitened relative to the centre of the tile they meet, so the FP32
@@ -37,9 +47,9 @@ template <typename TIN>
 __global__ void k_eval_queries(const DsDev* ds, const TIN* __restrict__ q, int64_t m, int64_t m_pad,
                                double* __restrict__ cent /* [q_tiles][KDE_MAX_D] */,
                                float* __restrict__ yq /* [dk][m_pad] */) {
-  const int d = ds->d, dk = ds->dk;
+  const int d = ds->d, dk = ds->dk, qt = qtile_of(dk);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m_pad; j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = j / kQT, j0 = t * kQT;
+    const int64_t t = j / qt, j0 = t * qt;
     float c[KDE_MAX_D] = {};
     for (int k = 0; k < d; ++k) {
       const double ck = (double)q[(int64_t)k * m + j0];  // j0 < m: every tile starts with a query
@@ -55,15 +65,65 @@ __global__ void k_eval_queries(const DsDev* ds, const TIN* __restrict__ q, int64
   }
 }
 
+// Samples staged per pass: wide samples cap the shared memory, narrow ones
+// take long passes (fewer barriers per evaluation).
+template <int D>
+constexpr int kStage = D <= 4 ? 2048 : 512;
+
+// Shared-memory reads of staged samples: one float4 covers 4 / D samples for
+// D = 1, 2, one sample for D = 4 k; D = 3 reads single floats.
+template <int D>
+struct SampleVec {
+  static constexpr int per = D == 1 ? 4 : D == 2 ? 2 : 1;   // samples per read group
+  static constexpr bool vec = (D % 4 == 0) || D == 1 || D == 2;
+  static __device__ __forceinline__ void load(const float* p, float (&v)[per * D]) {
+    if constexpr (vec) {
+#pragma unroll
+      for (int u = 0; u < per * D / 4; ++u) {
+        const float4 t = reinterpret_cast<const float4*>(p)[u];
+        v[4 * u] = t.x, v[4 * u + 1] = t.y, v[4 * u + 2] = t.z, v[4 * u + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < per * D; ++k) v[k] = p[k];
+    }
+  }
+};
+
+// One staged sample (negated, whitened: nf = -y_x) against the lane's queries.
+template <int D, int NP>
+__device__ __forceinline__ void eval_sample(const float* nf, const float2 (&yq2)[NP][D], float2 (&run)[NP]) {
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    float2 q = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float2 dl = __fadd2_rn(yq2[p][k], make_float2(nf[k], nf[k]));
+      q = __ffma2_rn(dl, dl, q);
+    }
+    run[p] = __fadd2_rn(run[p], make_float2(ex2_neg(q.x), ex2_neg(q.y)));
+  }
+}
+
 // items: (query tile, sample chunk); part[chunk][m_pad] FP64.  Each staged
-// sample is whitened against the tile's centre by the thread that loads it.
+// sample is whitened against the tile's centre by the thread that loads it
+// and stored negated, so the pair loop forms y_q - y_x with one packed add.
+// Each lane holds QPL queries as FP32x2 pairs (lane + 32 i); each warp walks
+// a contiguous slice of the staged samples with vector loads.
 template <typename TIN, int D>
 __global__ void __launch_bounds__(kThreads) k_eval(const DsDev* ds, const float* __restrict__ yq, int64_t m_pad,
                                                    int64_t q_tiles, int64_t chunk, int64_t n_chunks,
                                                    const double* __restrict__ cent,
                                                    double* __restrict__ part) {
-  __shared__ __align__(16) float sS[kSampleStage * D];
-  __shared__ double sRed[kWarps][kQT];
+  constexpr int ST = kStage<D>;
+  constexpr int QPL = qpl_of(D), NP = QPL / 2, QT = 32 * QPL;
+  constexpr bool kResident = D <= 4;  // queries stay in registers across passes
+  using SV = SampleVec<D>;
+  // staged samples during the passes, the per-warp query sums after them
+  constexpr int kBuf = ST * D * 4 > kWarps * QT * 8 ? ST * D * 4 : kWarps * QT * 8;
+  __shared__ __align__(16) unsigned char sBuf[kBuf];
+  float* sS = reinterpret_cast<float*>(sBuf);
+  double(*sRed)[QT] = reinterpret_cast<double(*)[QT]>(sBuf);
   __shared__ float sM[D * D];
   __shared__ TIN sC[D];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -72,16 +132,30 @@ __global__ void __launch_bounds__(kThreads) k_eval(const DsDev* ds, const float*
   const TIN* __restrict__ X = static_cast<const TIN*>(ds->x);
   for (int idx = threadIdx.x; idx < D * D; idx += kThreads) {
     const int k = idx / D, i = idx - k * D;
-    sM[idx] = (k < d && i <= k) ? 1.41421356237309505f * ds->M[k * KDE_MAX_D + i] : 0.f;
+    // sqrt(2) M, negated: staged samples are -y_x
+    sM[idx] = (k < d && i <= k) ? -1.41421356237309505f * ds->M[k * KDE_MAX_D + i] : 0.f;
   }
   const int64_t items = q_tiles * n_chunks;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t qt = it % q_tiles, c = it / q_tiles;
     if (threadIdx.x < D) sC[threadIdx.x] = threadIdx.x < d ? (TIN)cent[qt * KDE_MAX_D + threadIdx.x] : TIN(0);
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    float2 yq2[NP][D];  // pair p: queries lane + 64 p and lane + 64 p + 32 of the tile
+    auto load_queries = [&]() {
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float* col = yq + (int64_t)k * m_pad + qt * QT + lane + 64 * p;
+          yq2[p][k] = make_float2(col[0], col[32]);
+        }
+    };
+    if (kResident) load_queries();
+    float s[QPL], cc[QPL];
+#pragma unroll
+    for (int r = 0; r < QPL; ++r) s[r] = cc[r] = 0.f;
     const int64_t j0 = c * chunk, j1 = min(j0 + chunk, n);
-    for (int64_t jb = j0; jb < j1; jb += kSampleStage) {
-      const int cnt = (int)min((int64_t)kSampleStage, j1 - jb);
+    for (int64_t jb = j0; jb < j1; jb += ST) {
+      const int cnt = (int)min((int64_t)ST, j1 - jb);
       __syncthreads();  // previous readers of sS done; sC, sM visible
 #pragma unroll 1
       for (int jj = threadIdx.x; jj < cnt; jj += kThreads) {
@@ -100,43 +174,42 @@ __global__ void __launch_bounds__(kThreads) k_eval(const DsDev* ds, const float*
         }
       }
       __syncthreads();
-      // the tile's queries (reloaded per stage: not live while samples are whitened)
-      float yqr[4][D];
+      if (!kResident) load_queries();  // not live while samples are whitened
+      float2 run[NP];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int k = 0; k < D; ++k) yqr[r][k] = yq[(int64_t)k * m_pad + qt * kQT + lane + 32 * r];
-      float run[4] = {0.f, 0.f, 0.f, 0.f};
-      // warp w walks samples w, w + 8, ... of the staged block
-      constexpr int kUnroll = D > 4 ? 1 : 4;  // wide samples carry enough independent work
+      for (int p = 0; p < NP; ++p) run[p] = make_float2(0.f, 0.f);
+      // warp w: samples [a, b), a contiguous slice in whole read groups
+      const int slice = ((cnt + kWarps - 1) / kWarps + SV::per - 1) / SV::per * SV::per;
+      const int a = min(cnt, warp * slice), b = min(cnt, a + slice);
+      const int bv = a + (b - a) / SV::per * SV::per;
+      constexpr int kUnroll = D > 4 ? 1 : 2;
 #pragma unroll kUnroll
-      for (int jj = warp; jj < cnt; jj += kWarps) {
-        float f[D];
+      for (int jj = a; jj < bv; jj += SV::per) {
+        float v[SV::per * D];
+        SV::load(sS + jj * D, v);
 #pragma unroll
-        for (int k = 0; k < D; ++k) f[k] = sS[jj * D + k];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          float Q = 0.f;
-#pragma unroll
-          for (int k = 0; k < D; ++k) {
-            const float dl = yqr[r][k] - f[k];
-            Q = fmaf(dl, dl, Q);
-          }
-          run[r] += ex2(-Q);
-        }
+        for (int u = 0; u < SV::per; ++u) eval_sample<D, NP>(v + u * D, yq2, run);
       }
+      for (int jj = bv; jj < b; ++jj) eval_sample<D, NP>(sS + jj * D, yq2, run);
 #pragma unroll
-      for (int r = 0; r < 4; ++r) kahan_add(s[r], cc[r], run[r]);
+      for (int p = 0; p < NP; ++p) {
+        kahan_add(s[2 * p], cc[2 * p], run[p].x);
+        kahan_add(s[2 * p + 1], cc[2 * p + 1], run[p].y);
+      }
     }
-    // combine the 8 warps (each saw every query of the tile) in fixed order
-    __syncthreads();
+    // combine the 8 warps (each saw every query of the tile) in fixed order;
+    // s[2p], s[2p + 1] hold queries lane + 64 p and lane + 64 p + 32
+    __syncthreads();  // the sample buffer becomes sRed
 #pragma unroll
-    for (int r = 0; r < 4; ++r) sRed[warp][lane + 32 * r] = (double)s[r] - (double)cc[r];
+    for (int p = 0; p < NP; ++p) {
+      sRed[warp][lane + 64 * p] = (double)s[2 * p] - (double)cc[2 * p];
+      sRed[warp][lane + 64 * p + 32] = (double)s[2 * p + 1] - (double)cc[2 * p + 1];
+    }
     __syncthreads();
-    for (int qq = threadIdx.x; qq < kQT; qq += kThreads) {
+    for (int qq = threadIdx.x; qq < QT; qq += kThreads) {
       double t = 0.0;
       for (int w = 0; w < kWarps; ++w) t += sRed[w][qq];
-      part[c * m_pad + qt * kQT + qq] = t;
+      part[c * m_pad + qt * QT + qq] = t;
     }
   }
 }
@@ -224,12 +297,14 @@ struct EvalLayout {
 int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
   int rc = make_geometry(n, d, 1, nullptr, sms, &L->g);
   if (rc) return rc;
-  L->m_pad = (m + kQT - 1) / kQT * kQT;
-  L->q_tiles = L->m_pad / kQT;
-  // sample chunks: about 4 items per CTA over the whole launch, whole stage blocks
-  const int64_t ctas = (int64_t)std::max(1, sms) * 2;
-  int64_t want = std::max<int64_t>(1, (4 * ctas + L->q_tiles - 1) / L->q_tiles);
-  L->chunk = std::max<int64_t>(kSampleStage, (n + want - 1) / want / kSampleStage * kSampleStage);
+  const int qt = qtile_of(L->g.dk);
+  L->m_pad = (m + qt - 1) / qt * qt;
+  L->q_tiles = L->m_pad / qt;
+  // sample chunks (multiples of 256): about 16 items per SM over the launch.
+  // Finer chunks balance the last round better but cost more per-item work
+  // (staging, reductions): 64 items per SM measured 4 % slower at d = 1.
+  const int64_t want = std::max<int64_t>(1, (16 * (int64_t)std::max(1, sms) + L->q_tiles - 1) / L->q_tiles);
+  L->chunk = std::max<int64_t>(256, ((n + want - 1) / want + 255) / 256 * 256);
   L->n_chunks = (n + L->chunk - 1) / L->chunk;
   size_t o = (L->g.total + 255) / 256 * 256;
   L->off_yq = o;
@@ -244,23 +319,34 @@ int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
   return KDE_OK;
 }
 
+// Persistent grid: every CTA that fits on the device at once (occupancy of
+// this instance, looked up once), at most one per item.
 template <typename TIN, int D>
-void eval_launch(int grid, cudaStream_t st, const DsDev* ds, const float* yq, const EvalLayout& L,
-                 const double* cent, double* part) {
+cudaError_t eval_launch(cudaStream_t st, const DsDev* ds, const float* yq, const EvalLayout& L,
+                        const double* cent, double* part) {
+  static int per_sm = 0;
+  if (!per_sm) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<TIN, D>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, per_sm);
+  }
+  const int64_t items = L.q_tiles * L.n_chunks;
+  const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * per_sm);
   k_eval<TIN, D><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, cent, part);
+  return cudaGetLastError();
 }
 
 template <typename TIN>
-void eval_dispatch(int dk, int grid, cudaStream_t st, const DsDev* ds, const float* yq,
-                   const EvalLayout& L, const double* cent, double* part) {
+cudaError_t eval_dispatch(int dk, cudaStream_t st, const DsDev* ds, const float* yq,
+                          const EvalLayout& L, const double* cent, double* part) {
   switch (dk) {
-    case 1: eval_launch<TIN, 1>(grid, st, ds, yq, L, cent, part); break;
-    case 2: eval_launch<TIN, 2>(grid, st, ds, yq, L, cent, part); break;
-    case 3: eval_launch<TIN, 3>(grid, st, ds, yq, L, cent, part); break;
-    case 4: eval_launch<TIN, 4>(grid, st, ds, yq, L, cent, part); break;
-    case 8: eval_launch<TIN, 8>(grid, st, ds, yq, L, cent, part); break;
-    case 12: eval_launch<TIN, 12>(grid, st, ds, yq, L, cent, part); break;
-    default: eval_launch<TIN, 16>(grid, st, ds, yq, L, cent, part); break;
+    case 1: return eval_launch<TIN, 1>(st, ds, yq, L, cent, part);
+    case 2: return eval_launch<TIN, 2>(st, ds, yq, L, cent, part);
+    case 3: return eval_launch<TIN, 3>(st, ds, yq, L, cent, part);
+    case 4: return eval_launch<TIN, 4>(st, ds, yq, L, cent, part);
+    case 8: return eval_launch<TIN, 8>(st, ds, yq, L, cent, part);
+    case 12: return eval_launch<TIN, 12>(st, ds, yq, L, cent, part);
+    default: return eval_launch<TIN, 16>(st, ds, yq, L, cent, part);
   }
 }
 
@@ -334,14 +420,10 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    const int64_t items = L.q_tiles * L.n_chunks;
-    const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * 2);
     e = mark_event(0, st);
-    if (dtype == KDE_F64)
-      eval_dispatch<double>(L.g.dk, grid, st, ds, yq, L, cent, part);
-    else
-      eval_dispatch<float>(L.g.dk, grid, st, ds, yq, L, cent, part);
-    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess)
+      e = dtype == KDE_F64 ? eval_dispatch<double>(L.g.dk, st, ds, yq, L, cent, part)
+                           : eval_dispatch<float>(L.g.dk, st, ds, yq, L, cent, part);
     if (e == cudaSuccess) e = mark_event(1, st);
   }
   if (e == cudaSuccess) {
