@@ -480,9 +480,11 @@ int kde_aqp_workspace_size(int64_t n, int m, size_t* bytes);
  * memory; lo_host, hi_host: m <= KDE_MAX_NH bounds with lo <= hi (either may
  * be infinite; NaN is rejected), rounded to FP32.
  * count_host / sum_host: m doubles each, either may be NULL.  Arithmetic per
- * sample in FP32 (cdf differences taken from the smaller tails), FP32 Kahan
- * sums per thread, FP64 across threads; deterministic.  Synchronises the
- * stream.  Errors: KDE_EINVAL, KDE_ENOMEM, KDE_ECUDA. */
+ * sample in FP32 (cdf differences taken from the smaller tails; a range end
+ * more than 7 h from a sample counts as infinitely far, which changes a term
+ * by at most Phi(-7) = 1.3e-12, below its FP32 rounding), FP32 runs per
+ * thread and range, FP64 across threads; deterministic.  Synchronises the stream.  Errors: KDE_EINVAL, KDE_ENOMEM,
+ * KDE_ECUDA. */
 int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_host,
             const double* hi_host, int m, void* ws, size_t ws_bytes, void* stream,
             double* count_host, double* sum_host);

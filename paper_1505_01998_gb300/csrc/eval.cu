@@ -10,7 +10,8 @@
 // reduced in fixed order.
 // kde_aqp: for every sample and range, the exact integral of its Gaussian
 // term over the range (normal cdf differences, tails taken from the nearer
-// side); per-thread Kahan sums, FP64 across threads and items.
+// side), with samples far from the range's ends classified without cdfs and
+// the rest evaluated on compacted full warps; FP64 across threads and CTAs.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -233,48 +234,97 @@ __device__ __forceinline__ float cdf_diff(float a, float b) {
   return 1.f - 0.5f * (erfcf(b * r) + erfcf(-a * r));
 }
 
-constexpr int kRG = 8;  // ranges per pass of a thread
+// Beyond this many bandwidths from a range's end a sample's Gaussian lies on
+// one side of it up to Phi(-7) = 1.3e-12 of its mass (phi(7) = 9.1e-12), far
+// below the FP32 rounding of a term: that end contributes 0 or 1 to the cdf
+// difference and nothing to the pdf difference.
+constexpr float kAqpFar = 7.f;
+constexpr int kAqpChunk = 11264;  // samples per CTA, held in shared memory (44 KB)
 
+// Count / Sum terms of one sample and range from the normal cdf and pdf.
+// With one end far (the usual case) one cdf and one pdf suffice: for a far
+// upper end P = Phi(inf) - Phi(a) = erfc(a / sqrt 2) / 2 and only phi(a)
+// remains; for a far lower end P = Phi(b) = erfc(-b / sqrt 2) / 2 and only
+// -phi(b) remains.  Both take the same instructions (t = a or -b), so the
+// warp does not diverge between them.
+__device__ __forceinline__ void aqp_full(float xi, float lo, float hi, float inv_h, float h_phi,
+                                         float& cnt, float& sum) {
+  const float a = (lo - xi) * inv_h, b = (hi - xi) * inv_h;
+  const bool up_far = b >= kAqpFar, lo_far = a <= -kAqpFar;
+  float P, dphi;
+  if (up_far || lo_far) {
+    const float t = up_far ? a : -b;
+    P = 0.5f * erfcf(t * 0.70710678118654752f);
+    const float e = expf(-0.5f * t * t);
+    dphi = up_far ? e : -e;
+  } else {
+    P = cdf_diff(a, b);
+    // phi(a) - phi(b) as one difference of exponentials: exactly 0 when a == b
+    dphi = expf(-0.5f * a * a) - expf(-0.5f * b * b);
+  }
+  cnt += P;
+  sum += fmaf(xi, P, h_phi * dphi);
+}
+
+// One CTA per chunk of samples (staged in shared memory as FP32), ranges in
+// turn.  Per range every warp classifies its slice of the chunk: samples far
+// inside or outside the range take the closed values; the rest are queued in
+// a per-warp ring (ballot + prefix count) and evaluated 32 at a time, so the
+// cdf work runs on full warps.  Per-range FP32 runs per lane, FP64 across
+// lanes and warps; part[chunk][range][2].
 template <typename TIN>
 __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int64_t n, float h,
                                                   const float* __restrict__ rng /* [m][2] */, int m,
-                                                  int64_t chunk, double* __restrict__ part /* [chunks][m][2] */) {
-  __shared__ double sRed[kWarps][kRG][2];
+                                                  int64_t chunk, double* __restrict__ part) {
+  __shared__ float sX[kAqpChunk];
+  __shared__ float sQ[kWarps][64];
+  __shared__ double sRed[kWarps][2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i0 = blockIdx.x * chunk, i1 = min(i0 + chunk, n);
+  const int64_t i0 = blockIdx.x * chunk;
+  const int cnt_x = (int)min(chunk, n - i0);
+  for (int i = threadIdx.x; i < cnt_x; i += kThreads) sX[i] = (float)x[i0 + i];
+  __syncthreads();
   const float inv_h = 1.f / h, h_phi = h * 0.39894228040143268f;  // h / sqrt(2 pi)
-  for (int k0 = 0; k0 < m; k0 += kRG) {
-    float sc[kRG], cc[kRG], ss[kRG], cs[kRG];
-#pragma unroll
-    for (int g = 0; g < kRG; ++g) sc[g] = cc[g] = ss[g] = cs[g] = 0.f;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += kThreads) {
-      const float xi = (float)x[i];
-#pragma unroll
-      for (int g = 0; g < kRG; ++g) {
-        if (k0 + g >= m) break;
-        const float a = (rng[2 * (k0 + g)] - xi) * inv_h, b = (rng[2 * (k0 + g) + 1] - xi) * inv_h;
-        const float P = cdf_diff(a, b);
-        // phi(a) - phi(b) as one difference of exponentials: exactly 0 when a == b
-        const float ea = expf(-0.5f * a * a), eb = expf(-0.5f * b * b);
-        kahan_add(sc[g], cc[g], P);
-        kahan_add(ss[g], cs[g], fmaf(xi, P, h_phi * (ea - eb)));
+  const int slice = (cnt_x + kWarps - 1) / kWarps;
+  const int s0 = min(cnt_x, warp * slice), s1 = min(cnt_x, s0 + slice);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int g = 0; g < m; ++g) {
+    const float lo = rng[2 * g], hi = rng[2 * g + 1];
+    float c_run = 0.f, s_run = 0.f;
+    int qh = 0, qn = 0;  // ring head and fill (warp-uniform)
+    for (int i = s0; i < s1; i += 32) {
+      const bool valid = i + lane < s1;
+      const float xi = valid ? sX[i + lane] : 0.f;
+      const float a = (lo - xi) * inv_h, b = (hi - xi) * inv_h;
+      const bool inside = a <= -kAqpFar && b >= kAqpFar;
+      const bool outside = a >= kAqpFar || b <= -kAqpFar;
+      if (valid && inside) {
+        c_run += 1.f;
+        s_run += xi;
+      }
+      const unsigned need = __ballot_sync(0xffffffffu, valid && !inside && !outside);
+      if (valid && !inside && !outside) sQ[warp][(qh + qn + __popc(need & lt)) & 63] = xi;
+      qn += __popc(need);
+      __syncwarp();
+      if (qn >= 32) {
+        aqp_full(sQ[warp][(qh + lane) & 63], lo, hi, inv_h, h_phi, c_run, s_run);
+        qh = (qh + 32) & 63;
+        qn -= 32;
+        __syncwarp();
       }
     }
-#pragma unroll
-    for (int g = 0; g < kRG; ++g) {
-      double vc = warp_sum((double)sc[g] - (double)cc[g]);
-      double vs = warp_sum((double)ss[g] - (double)cs[g]);
-      if (lane == 0) {
-        sRed[warp][g][0] = vc;
-        sRed[warp][g][1] = vs;
-      }
+    if (lane < qn) aqp_full(sQ[warp][(qh + lane) & 63], lo, hi, inv_h, h_phi, c_run, s_run);
+    __syncwarp();
+    const double vc = warp_sum((double)c_run), vs = warp_sum((double)s_run);
+    if (lane == 0) {
+      sRed[warp][0] = vc;
+      sRed[warp][1] = vs;
     }
     __syncthreads();
-    if (threadIdx.x < 2 * kRG) {
-      const int g = threadIdx.x >> 1, w2 = threadIdx.x & 1;
+    if (threadIdx.x < 2) {
       double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += sRed[w][g][w2];
-      if (k0 + g < m) part[((int64_t)blockIdx.x * m + k0 + g) * 2 + w2] = t;
+      for (int w = 0; w < kWarps; ++w) t += sRed[w][threadIdx.x];
+      part[((int64_t)blockIdx.x * m + g) * 2 + threadIdx.x] = t;
     }
     __syncthreads();
   }
@@ -355,11 +405,14 @@ struct AqpLayout {
   size_t off_part, off_out, total;
 };
 
-// One CTA per sample chunk, about 4 CTAs per SM.
+// One CTA per chunk of at most kAqpChunk samples; chunks sized so that the
+// CTAs come in whole waves of 4 per SM (the shared-memory occupancy).
 AqpLayout aqp_layout(int64_t n, int m, int sms) {
   AqpLayout L;
   const int64_t ctas = (int64_t)std::max(1, sms) * 4;
-  L.chunk = std::max<int64_t>(kThreads, (n + ctas - 1) / ctas);
+  const int64_t waves = std::max<int64_t>(1, (n + ctas * kAqpChunk - 1) / (ctas * kAqpChunk));
+  L.chunk = std::min<int64_t>(kAqpChunk, ((n + waves * ctas - 1) / (waves * ctas) + 31) / 32 * 32);
+  L.chunk = std::max<int64_t>(L.chunk, kThreads);
   L.chunks = (n + L.chunk - 1) / L.chunk;
   L.off_part = ((size_t)m * 2 * sizeof(float) + 255) / 256 * 256;
   L.off_out = L.off_part + ((size_t)L.chunks * m * 2 * sizeof(double) + 255) / 256 * 256;
