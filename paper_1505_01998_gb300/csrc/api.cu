@@ -275,13 +275,24 @@ PsiCoef psi_coef(int r) {
   }
   const double kappa = 2.0 * std::log(2.0);
   const int M = r / 2;
+  // b[m]: coefficient of y^m in the monic p_r(y) = He_r(sqrt(kappa y)) / kappa^M
+  std::vector<double> b(M + 1);
+  for (int m = 0; m <= M; ++m) b[m] = h[2 * m] * std::pow(kappa, (double)(m - M));
+  // y = w - s with s = b[M-1] / M: q(w) = sum_k b[k] (w - s)^k, whose w^(M-1) term vanishes
+  const double sh = b[M - 1] / (double)M;
+  std::vector<double> dq(M + 1, 0.0);
+  for (int k = 0; k <= M; ++k) {
+    double binom = 1.0;  // C(k, m)
+    for (int m = 0; m <= k; ++m) {
+      dq[m] += b[k] * binom * std::pow(-sh, (double)(k - m));
+      binom = binom * (double)(k - m) / (double)(m + 1);
+    }
+  }
   PsiCoef cf;
   memset(&cf, 0, sizeof(cf));
-  // coefficient of y^m in p_r: a_{2m} kappa^(m - M); Horner c_i multiplies y^(M-1-i)
-  for (int i = 0; i < M; ++i) {
-    const int m = M - 1 - i;
-    cf.c[i] = (float)(h[2 * m] * std::pow(kappa, (double)(m - M)));
-  }
+  for (int i = 0; i + 2 <= M; ++i) cf.c[i] = (float)dq[M - 2 - i];  // Horner: w^(M-2), ..., w^0
+  cf.shift = (float)sh;
+  cf.post = std::exp2(sh);
   return cf;
 }
 

@@ -31,12 +31,6 @@ constexpr double kPi = 3.14159265358979323846;
 __host__ __device__ constexpr int qpl_of(int dk) { return dk <= 4 ? 8 : 4; }
 __host__ __device__ constexpr int qtile_of(int dk) { return 32 * qpl_of(dk); }
 
-// 2^-a (the negation folded into the exponential's operand).
-__device__ __forceinline__ float ex2_neg(float a) {
-  float r;
-  asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "=f"(r) : "f"(a));
-  return r;
-}
 
 // Every query tile t has a centre c_t (its first query).  Queries and samples
 // are whitened relative to the centre of the tile they meet, so the FP32

@@ -76,8 +76,14 @@ struct Phase {
 };
 
 // Horner coefficients of the psi kernel polynomial (see psi kernels).
+// The monic polynomial p_r(y) of degree M = r/2 in shifted form: with
+// w = y + shift (shift = one M-th of p's y^(M-1) coefficient, so that w^(M-1)
+// drops out), p_r(y) = q(w) = ((w w + c0) w + c1) w ... (M - 1 coefficients),
+// and p_r(y) 2^-y = post * q(w) 2^-w with post = 2^shift.
 struct PsiCoef {
-  float c[5];  // p(y) = ((y + c0) y + c1) y ... ; degree r/2, monic
+  float c[4];
+  float shift;
+  double post;
 };
 
 // Tile map of the upper pair triangle (Sec. 5.4.2, Eqs. colInTriangleMatrix,
@@ -122,6 +128,15 @@ __host__ __device__ inline int64_t tri_tiles(int64_t n, int tile) {
 __device__ __forceinline__ float ex2(float a) {
   float r;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+// 2^-a: the negation sits in the same asm block as the ex2, so that it can
+// be taken as an operand modifier of the MUFU instruction instead of costing
+// a separate FP32 instruction.
+__device__ __forceinline__ float ex2_neg(float a) {
+  float r;
+  asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "=f"(r) : "f"(a));
   return r;
 }
 

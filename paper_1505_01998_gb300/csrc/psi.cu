@@ -6,15 +6,19 @@
 // u^2 = ((x_i - x_j)/g)^2 = kappa y (kappa = 2 ln 2) and exp(-u^2/2) = 2^-y, so
 // K^(r)(u) = He_r(u) phi(u) = kappa^(r/2) p_r(y) 2^-y / sqrt(2 pi), where p_r is
 // He_r rewritten in y and made monic (host code derives its coefficients from
-// the Hermite recurrence).  The kernel sums p_r(y) 2^-y over pairs: per pair one
-// subtraction, one square, one ex2, a Horner chain in y (Sec. 7.1 uses Horner's
-// rule as well) and one fused multiply-add, packed two rows at a time in FP32x2.
+// the Hermite recurrence).  The kernel sums q(w) 2^-w over pairs, where
+// w = y + shift removes the y^(r/2 - 1) term of p_r (so p_r(y) 2^-y =
+// 2^shift q(w) 2^-w, the constant applied in FP64 by the finish): per pair one
+// subtraction, one FMA for w, one ex2, r/2 - 1 Horner FMAs in w (Sec. 7.1
+// uses Horner's rule as well) and one accumulating FMA, packed two rows at a
+// time in FP32x2 -- r/2 + 2 FP32 lane-operations per pair.
 //
 // Schedule: T x T tiles of the pair triangle in the numbering of Sec. 5.4.2;
 // items of K consecutive tiles; persistent CTAs of 8 warps; each warp covers
 // all T rows (R per lane, in registers) against a slice of T/8 columns staged
 // in shared memory.  Per-lane FP32 runs over a tile are folded into a Kahan
 // pair; item totals are reduced in FP64 and written to a per-item slot.
+#include "host.hpp"
 #include "internal.cuh"
 
 namespace gbkde {
@@ -30,9 +34,10 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
                                             const PsiCoef& cf, int64_t i0, int64_t jg0,
                                             int64_t n) {
   constexpr int M = RD / 2;
-  float2 cc[M];
+  float2 cc[M - 1];
 #pragma unroll
-  for (int m = 0; m < M; ++m) cc[m] = make_float2(cf.c[m], cf.c[m]);
+  for (int m = 0; m < M - 1; ++m) cc[m] = make_float2(cf.c[m], cf.c[m]);
+  const float2 sh2 = make_float2(cf.shift, cf.shift);
 #pragma unroll 1
   for (int jj = j_lo; jj < j_hi; jj += 4) {
     const float4 v = *reinterpret_cast<const float4*>(sF + jj);
@@ -43,17 +48,17 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
 #pragma unroll
       for (int p = 0; p < R / 2; ++p) {
         const float2 dl = __fadd2_rn(z[p], nf);
-        const float2 y = __fmul2_rn(dl, dl);
-        float2 e = make_float2(ex2(-y.x), ex2(-y.y));
+        const float2 w = __ffma2_rn(dl, dl, sh2);  // y + shift
+        float2 e = make_float2(ex2_neg(w.x), ex2_neg(w.y));
         if (EDGE) {
           const int64_t i = i0 + 64 * p, j = jg0 + jj + c;
           if (!(i < j && j < n)) e.x = 0.f;
           if (!(i + 32 < j && j < n)) e.y = 0.f;
         }
-        float2 pq = __fadd2_rn(y, cc[0]);
+        float2 q = __ffma2_rn(w, w, cc[0]);
 #pragma unroll
-        for (int m = 1; m < M; ++m) pq = __ffma2_rn(pq, y, cc[m]);
-        acc[p] = __ffma2_rn(pq, e, acc[p]);
+        for (int m = 1; m < M - 1; ++m) q = __ffma2_rn(q, w, cc[m]);
+        acc[p] = __ffma2_rn(q, e, acc[p]);
       }
     }
   }
@@ -85,6 +90,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
     int64_t l, q;
     tile_coords(t0, l, q);
     int64_t l_loaded = -1;
+    // row samples of the current tile; those of the next tile are loaded
+    // before the current one is evaluated (a tile is only ~6k clocks of work,
+    // so an exposed global-load latency per tile would cost ~10 %)
+    float zr[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) zr[k] = X[q * T + lane + 32 * k];
     for (int64_t t = t0; t < t1; ++t) {
       if (l != l_loaded) {
         __syncthreads();
@@ -94,8 +105,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
       }
       float2 z[R / 2];
 #pragma unroll
-      for (int p = 0; p < R / 2; ++p)
-        z[p] = make_float2(X[q * T + lane + 64 * p] * sc, X[q * T + lane + 64 * p + 32] * sc);
+      for (int p = 0; p < R / 2; ++p) z[p] = make_float2(zr[2 * p] * sc, zr[2 * p + 1] * sc);
+      {
+        const int64_t qn = (q + 1 > l) ? 0 : q + 1;
+        if (t + 1 < t1) {
+#pragma unroll
+          for (int k = 0; k < R; ++k) zr[k] = X[qn * T + lane + 32 * k];
+        }
+      }
       const bool edge = (q == l) || ((l + 1) * T > n);
       const int64_t i0 = q * T + lane, jg0 = l * T;
       if (edge)
@@ -145,7 +162,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
 //   stage 4: psi_4(g2) (Eq. PLUGIN-Psi4Estimate, reading R1), then h
 //            (Eq. PLUGIN-Final_h);
 //   stage 0: raw pair sum only (psi tile-sum entry point), into res.g_min.
-__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r) {
+__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r,
+                                                         double post) {
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   __shared__ double sRed[kWarps];
   if (ds->res.status != KDE_OK) return;
@@ -158,6 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
   if (threadIdx.x != 0) return;
   double P = 0.0;
   for (int w = 0; w < kWarps; ++w) P += sRed[w];
+  P *= post;  // sum of p_r(y) 2^-y from the kernel's sum of q(w) 2^-w
   const double kappa = 2.0 * 0.69314718055994530942;
   const double inv_sqrt_2pi = 0.39894228040143267794;
   // sum_{i<j} K^(r)((x_i - x_j)/g) = kappa^(r/2) P / sqrt(2 pi)
@@ -234,7 +253,7 @@ cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef&
 
 cudaError_t launch_psi_finish(DsDev* ds, int n_ds, const int* ids, int stage, int r, cudaStream_t st) {
   if (n_ds <= 0) return cudaSuccess;
-  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, ids, stage, r);
+  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, ids, stage, r, psi_coef(r).post);
   return cudaGetLastError();
 }
 
