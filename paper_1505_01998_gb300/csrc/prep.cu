@@ -69,31 +69,71 @@ __device__ void block_sum(double* v, int cnt, double (*scratch)[kNPairs], double
   __syncthreads();
 }
 
-// One CTA per dataset.  Pass 1: mean (Eq. LSCV-covariance / PLUGIN-
+// Shared memory of the prologue, declared once in the kernel for every
+// (element type, dimension) instance.
+struct PrepSmem {
+  double scratch[kPrepThreads / 32][kNPairs];
+  double sv[kNPairs];
+  double sMean[KDE_MAX_D];
+  float sM[KDE_MAX_D * KDE_MAX_D];
+  float sMeanF[KDE_MAX_D];
+  int sOk;
+  // centred samples of the pair-parallel covariance pass (D >= 8)
+  alignas(16) unsigned char stage[16384];
+};
+
+// samples per thread whose loads are issued together (wide samples already
+// issue D independent loads per sample)
+template <int D>
+constexpr int kPrepBatch = D >= 8 ? 1 : 4;
+
+// One CTA per dataset, D = the dataset's kernel dimension (d <= D; coordinates
+// d..D-1 are absent).  Pass 1: mean (Eq. LSCV-covariance / PLUGIN-
 // VarianceEstimator evaluated two-pass, reading R7).  Pass 2: covariance with
 // the n-1 denominator.  Then, on one thread in FP64: Cholesky S = L L^T,
 // log|S|, the whitening matrix M = sqrt(log2 e / 4) L^-1, sigma, A and, for
 // the PLUGIN method, psi_8^NS (Eq. PLUGIN-Psi8Estimate) and g1
 // (Eq. PLUGIN-g1).  Pass 3: y = M (x - mean) and x - mean in FP32.
-template <typename TIN>
-__device__ __forceinline__ void prep_body(DsDev* ds) {
-  __shared__ double scratch[kPrepThreads / 32][kNPairs];
-  __shared__ double sv[kNPairs];
-  __shared__ float sM[KDE_MAX_D * KDE_MAX_D];
-  __shared__ float sMeanF[KDE_MAX_D];
-  __shared__ double sMean[KDE_MAX_D];
-  __shared__ int sOk;
+// Every thread walks samples tid, tid + 512, ... in order; loads are issued
+// kPrepBatch samples at a time.  For D >= 8 the covariance is pair-parallel:
+// blocks of centred samples are staged in shared memory and thread t adds
+// pair t mod P (P = d(d+1)/2) over every G-th sample of the block.
+template <typename TIN, int D>
+__device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
+  double(*scratch)[kNPairs] = sm.scratch;
+  double* sv = sm.sv;
+  float* sM = sm.sM;
+  float* sMeanF = sm.sMeanF;
+  double* sMean = sm.sMean;
+  int& sOk = sm.sOk;
   const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
   const int64_t n = ds->n, n_pad = ds->n_pad;
   const int d = ds->d;
 
   // ---- pass 1: mean
-  Acc<TIN> a1[KDE_MAX_D];
-  for (int64_t i = threadIdx.x; i < n; i += kPrepThreads)
-    for (int k = 0; k < d; ++k) a1[k].add(x[(int64_t)k * n + i]);
-  double v[kNPairs];
-  for (int k = 0; k < d; ++k) v[k] = a1[k].get();
-  block_sum(v, d, scratch, sv);
+  {
+    Acc<TIN> a1[D];
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+      TIN v[kPrepBatch<D>][D];
+#pragma unroll
+      for (int u = 0; u < kPrepBatch<D>; ++u) {
+        const int64_t i = i0 + (int64_t)u * kPrepThreads;
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[u][k] = (i < n && k < d) ? x[(int64_t)k * n + i] : TIN(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kPrepBatch<D>; ++u)
+        if (i0 + (int64_t)u * kPrepThreads < n) {
+#pragma unroll
+          for (int k = 0; k < D; ++k)
+            if (k < d) a1[k].add(v[u][k]);
+        }
+    }
+    double v[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = a1[k].get();
+    block_sum(v, d, scratch, sv);
+  }
   if (threadIdx.x < d) {
     sMean[threadIdx.x] = sv[threadIdx.x] / (double)n;
     sMeanF[threadIdx.x] = (float)sMean[threadIdx.x];
@@ -101,22 +141,94 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
   __syncthreads();
 
   // ---- pass 2: centred cross products, upper triangle a <= b
-  Acc<TIN> a2[kNPairs];
-  for (int64_t i = threadIdx.x; i < n; i += kPrepThreads) {
-    TIN c[KDE_MAX_D];
-    for (int k = 0; k < d; ++k) {
-      if constexpr (sizeof(TIN) == 4)
-        c[k] = x[(int64_t)k * n + i] - sMeanF[k];
-      else
-        c[k] = x[(int64_t)k * n + i] - sMean[k];
-    }
-    int m = 0;
-    for (int a = 0; a < d; ++a)
-      for (int b = a; b < d; ++b) a2[m++].add(c[a] * c[b]);
-  }
   const int npairs = d * (d + 1) / 2;
-  for (int m = 0; m < npairs; ++m) v[m] = a2[m].get();
-  block_sum(v, npairs, scratch, sv);
+  if constexpr (D <= 4) {
+    constexpr int NP = D * (D + 1) / 2;
+    Acc<TIN> a2[NP];
+    for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+      TIN c[kPrepBatch<D>][D];
+#pragma unroll
+      for (int u = 0; u < kPrepBatch<D>; ++u) {
+        const int64_t i = i0 + (int64_t)u * kPrepThreads;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const TIN xv = (i < n && k < d) ? x[(int64_t)k * n + i] : TIN(0);
+          if constexpr (sizeof(TIN) == 4)
+            c[u][k] = xv - sMeanF[k < d ? k : 0];
+          else
+            c[u][k] = xv - sMean[k < d ? k : 0];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kPrepBatch<D>; ++u)
+        if (i0 + (int64_t)u * kPrepThreads < n) {
+          int m = 0;
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) {
+              if (b < d) a2[m].add(c[u][a] * c[u][b]);
+              ++m;
+            }
+        }
+    }
+    // pairs in the order (0,0), (0,1), ..., (1,1), ... of the first d coordinates
+    double v[NP];
+    {
+      int m = 0, mo = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+          if (b < d) v[mo++] = a2[m].get();
+          ++m;
+        }
+    }
+    block_sum(v, npairs, scratch, sv);
+  } else {
+    constexpr int SB = 16384 / (D * (int)sizeof(TIN));  // staged samples per block
+    TIN(*st)[D] = reinterpret_cast<TIN(*)[D]>(sm.stage);
+    const int G = kPrepThreads / npairs;  // threads per pair
+    const int t = threadIdx.x;
+    const bool active = t < G * npairs;
+    const int m = t % npairs, g = t / npairs;
+    int pa = 0, rem = m;
+    while (rem >= d - pa) {
+      rem -= d - pa;
+      ++pa;
+    }
+    const int pb = pa + rem;
+    Acc<TIN> acc;
+    for (int64_t i0 = 0; i0 < n; i0 += SB) {
+      const int cnt = (int)min((int64_t)SB, n - i0);
+      __syncthreads();  // previous block consumed
+      for (int idx = threadIdx.x; idx < cnt * D; idx += kPrepThreads) {
+        const int k = idx / cnt, i = idx - k * cnt;  // coordinate-major: coalesced reads
+        TIN c = TIN(0);
+        if (k < d) {
+          const TIN xv = x[(int64_t)k * n + i0 + i];
+          if constexpr (sizeof(TIN) == 4)
+            c = xv - sMeanF[k];
+          else
+            c = xv - sMean[k];
+        }
+        st[i][k] = c;
+      }
+      __syncthreads();
+      if (active)
+        for (int i = g; i < cnt; i += G) acc.add(st[i][pa] * st[i][pb]);
+    }
+    __syncthreads();
+    double* vals = &scratch[0][0];  // kPrepThreads values
+    vals[threadIdx.x] = active ? acc.get() : 0.0;
+    __syncthreads();
+    if (threadIdx.x < npairs) {
+      double tsum = 0.0;
+      for (int gg = 0; gg < G; ++gg) tsum += vals[gg * npairs + threadIdx.x];
+      sv[threadIdx.x] = tsum;
+    }
+    __syncthreads();
+  }
 
   // ---- scalar work, FP64, one thread
   if (threadIdx.x == 0) {
@@ -209,35 +321,62 @@ __device__ __forceinline__ void prep_body(DsDev* ds) {
   // ---- pass 3: whitened (LSCV) and centred (PLUGIN, d = 1) samples
   float* __restrict__ y = ds->y;
   float* __restrict__ xc = ds->xc;
-  for (int64_t i = threadIdx.x; i < n_pad; i += kPrepThreads) {
-    float c[KDE_MAX_D] = {};
-    if (i < n) {
-      for (int k = 0; k < d; ++k) {
-        if constexpr (sizeof(TIN) == 4)
-          c[k] = x[(int64_t)k * n + i] - sMeanF[k];
-        else
-          c[k] = (float)(x[(int64_t)k * n + i] - sMean[k]);
+  const int dk = ds->dk;
+  for (int64_t i0 = threadIdx.x; i0 < n_pad; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+    float c[kPrepBatch<D>][D];
+#pragma unroll
+    for (int u = 0; u < kPrepBatch<D>; ++u) {
+      const int64_t i = i0 + (int64_t)u * kPrepThreads;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        c[u][k] = 0.f;
+        if (i < n && k < d) {
+          if constexpr (sizeof(TIN) == 4)
+            c[u][k] = x[(int64_t)k * n + i] - sMeanF[k];
+          else
+            c[u][k] = (float)(x[(int64_t)k * n + i] - sMean[k]);
+        }
       }
     }
-    if (y) {
-      for (int k = 0; k < d; ++k) {
-        float t = 0.f;
-        for (int j = 0; j <= k; ++j) t = fmaf(sM[k * KDE_MAX_D + j], c[j], t);
-        y[(int64_t)k * n_pad + i] = t;
+#pragma unroll
+    for (int u = 0; u < kPrepBatch<D>; ++u) {
+      const int64_t i = i0 + (int64_t)u * kPrepThreads;
+      if (i >= n_pad) break;
+      if (y) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          float t = 0.f;
+#pragma unroll
+          for (int j = 0; j <= k; ++j) t = fmaf(sM[k * KDE_MAX_D + j], c[u][j], t);
+          if (k < dk) y[(int64_t)k * n_pad + i] = t;  // rows d..dk-1: zero padding (M is 0 there)
+        }
       }
-      for (int k = d; k < ds->dk; ++k) y[(int64_t)k * n_pad + i] = 0.f;  // padded coordinates
+      if (xc && d == 1) xc[i] = c[u][0];
     }
-    if (xc && d == 1) xc[i] = c[0];
   }
 }
 
 // One CTA per dataset; `ids` (optional) selects the datasets of a table.
+template <typename TIN>
+__device__ __forceinline__ void prep_dispatch(DsDev* ds, PrepSmem& sm) {
+  switch (ds->dk) {
+    case 1: prep_body<TIN, 1>(ds, sm); break;
+    case 2: prep_body<TIN, 2>(ds, sm); break;
+    case 3: prep_body<TIN, 3>(ds, sm); break;
+    case 4: prep_body<TIN, 4>(ds, sm); break;
+    case 8: prep_body<TIN, 8>(ds, sm); break;
+    case 12: prep_body<TIN, 12>(ds, sm); break;
+    default: prep_body<TIN, 16>(ds, sm); break;
+  }
+}
+
 __global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa, const int* ids) {
+  __shared__ PrepSmem sm;
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   if (ds->dtype == KDE_F64)
-    prep_body<double>(ds);
+    prep_dispatch<double>(ds, sm);
   else
-    prep_body<float>(ds);
+    prep_dispatch<float>(ds, sm);
 }
 
 constexpr int kProbeThreads = 1024;
