@@ -169,6 +169,9 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   o0 = align_up(o0 + (n_h > 0 ? (size_t)g->rows * 2 * g->n_h_pad * sizeof(double) : 0), 256);
   g->off_ppart = o0;
   o0 = align_up(o0 + (size_t)g->prows * sizeof(double), 256);
+  g->prep_parts = prep_parts_for(n);
+  g->off_prep = o0;
+  o0 = align_up(o0 + (size_t)g->prep_parts * kPrepRecord * sizeof(double), 256);
   g->total = o0;
   return KDE_OK;
 }
@@ -234,6 +237,9 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
   s.methods = methods;
   s.y = reinterpret_cast<float*>(ws + g.off_y);
   s.xc = g.d == 1 ? reinterpret_cast<float*>(ws + g.off_xc) : nullptr;
+  s.prep_parts = g.prep_parts;
+  s.prep_part = reinterpret_cast<double*>(ws + g.off_prep);
+  s.prep_count = 0;
   s.n_h = g.n_h;
   s.n_h_pad = g.n_h > 0 ? g.n_h_pad : 0;
   s.n_chunks = g.n_chunks;
@@ -409,7 +415,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, g.items, 0, 0};
   CK(launch_setup(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, st));
+  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
   Phase ph{ds, off, nullptr, 1, 0, g.items};
   const int grid = (int)std::min<int64_t>(g.items, g.ctas);
   CK(mark(0, st));
@@ -543,7 +549,7 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, g.prows};
   CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, st));
+  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, g.prows};
   const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));
   CK(mark(2, st));
@@ -631,7 +637,7 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpi
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, init.psi_rows};
   CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, st));
+  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, init.psi_rows};
   const int grid = std::max(1, (int)std::min<int64_t>(init.psi_rows, g.ctas));
   CK(launch_psi(ph, r, g.Rp, g.kahan, psi_coef(r), grid, st));

@@ -39,7 +39,8 @@ struct kde_batch_plan {
   int n_h_pad_max = 0;
   // workspace layout (bytes from the base)
   size_t off_desc = 0, off_offs = 0, off_tables = 0, staged = 0, total = 0;
-  std::vector<size_t> off_h, off_nc, off_y, off_xc, off_lpart, off_lsum, off_g, off_ppart;
+  std::vector<size_t> off_h, off_nc, off_y, off_xc, off_lpart, off_lsum, off_g, off_ppart, off_prep;
+  int prep_parts_max = 1;
   // host staging and graph
   unsigned char* pin_in = nullptr;   // image of ws[0, staged)
   unsigned char* pin_out = nullptr;  // copy of the descriptor table after a run
@@ -146,6 +147,7 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
   p->off_lsum.assign(n_req, 0);
   p->off_g.assign(n_req, 0);
   p->off_ppart.assign(n_req, 0);
+  p->off_prep.assign(n_req, 0);
   for (int r = 0; r < n_req; ++r) {
     const Geometry& g = p->geo[r];
     const int m = reqs[r].methods;
@@ -165,6 +167,12 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
       p->off_ppart[r] = o;
       o = align256(o + sizeof(double) * g.prows);
     }
+  }
+  p->prep_parts_max = 1;
+  for (int r = 0; r < n_req; ++r) {
+    p->off_prep[r] = o;
+    o = align256(o + sizeof(double) * kPrepRecord * p->geo[r].prep_parts);
+    p->prep_parts_max = std::max(p->prep_parts_max, p->geo[r].prep_parts);
   }
   p->total = o;
   // ---- host descriptor images (pointers are relative until bound to a workspace)
@@ -203,6 +211,8 @@ static int batch_bind(kde_batch_plan* p, unsigned char* ws) {
     s.lscv_sum = (m & KDE_METHOD_LSCV) ? reinterpret_cast<double*>(at(p->off_lsum[r])) : nullptr;
     s.g = (m & KDE_METHOD_LSCV) ? reinterpret_cast<double*>(at(p->off_g[r])) : nullptr;
     s.psi_part = (m & KDE_METHOD_PLUGIN) ? reinterpret_cast<double*>(at(p->off_ppart[r])) : nullptr;
+    s.prep_part = reinterpret_cast<double*>(at(p->off_prep[r]));
+    s.prep_count = 0;
     d[r] = s;
     if (m & KDE_METHOD_LSCV) {
       double* h = reinterpret_cast<double*>(img + p->off_h[r]);
@@ -239,7 +249,7 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
   const int n = p->n_req;
   const int ctas = std::max(1, p->sms) * ((p->has_opts && p->opts.ctas_per_sm) ? p->opts.ctas_per_sm : 2);
   BK(cudaMemcpyAsync(ws, p->pin_in, p->staged, cudaMemcpyHostToDevice, st));
-  BK(launch_prep(ds, n, nullptr, st));
+  BK(launch_prep(ds, n, nullptr, p->prep_parts_max, st));
   size_t k = 0;
   BK(mark_event(0, st));
   for (auto& G : p->lscv_groups) {

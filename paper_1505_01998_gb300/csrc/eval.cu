@@ -457,7 +457,7 @@ int kde_eval(const void* x_dev, int dtype, int64_t n, int d, const double* H_hos
   double* part = reinterpret_cast<double*>(w + L.off_part);
   double* f = reinterpret_cast<double*>(w + L.off_f);
   cudaError_t e = launch_setup(ds, init, &one, 1, off, offs, 4, st);
-  if (e == cudaSuccess) e = launch_prep(ds, 1, nullptr, st);
+  if (e == cudaSuccess) e = launch_prep(ds, 1, nullptr, L.g.prep_parts, st);
   if (e == cudaSuccess) {
     const int blocks = (int)std::min<int64_t>(1024, (L.m_pad + 255) / 256);
     if (dtype == KDE_F64)

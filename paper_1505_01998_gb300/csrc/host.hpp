@@ -26,8 +26,9 @@ struct Geometry {
   int Tp, Rp, Kp;
   int64_t ptiles, prows;
   // workspace offsets (bytes)
+  int prep_parts;  // CTAs of the prologue (prep_parts_for(n))
   size_t off_ds, off_off, off_h, off_nc, off_g, off_sum, off_x, off_y, off_xc, off_lpart,
-      off_ppart, total;
+      off_ppart, off_prep, total;
 };
 
 int fail(int status, const char* fmt, ...);

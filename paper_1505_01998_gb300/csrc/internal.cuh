@@ -53,6 +53,9 @@ struct DsDev {
   int64_t psi_t0;
   double* psi_part;        // [psi_rows]
   float psi_scale;         // sqrt(log2(e)/2) / g for the pilot g of the running phase
+  int32_t prep_parts;      // CTAs of the prologue: the samples are cut into this many ranges
+  double* prep_part;       // [prep_parts][kPrepRecord] per-range count, mean, centred moments
+  uint32_t prep_count;     // ranges finished (the last CTA combines them and resets it to 0)
   int32_t pad1;
   // ---- statistics (written on the device)
   double mean[KDE_MAX_D];
@@ -174,10 +177,21 @@ __device__ __forceinline__ int find_ds(const int64_t* off, int n, int64_t it) {
 }
 #endif
 
+// Prologue ranges: at most 128, about 1,024 samples each; per range one
+// record of kPrepRecord doubles: count, mean[KDE_MAX_D], the centre the
+// moments were taken about[KDE_MAX_D], centred moments[kNPairs].
+constexpr int kNPairs = KDE_MAX_D * (KDE_MAX_D + 1) / 2;  // covariance entries a <= b
+constexpr int kPrepRecord = 1 + 2 * KDE_MAX_D + kNPairs;
+inline int prep_parts_for(int64_t n) {
+  const int64_t p = (n + 1023) / 1024;
+  return (int)(p < 1 ? 1 : (p > 128 ? 128 : p));
+}
+
 // ------------------------------------------------------------- launchers
 // (defined in the .cu files; return a cudaError_t)
 // ids: optional list of dataset indices into ds (one CTA each); NULL = ds[0..n_ds)
-cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, cudaStream_t st);
+// parts_max: the largest prep_parts among the datasets launched
+cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st);
 cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
                         cudaStream_t st);
 size_t lscv_smem_bytes(int d, int B, int R, bool kahan);

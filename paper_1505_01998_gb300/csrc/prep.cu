@@ -1,5 +1,7 @@
 // Prologue kernels: descriptor setup, sample statistics, Cholesky whitening
 // and the first links of the PLUGIN chain; plus the ALU throughput probe.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace gbkde {
@@ -52,8 +54,6 @@ struct Acc<double> {
 
 // Block-wide FP64 sum of `cnt` values per thread, deterministic order;
 // results land in out[0..cnt) (shared memory) for every thread.
-constexpr int kNPairs = KDE_MAX_D * (KDE_MAX_D + 1) / 2;  // covariance entries a <= b
-
 __device__ void block_sum(double* v, int cnt, double (*scratch)[kNPairs], double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k < cnt; ++k) {
@@ -69,7 +69,7 @@ __device__ void block_sum(double* v, int cnt, double (*scratch)[kNPairs], double
   __syncthreads();
 }
 
-// Shared memory of the prologue, declared once in the kernel for every
+// Shared memory of the prologue kernels, declared once per kernel for every
 // (element type, dimension) instance.
 struct PrepSmem {
   double scratch[kPrepThreads / 32][kNPairs];
@@ -77,8 +77,8 @@ struct PrepSmem {
   double sMean[KDE_MAX_D];
   float sM[KDE_MAX_D * KDE_MAX_D];
   float sMeanF[KDE_MAX_D];
-  int sOk;
-  // centred samples of the pair-parallel covariance pass (D >= 8)
+  int last;
+  // centred samples of the pair-parallel moment pass (D >= 8)
   alignas(16) unsigned char stage[16384];
 };
 
@@ -87,43 +87,39 @@ struct PrepSmem {
 template <int D>
 constexpr int kPrepBatch = D >= 8 ? 1 : 4;
 
-// One CTA per dataset, D = the dataset's kernel dimension (d <= D; coordinates
-// d..D-1 are absent).  Pass 1: mean (Eq. LSCV-covariance / PLUGIN-
-// VarianceEstimator evaluated two-pass, reading R7).  Pass 2: covariance with
-// the n-1 denominator.  Then, on one thread in FP64: Cholesky S = L L^T,
-// log|S|, the whitening matrix M = sqrt(log2 e / 4) L^-1, sigma, A and, for
-// the PLUGIN method, psi_8^NS (Eq. PLUGIN-Psi8Estimate) and g1
-// (Eq. PLUGIN-g1).  Pass 3: y = M (x - mean) and x - mean in FP32.
-// Every thread walks samples tid, tid + 512, ... in order; loads are issued
-// kPrepBatch samples at a time.  For D >= 8 the covariance is pair-parallel:
-// blocks of centred samples are staged in shared memory and thread t adds
-// pair t mod P (P = d(d+1)/2) over every G-th sample of the block.
-template <typename TIN, int D>
-__device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
-  double(*scratch)[kNPairs] = sm.scratch;
-  double* sv = sm.sv;
-  float* sM = sm.sM;
-  float* sMeanF = sm.sMeanF;
-  double* sMean = sm.sMean;
-  int& sOk = sm.sOk;
-  const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
-  const int64_t n = ds->n, n_pad = ds->n_pad;
-  const int d = ds->d;
+// The sample range [lo, hi) of part b of a dataset cut into `parts` ranges.
+__device__ __forceinline__ void prep_range(int64_t n, int parts, int b, int64_t& lo, int64_t& hi) {
+  const int64_t blk = (n + parts - 1) / parts;
+  lo = min(n, (int64_t)b * blk);
+  hi = min(n, lo + blk);
+}
 
-  // ---- pass 1: mean
+// Mean of samples [lo, hi) into sMean / sMeanF, then the cross products of
+// the samples centred about it (in the input precision: FP32 samples take
+// the FP32-rounded mean as the centre) into sv, pairs a <= b in order.
+// Per-thread sums: FP32 Kahan (FP32 input) or FP64; across threads FP64.
+// For D >= 8 the cross products are pair-parallel: blocks of centred samples
+// are staged in shared memory and thread t adds pair t mod P (P = d(d+1)/2)
+// over every G-th sample of the block.
+template <typename TIN, int D>
+__device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int64_t lo, int64_t hi) {
+  const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
+  const int64_t n = ds->n;
+  const int d = ds->d;
+  const int64_t cnt = hi - lo;
   {
     Acc<TIN> a1[D];
-    for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+    for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
       TIN v[kPrepBatch<D>][D];
 #pragma unroll
       for (int u = 0; u < kPrepBatch<D>; ++u) {
         const int64_t i = i0 + (int64_t)u * kPrepThreads;
 #pragma unroll
-        for (int k = 0; k < D; ++k) v[u][k] = (i < n && k < d) ? x[(int64_t)k * n + i] : TIN(0);
+        for (int k = 0; k < D; ++k) v[u][k] = (i < hi && k < d) ? x[(int64_t)k * n + i] : TIN(0);
       }
 #pragma unroll
       for (int u = 0; u < kPrepBatch<D>; ++u)
-        if (i0 + (int64_t)u * kPrepThreads < n) {
+        if (i0 + (int64_t)u * kPrepThreads < hi) {
 #pragma unroll
           for (int k = 0; k < D; ++k)
             if (k < d) a1[k].add(v[u][k]);
@@ -132,36 +128,34 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
     double v[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) v[k] = a1[k].get();
-    block_sum(v, d, scratch, sv);
+    block_sum(v, d, sm.scratch, sm.sv);
   }
   if (threadIdx.x < d) {
-    sMean[threadIdx.x] = sv[threadIdx.x] / (double)n;
-    sMeanF[threadIdx.x] = (float)sMean[threadIdx.x];
+    sm.sMean[threadIdx.x] = cnt > 0 ? sm.sv[threadIdx.x] / (double)cnt : 0.0;
+    sm.sMeanF[threadIdx.x] = (float)sm.sMean[threadIdx.x];
   }
   __syncthreads();
-
-  // ---- pass 2: centred cross products, upper triangle a <= b
   const int npairs = d * (d + 1) / 2;
   if constexpr (D <= 4) {
     constexpr int NP = D * (D + 1) / 2;
     Acc<TIN> a2[NP];
-    for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+    for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
       TIN c[kPrepBatch<D>][D];
 #pragma unroll
       for (int u = 0; u < kPrepBatch<D>; ++u) {
         const int64_t i = i0 + (int64_t)u * kPrepThreads;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const TIN xv = (i < n && k < d) ? x[(int64_t)k * n + i] : TIN(0);
+          const TIN xv = (i < hi && k < d) ? x[(int64_t)k * n + i] : TIN(0);
           if constexpr (sizeof(TIN) == 4)
-            c[u][k] = xv - sMeanF[k < d ? k : 0];
+            c[u][k] = xv - sm.sMeanF[k < d ? k : 0];
           else
-            c[u][k] = xv - sMean[k < d ? k : 0];
+            c[u][k] = xv - sm.sMean[k < d ? k : 0];
         }
       }
 #pragma unroll
       for (int u = 0; u < kPrepBatch<D>; ++u)
-        if (i0 + (int64_t)u * kPrepThreads < n) {
+        if (i0 + (int64_t)u * kPrepThreads < hi) {
           int m = 0;
 #pragma unroll
           for (int a = 0; a < D; ++a)
@@ -172,7 +166,6 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
             }
         }
     }
-    // pairs in the order (0,0), (0,1), ..., (1,1), ... of the first d coordinates
     double v[NP];
     {
       int m = 0, mo = 0;
@@ -184,7 +177,7 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
           ++m;
         }
     }
-    block_sum(v, npairs, scratch, sv);
+    block_sum(v, npairs, sm.scratch, sm.sv);
   } else {
     constexpr int SB = 16384 / (D * (int)sizeof(TIN));  // staged samples per block
     TIN(*st)[D] = reinterpret_cast<TIN(*)[D]>(sm.stage);
@@ -199,130 +192,257 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
     }
     const int pb = pa + rem;
     Acc<TIN> acc;
-    for (int64_t i0 = 0; i0 < n; i0 += SB) {
-      const int cnt = (int)min((int64_t)SB, n - i0);
+    for (int64_t i0 = lo; i0 < hi; i0 += SB) {
+      const int c = (int)min((int64_t)SB, hi - i0);
       __syncthreads();  // previous block consumed
-      for (int idx = threadIdx.x; idx < cnt * D; idx += kPrepThreads) {
-        const int k = idx / cnt, i = idx - k * cnt;  // coordinate-major: coalesced reads
-        TIN c = TIN(0);
+      for (int idx = threadIdx.x; idx < c * D; idx += kPrepThreads) {
+        const int k = idx / c, i = idx - k * c;  // coordinate-major: coalesced reads
+        TIN v = TIN(0);
         if (k < d) {
           const TIN xv = x[(int64_t)k * n + i0 + i];
           if constexpr (sizeof(TIN) == 4)
-            c = xv - sMeanF[k];
+            v = xv - sm.sMeanF[k];
           else
-            c = xv - sMean[k];
+            v = xv - sm.sMean[k];
         }
-        st[i][k] = c;
+        st[i][k] = v;
       }
       __syncthreads();
       if (active)
-        for (int i = g; i < cnt; i += G) acc.add(st[i][pa] * st[i][pb]);
+        for (int i = g; i < c; i += G) acc.add(st[i][pa] * st[i][pb]);
     }
     __syncthreads();
-    double* vals = &scratch[0][0];  // kPrepThreads values
+    double* vals = &sm.scratch[0][0];  // kPrepThreads values
     vals[threadIdx.x] = active ? acc.get() : 0.0;
     __syncthreads();
     if (threadIdx.x < npairs) {
       double tsum = 0.0;
       for (int gg = 0; gg < G; ++gg) tsum += vals[gg * npairs + threadIdx.x];
-      sv[threadIdx.x] = tsum;
+      sm.sv[threadIdx.x] = tsum;
     }
     __syncthreads();
   }
+}
 
-  // ---- scalar work, FP64, one thread
+// Part b of the prologue of one dataset (grid: parts x datasets).  Each CTA
+// takes the moments of its sample range and stores them as a record; the
+// CTA that finishes last (a counter in the descriptor; no CTA waits for
+// another) combines the records in range order -- the dataset mean
+// mu = sum_b n_b m_b / n and the centred cross products
+// sum_b [M_b + n_b (u v^T + v u^T + v v^T)], u = m_b - c_b, v = c_b - mu
+// (c_b the centre M_b was taken about), which equals the two-pass
+// sum (x - mu)(x - mu)^T (Eq. LSCV-covariance / PLUGIN-VarianceEstimator
+// evaluated two-pass, reading R7) -- and then, on one thread in FP64:
+// Cholesky S = L L^T, log|S|, the whitening matrix M = sqrt(log2 e / 4) L^-1,
+// sigma, A and, for the PLUGIN method, psi_8^NS (Eq. PLUGIN-Psi8Estimate)
+// and g1 (Eq. PLUGIN-g1).
+template <typename TIN, int D>
+__device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
+  const int parts = ds->prep_parts;
+  if (b >= parts) return;
+  const int64_t n = ds->n;
+  const int d = ds->d;
+  int64_t lo, hi;
+  prep_range(n, parts, b, lo, hi);
+  prep_moments<TIN, D>(ds, sm, lo, hi);
+  const int npairs = d * (d + 1) / 2;
+  double* rec = ds->prep_part + (size_t)b * kPrepRecord;
+  if (threadIdx.x == 0) rec[0] = (double)(hi - lo);
+  if (threadIdx.x < d) {
+    rec[1 + threadIdx.x] = sm.sMean[threadIdx.x];
+    rec[1 + KDE_MAX_D + threadIdx.x] = sizeof(TIN) == 4 ? (double)sm.sMeanF[threadIdx.x] : sm.sMean[threadIdx.x];
+  }
+  if (threadIdx.x < npairs) rec[1 + 2 * KDE_MAX_D + threadIdx.x] = sm.sv[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sm.last = (atomicAdd(&ds->prep_count, 1u) == (unsigned)parts - 1u);
+  __syncthreads();
+  if (!sm.last) return;
+  __threadfence();
+  // ---- combine the records in range order (records staged in shared memory,
+  // kChunk at a time, by coalesced loads; the sums run in range order)
+  double* sMean = sm.sMean;
+  double* sv = sm.sv;
+  float* sM = sm.sM;
+  const double* recs = ds->prep_part;
+  constexpr int kChunk = (int)(sizeof(sm.stage) / (kPrepRecord * sizeof(double)));
+  double* cache = reinterpret_cast<double*>(sm.stage);
+  int pa = 0, pb = 0;
+  if (threadIdx.x < npairs) {
+    int rem = threadIdx.x;
+    while (rem >= d - pa) {
+      rem -= d - pa;
+      ++pa;
+    }
+    pb = pa + rem;
+  }
+  double tmean = 0.0;
+  for (int r0 = 0; r0 < parts; r0 += kChunk) {
+    const int nr = min(kChunk, parts - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
+      cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
+    __syncthreads();
+    if (threadIdx.x < d)
+      for (int r = 0; r < nr; ++r) tmean += cache[r * kPrepRecord] * cache[r * kPrepRecord + 1 + threadIdx.x];
+  }
+  if (threadIdx.x < d) sMean[threadIdx.x] = tmean / (double)n;
+  __syncthreads();
+  double tpair = 0.0;
+  for (int r0 = 0; r0 < parts; r0 += kChunk) {
+    const int nr = min(kChunk, parts - r0);
+    if (parts > kChunk || r0 > 0) {  // one chunk: still cached from the mean pass
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
+        cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
+      __syncthreads();
+    }
+    if (threadIdx.x < npairs)
+      for (int r = 0; r < nr; ++r) {
+        const double* q = cache + r * kPrepRecord;
+        const double nb = q[0];
+        const double ua = q[1 + pa] - q[1 + KDE_MAX_D + pa];
+        const double ub = q[1 + pb] - q[1 + KDE_MAX_D + pb];
+        const double va = q[1 + KDE_MAX_D + pa] - sMean[pa];
+        const double vb = q[1 + KDE_MAX_D + pb] - sMean[pb];
+        tpair += q[1 + 2 * KDE_MAX_D + threadIdx.x] + nb * (ua * vb + va * ub + va * vb);
+      }
+  }
+  __syncthreads();
+  if (threadIdx.x < npairs) sv[threadIdx.x] = tpair;
+  if (threadIdx.x == 0) ds->prep_count = 0u;  // ready for the next run of this descriptor
+  __syncthreads();
+  // ---- factorisation, FP64, shared by the CTA's threads (the operation order
+  // of every entry is that of the textbook serial loops)
+  double(*S)[KDE_MAX_D] = reinterpret_cast<double(*)[KDE_MAX_D]>(&sm.scratch[0][0]);
+  double(*L)[KDE_MAX_D] = S + KDE_MAX_D;
+  double(*W)[KDE_MAX_D] = S + 2 * KDE_MAX_D;
+  kde_result& res = ds->res;
+  bool fin = true;
+  for (int t = threadIdx.x; t < KDE_MAX_D * KDE_MAX_D; t += kPrepThreads) {
+    const int ra = t / KDE_MAX_D, rb = t % KDE_MAX_D;
+    double v = 0.0;
+    if (ra < d && rb < d) {
+      const int lo_ = min(ra, rb), hi_ = max(ra, rb);
+      const int m = lo_ * d - lo_ * (lo_ - 1) / 2 + (hi_ - lo_);  // pair (lo_, hi_) in a <= b order
+      // LSCV_H: whiten by the given bandwidth matrix instead of S
+      v = ds->given_H ? ds->cov[ra * d + rb] : sv[m] / (double)(n - 1);
+      fin = fin && isfinite(v);
+    }
+    S[ra][rb] = v;
+    L[ra][rb] = 0.0;
+    W[ra][rb] = 0.0;
+  }
+  if (threadIdx.x < d) fin = fin && isfinite(sMean[threadIdx.x]);
+  const bool finite = __syncthreads_and(fin) != 0;
   if (threadIdx.x == 0) {
-    kde_result& res = ds->res;
     res.status = KDE_OK;
     res.method = ds->methods;
     res.d = d;
     res.n_h = ds->n_h;
-    double S[KDE_MAX_D][KDE_MAX_D];
-    int m = 0;
-    bool finite = true;
-    for (int a = 0; a < d; ++a) {
-      ds->mean[a] = sMean[a];
-      finite = finite && isfinite(sMean[a]);
-      for (int b = a; b < d; ++b) {
-        // LSCV_H: whiten by the given bandwidth matrix instead of S
-        const double sab = ds->given_H ? ds->cov[a * d + b] : sv[m] / (double)(n - 1);
-        S[a][b] = S[b][a] = sab;
-        ++m;
-      }
-    }
-    for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) {
-        ds->cov[a * d + b] = S[a][b];
-        finite = finite && isfinite(S[a][b]);
-      }
-    double L[KDE_MAX_D][KDE_MAX_D] = {};
-    bool pd = finite;
-    for (int j = 0; j < d && pd; ++j) {
-      double s = S[j][j];
-      for (int k = 0; k < j; ++k) s -= L[j][k] * L[j][k];
+    for (int a2 = 0; a2 < d; ++a2) ds->mean[a2] = sMean[a2];
+  }
+  for (int t = threadIdx.x; t < d * d; t += kPrepThreads) ds->cov[t] = S[t / d][t % d];
+  // Cholesky S = L L^T, column by column
+  if (threadIdx.x == 0) sm.last = finite ? 1 : 0;  // reused as the "positive definite so far" flag
+  __syncthreads();
+  for (int j = 0; j < d && sm.last; ++j) {
+    if (threadIdx.x == 0) {
+      double sj = S[j][j];
+      for (int k = 0; k < j; ++k) sj -= L[j][k] * L[j][k];
       // Numerically singular for FP32 pair arithmetic: a Schur complement below
       // 1e-6 of the variance (the whitened coordinate would be rounding noise),
       // or a spread below 1e-5 of the magnitude of the values.
       const double mag = ds->given_H ? 0.0 : 1e-5 * fabs(sMean[j]);
-      if (!(s > 1e-300) || !(s > 1e-6 * S[j][j]) || !(S[j][j] > mag * mag)) {
-        pd = false;
-        break;
-      }
-      L[j][j] = sqrt(s);
-      for (int i = j + 1; i < d; ++i) {
-        double t = S[i][j];
-        for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-        L[i][j] = t / L[j][j];
+      if (!(sj > 1e-300) || !(sj > 1e-6 * S[j][j]) || !(S[j][j] > mag * mag))
+        sm.last = 0;
+      else
+        L[j][j] = sqrt(sj);
+    }
+    __syncthreads();
+    if (!sm.last) break;
+    const int i = j + 1 + (int)threadIdx.x;
+    if (i < d) {
+      double t = S[i][j];
+      for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+      L[i][j] = t / L[j][j];
+    }
+    __syncthreads();
+  }
+  const bool pd = finite && sm.last;
+  if (!finite || !pd) {
+    if (threadIdx.x == 0) res.status = finite ? KDE_EDEGENERATE : KDE_EINVAL;
+    return;
+  }
+  // W = L^-1, one column per thread (forward substitution)
+  if (threadIdx.x < d) {
+    const int j = threadIdx.x;
+    for (int i = j; i < d; ++i) {
+      if (i == j) {
+        W[i][j] = 1.0 / L[i][i];
+      } else {
+        double t = 0.0;
+        for (int k = j; k < i; ++k) t += L[i][k] * W[k][j];
+        W[i][j] = -t / L[i][i];
       }
     }
-    if (!finite) {
-      res.status = KDE_EINVAL;
-    } else if (!pd) {
-      res.status = KDE_EDEGENERATE;
-    } else {
-      double W[KDE_MAX_D][KDE_MAX_D] = {};
-      double logdet = 0.0;
-      for (int i = 0; i < d; ++i) {
-        logdet += 2.0 * log(L[i][i]);
-        W[i][i] = 1.0 / L[i][i];
-        for (int j = 0; j < i; ++j) {
-          double t = 0.0;
-          for (int k = j; k < i; ++k) t += L[i][k] * W[k][j];
-          W[i][j] = -t / L[i][i];
-        }
-      }
-      const double sl = sqrt(0.25 * kLog2e);
-      for (int i = 0; i < KDE_MAX_D; ++i)
-        for (int j = 0; j < KDE_MAX_D; ++j) {
-          const float mv = (i < d && j <= i) ? (float)(sl * W[i][j]) : 0.f;
-          ds->M[i * KDE_MAX_D + j] = mv;
-          sM[i * KDE_MAX_D + j] = mv;
-        }
-      ds->logdet = logdet;
-      res.logdet_S = logdet;
-      ds->A = pow(4.0 * kPi, -0.5 * d) * exp(-0.5 * logdet);
-      ds->sigma = sqrt(S[0][0]);
-      if (d == 1) res.sigma = ds->sigma;
-      if ((ds->methods & KDE_METHOD_PLUGIN) && d == 1) {
-        const double sg = ds->sigma;
-        const double psi8 = 105.0 / (32.0 * sqrt(kPi) * pow(sg, 9.0));
-        const double k6_0 = -15.0 / sqrt(2.0 * kPi);
-        const double g1 = pow(-2.0 * k6_0 / (psi8 * (double)n), 1.0 / 9.0);
-        res.psi8_ns = psi8;
-        res.g1 = g1;
-        ds->psi_scale = (float)(sqrt(0.5 * kLog2e) / g1);
-      }
-    }
-    sOk = (res.status == KDE_OK);
   }
   __syncthreads();
-  if (!sOk) return;
+  const double sl = sqrt(0.25 * kLog2e);
+  for (int t = threadIdx.x; t < KDE_MAX_D * KDE_MAX_D; t += kPrepThreads) {
+    const int i = t / KDE_MAX_D, j = t % KDE_MAX_D;
+    const float mv = (i < d && j <= i) ? (float)(sl * W[i][j]) : 0.f;
+    ds->M[t] = mv;
+    sM[t] = mv;
+  }
+  if (threadIdx.x == 0) {
+    double logdet = 0.0;
+    for (int i = 0; i < d; ++i) logdet += 2.0 * log(L[i][i]);
+    ds->logdet = logdet;
+    res.logdet_S = logdet;
+    ds->A = pow(4.0 * kPi, -0.5 * d) * exp(-0.5 * logdet);
+    ds->sigma = sqrt(S[0][0]);
+    if (d == 1) res.sigma = ds->sigma;
+    if ((ds->methods & KDE_METHOD_PLUGIN) && d == 1) {
+      const double sg = ds->sigma;
+      const double psi8 = 105.0 / (32.0 * sqrt(kPi) * pow(sg, 9.0));
+      const double k6_0 = -15.0 / sqrt(2.0 * kPi);
+      const double g1 = pow(-2.0 * k6_0 / (psi8 * (double)n), 1.0 / 9.0);
+      res.psi8_ns = psi8;
+      res.g1 = g1;
+      ds->psi_scale = (float)(sqrt(0.5 * kLog2e) / g1);
+    }
+  }
+}
 
-  // ---- pass 3: whitened (LSCV) and centred (PLUGIN, d = 1) samples
+// Part b of the whitening pass: y = M (x - mean) and x - mean in FP32 for
+// the samples of range b (the last range also writes the zero padding up to
+// n_pad).
+struct WhitenSmem {
+  double sMean[KDE_MAX_D];
+  float sM[KDE_MAX_D * KDE_MAX_D];
+  float sMeanF[KDE_MAX_D];
+};
+
+template <typename TIN, int D>
+__device__ __forceinline__ void prep_whiten(const DsDev* ds, WhitenSmem& sm, int b) {
+  const int parts = ds->prep_parts;
+  if (b >= parts || ds->res.status != KDE_OK) return;
+  const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
+  const int64_t n = ds->n, n_pad = ds->n_pad;
+  const int d = ds->d, dk = ds->dk;
+  for (int k = threadIdx.x; k < KDE_MAX_D * KDE_MAX_D; k += kPrepThreads) sm.sM[k] = ds->M[k];
+  if (threadIdx.x < KDE_MAX_D) {
+    sm.sMean[threadIdx.x] = threadIdx.x < d ? ds->mean[threadIdx.x] : 0.0;
+    sm.sMeanF[threadIdx.x] = (float)sm.sMean[threadIdx.x];
+  }
+  __syncthreads();
+  int64_t lo, hi;
+  prep_range(n, parts, b, lo, hi);
+  if (b == parts - 1) hi = n_pad;
   float* __restrict__ y = ds->y;
   float* __restrict__ xc = ds->xc;
-  const int dk = ds->dk;
-  for (int64_t i0 = threadIdx.x; i0 < n_pad; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
+  for (int64_t i0 = lo + threadIdx.x; i0 < hi; i0 += (int64_t)kPrepThreads * kPrepBatch<D>) {
     float c[kPrepBatch<D>][D];
 #pragma unroll
     for (int u = 0; u < kPrepBatch<D>; ++u) {
@@ -332,22 +452,25 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
         c[u][k] = 0.f;
         if (i < n && k < d) {
           if constexpr (sizeof(TIN) == 4)
-            c[u][k] = x[(int64_t)k * n + i] - sMeanF[k];
+            c[u][k] = x[(int64_t)k * n + i] - sm.sMeanF[k];
           else
-            c[u][k] = (float)(x[(int64_t)k * n + i] - sMean[k]);
+            c[u][k] = (float)(x[(int64_t)k * n + i] - sm.sMean[k]);
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < kPrepBatch<D>; ++u) {
       const int64_t i = i0 + (int64_t)u * kPrepThreads;
-      if (i >= n_pad) break;
+      if (i >= hi) break;
       if (y) {
+        // M is re-read from shared memory per sample (volatile): hoisting its
+        // D(D+1)/2 entries out of the loop would exhaust the registers at D = 16
+        const volatile float* vM = sm.sM;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
           float t = 0.f;
 #pragma unroll
-          for (int j = 0; j <= k; ++j) t = fmaf(sM[k * KDE_MAX_D + j], c[u][j], t);
+          for (int j = 0; j <= k; ++j) t = fmaf(vM[k * KDE_MAX_D + j], c[u][j], t);
           if (k < dk) y[(int64_t)k * n_pad + i] = t;  // rows d..dk-1: zero padding (M is 0 there)
         }
       }
@@ -356,27 +479,49 @@ __device__ __forceinline__ void prep_body(DsDev* ds, PrepSmem& sm) {
   }
 }
 
-// One CTA per dataset; `ids` (optional) selects the datasets of a table.
 template <typename TIN>
-__device__ __forceinline__ void prep_dispatch(DsDev* ds, PrepSmem& sm) {
+__device__ __forceinline__ void stats_dispatch(DsDev* ds, PrepSmem& sm, int b) {
   switch (ds->dk) {
-    case 1: prep_body<TIN, 1>(ds, sm); break;
-    case 2: prep_body<TIN, 2>(ds, sm); break;
-    case 3: prep_body<TIN, 3>(ds, sm); break;
-    case 4: prep_body<TIN, 4>(ds, sm); break;
-    case 8: prep_body<TIN, 8>(ds, sm); break;
-    case 12: prep_body<TIN, 12>(ds, sm); break;
-    default: prep_body<TIN, 16>(ds, sm); break;
+    case 1: prep_stats<TIN, 1>(ds, sm, b); break;
+    case 2: prep_stats<TIN, 2>(ds, sm, b); break;
+    case 3: prep_stats<TIN, 3>(ds, sm, b); break;
+    case 4: prep_stats<TIN, 4>(ds, sm, b); break;
+    case 8: prep_stats<TIN, 8>(ds, sm, b); break;
+    case 12: prep_stats<TIN, 12>(ds, sm, b); break;
+    default: prep_stats<TIN, 16>(ds, sm, b); break;
   }
 }
 
-__global__ void __launch_bounds__(kPrepThreads) k_prep(DsDev* dsa, const int* ids) {
+template <typename TIN>
+__device__ __forceinline__ void whiten_dispatch(DsDev* ds, WhitenSmem& sm, int b) {
+  switch (ds->dk) {
+    case 1: prep_whiten<TIN, 1>(ds, sm, b); break;
+    case 2: prep_whiten<TIN, 2>(ds, sm, b); break;
+    case 3: prep_whiten<TIN, 3>(ds, sm, b); break;
+    case 4: prep_whiten<TIN, 4>(ds, sm, b); break;
+    case 8: prep_whiten<TIN, 8>(ds, sm, b); break;
+    case 12: prep_whiten<TIN, 12>(ds, sm, b); break;
+    default: prep_whiten<TIN, 16>(ds, sm, b); break;
+  }
+}
+
+// grid: (parts_max, datasets); `ids` (optional) selects the datasets of a table.
+__global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const int* ids) {
   __shared__ PrepSmem sm;
-  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
+  DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
   if (ds->dtype == KDE_F64)
-    prep_dispatch<double>(ds, sm);
+    stats_dispatch<double>(ds, sm, blockIdx.x);
   else
-    prep_dispatch<float>(ds, sm);
+    stats_dispatch<float>(ds, sm, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_prep_whiten(DsDev* dsa, const int* ids) {
+  __shared__ WhitenSmem sm;
+  DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
+  if (ds->dtype == KDE_F64)
+    whiten_dispatch<double>(ds, sm, blockIdx.x);
+  else
+    whiten_dispatch<float>(ds, sm, blockIdx.x);
 }
 
 constexpr int kProbeThreads = 1024;
@@ -431,9 +576,13 @@ cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, cudaStream_t st) {
+cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st) {
   if (n_ds <= 0) return cudaSuccess;
-  k_prep<<<n_ds, kPrepThreads, 0, st>>>(ds, ids);
+  const dim3 grid((unsigned)std::max(1, parts_max), (unsigned)n_ds);
+  k_prep_stats<<<grid, kPrepThreads, 0, st>>>(ds, ids);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_prep_whiten<<<grid, kPrepThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }
 

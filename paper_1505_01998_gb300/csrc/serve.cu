@@ -277,7 +277,7 @@ bool launch_step(kde_server* s, int* err) {
   int* p6_ids = lfin_ids + S;
   int* p4_ids = p6_ids + S;
   int64_t* arrays = reinterpret_cast<int64_t*>(pin + (size_t)4 * S * sizeof(int) + 256 - ((size_t)4 * S * sizeof(int)) % 256);
-  int n_prep = 0, n_lfin = 0, n_p6 = 0, n_p4 = 0;
+  int n_prep = 0, n_lfin = 0, n_p6 = 0, n_p4 = 0, prep_parts_max = 1;
   struct G {
     int kind, d, B, R, Rp, r;
     bool kahan;
@@ -325,6 +325,7 @@ bool launch_step(kde_server* s, int* err) {
     bool referenced = false;
     if (!r->prepped) {
       prep_ids[n_prep++] = r->slot;
+      prep_parts_max = std::max(prep_parts_max, r->geo.prep_parts);
       new_descs.push_back(r);
       r->prepped = true;
       referenced = true;
@@ -421,7 +422,7 @@ bool launch_step(kde_server* s, int* err) {
   const int* d_lfin = d_prep + S;
   const int* d_p6 = d_lfin + S;
   const int* d_p4 = d_p6 + S;
-  ck(launch_prep(table, n_prep, d_prep, cs), "prep");
+  ck(launch_prep(table, n_prep, d_prep, prep_parts_max, cs), "prep");
   const int ctas = std::max(1, s->sms) * ((s->has_opts && s->opts.ctas_per_sm) ? s->opts.ctas_per_sm : 2);
   const PsiCoef c6 = psi_coef(6), c4 = psi_coef(4);
   // One persistent launch per kernel variant, forked over side streams so

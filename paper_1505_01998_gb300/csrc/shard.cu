@@ -33,7 +33,7 @@ int kde_lscv_logdet(const void* x_dev, int dtype, int64_t n, int d, void* ws, si
   const double one = 1.0;
   const int64_t offs[4] = {0, 0, 0, 0};
   cudaError_t e = launch_setup(ds, init, &one, 1, off, offs, 4, st);
-  if (e == cudaSuccess) e = launch_prep(ds, 1, nullptr, st);
+  if (e == cudaSuccess) e = launch_prep(ds, 1, nullptr, g.prep_parts, st);
   kde_result r;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&r, w + g.off_ds + offsetof(DsDev, res), sizeof(r), cudaMemcpyDeviceToHost, st);
