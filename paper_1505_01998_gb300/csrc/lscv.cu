@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
 }
 
 // Sum of the per-item partial rows, one 32-column strip per CTA: warp w adds
-// rows w, w+8, ... ; the 8 warp sums are added in order.
+// rows w, w+8, ... in that order; the 8 warp sums are added in order.  The
+// loads of 8 consecutive rows of a warp are issued before their adds (the
+// addition order is unchanged), so the loop is not bound by load latency.
 __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   __shared__ double s[kWarps][32];
@@ -224,7 +226,17 @@ __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int*
   double acc = 0.0;
   if (col < W) {
     const double* p = ds->lscv_part + col;
-    for (int64_t r = warp; r < ds->lscv_rows; r += kWarps) acc += p[r * W];
+    const int64_t rows = ds->lscv_rows;
+    constexpr int U = 8;
+    int64_t r = warp;
+    for (; r + (U - 1) * kWarps < rows; r += U * kWarps) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = p[(r + u * kWarps) * W];
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc += v[u];
+    }
+    for (; r < rows; r += kWarps) acc += p[r * W];
   }
   s[warp][lane] = acc;
   __syncthreads();
