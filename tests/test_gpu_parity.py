@@ -346,6 +346,38 @@ def test_full_size_skewed_column_sampled_tiles(kde):
     assert rel_err(p["h"], oracle.plugin_h(p["psi4"], n)) < 1e-12
 
 
+def test_full_size_skewed_column_against_full_oracle(kde):
+    """The benchmark selection (n = 65,536 skewed column, 256-point grid over
+    Z(h0), default launch geometry, Kahan FP32) against the FP64 oracle over
+    all 2.1e9 pairs, stored by tests/golden/make_golden.py --full-skewed:
+    S1, S2 and g(h) at every grid point, the argmin, and the PLUGIN chain."""
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "skewed65536_oracle.json")))
+    n = ref["n"]
+    x = datagen.skewed_column(n, seed=ref["seed"])
+    xd = dev(x)
+    x64 = host64(x)
+    h = np.asarray(ref["h"])
+    grid, _ = kde.make_grid(n_h=256)
+    res, g, hh = kde.kde_lscv(xd, grid)
+    assert np.allclose(hh, h, rtol=1e-15, atol=0)
+    s_kk, s_k, g_ref = np.asarray(ref["s_kk"]), np.asarray(ref["s_k"]), np.asarray(ref["g"])
+    err = g_err(g, g_ref, s_kk, s_k, h, n, 1, lscv_A(x64))
+    assert err.max() < TOL, (err.max(), int(err.argmax()))
+    assert argmin_ok(res["argmin"], g_ref, TOL * np.max(np.abs(g_ref)))
+    tiles = kde.kde_tile_count(n, 128)
+    s1, s2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles)
+    npairs = n * (n - 1) // 2
+    assert s_err(s1, s_kk, npairs).max() < TOL
+    assert s_err(s2, s_k, npairs).max() < TOL
+    p = kde.kde_plugin(xd)
+    rp = ref["plugin"]
+    for key in ("sigma", "g1", "psi6", "g2", "psi4"):
+        assert rel_err(p[key], rp[key]) < TOL, (key, p[key], rp[key])
+    assert rel_err(p["h"], rp["h"]) < TOL
+
+
 @pytest.mark.parametrize("d", [2, 3, 4])
 def test_full_size_correlated_mixture(kde, d):
     """n = 16,384, d = 2..4, H = h^2 S on a 128-point grid: the oracle's g at
@@ -372,3 +404,22 @@ def test_full_size_correlated_mixture(kde, d):
         r1, r2 = oracle_tile_sums_lscv(x64, h, T, tb, te, kde)
         assert s_err(s1, r1, (te - tb) * T * T).max() < TOL
         assert s_err(s2, r2, (te - tb) * T * T).max() < TOL
+
+
+@pytest.mark.parametrize("n,d,dtype", [(1025, 1, "float32"), (131073, 3, "float32"), (300001, 2, "float64"),
+                                       (70001, 16, "float32"), (5000, 12, "float64")])
+def test_prologue_statistics_across_ranges(kde, n, d, dtype):
+    """The prologue cuts the samples into up to 128 ranges and combines their
+    moments: sample covariance and log|S| against the oracle for sizes that
+    give 2 and 128 ranges with ragged ends, FP32 and FP64 input.  The mean
+    is offset far from zero so that centring errors would show."""
+    x = datagen.correlated_mixture(n, d, seed=500 + d) if d > 1 else datagen.mixture_1d(n, seed=501)
+    x = (np.asarray(x, dtype=np.float64) + 40.0).astype(dtype)
+    x64 = host64(x, dtype)
+    xd = dev(x, dtype)
+    _, S_ref = oracle.mean_cov(x64)
+    S = kde.kde_sample_covariance(xd)
+    scale = np.sqrt(np.outer(np.diag(S_ref), np.diag(S_ref)))
+    assert (np.abs(S - S_ref) / scale).max() < 1e-6
+    logdet = kde.kde_lscv_logdet(xd)
+    assert abs(logdet - np.linalg.slogdet(S_ref)[1]) < 1e-5 * max(1.0, abs(np.linalg.slogdet(S_ref)[1])) * d
