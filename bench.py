@@ -311,18 +311,23 @@ def run_serve(args):
             m = gbkde.KDE_METHOD_LSCV if r.method == "lscv" else gbkde.KDE_METHOD_PLUGIN
             tickets.append(srv.submit(r.x, m, grid))
         failures = []
+        served_res = {}
+        keys = ("sigma", "g1", "psi6", "g2", "psi4", "h", "argmin", "g_min", "logdet_S")
         for k, t in enumerate(tickets):
-            rc, _ = srv.wait(t, 600000)
+            rc, res = srv.wait(t, 600000)
             if rc != 0:
                 r = reqs[k]
                 failures.append({"index": k, "status": rc, "n": r.n, "d": r.d, "method": r.method,
-                                 "seed": r.seed})
+                                 "seed": r.seed, "served": {q: res.get(q) for q in keys}})
+            else:
+                served_res[k] = res
         st = srv.stats()
         srv.close()
         # plain path: arrivals at the same times, served one at a time
         ws = gbkde.workspace(max(gbkde.kde_workspace_size(r.n, r.d, 128) for r in reqs))
         lat = []
         plain_fail = {}
+        plain_res = {}
         t0 = time.perf_counter()
         for k, r in enumerate(reqs):
             now = time.perf_counter() - t0
@@ -331,16 +336,26 @@ def run_serve(args):
             xd = torch.from_numpy(r.x).cuda()
             try:
                 if r.method == "lscv":
-                    gbkde.kde_lscv(xd, grid, None, ws, stream)
+                    plain_res[k] = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
                 else:
-                    gbkde.kde_plugin(xd, None, ws, stream)
+                    plain_res[k] = gbkde.kde_plugin(xd, None, ws, stream)
             except gbkde.KdeError as e:
                 plain_fail[k] = e.status
             lat.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
         span = time.perf_counter() - t0
         for f in failures:  # the same request through the single-call path
             f["plain_status"] = plain_fail.get(f["index"], 0)
+            if f["index"] in plain_res:
+                f["plain"] = {q: plain_res[f["index"]].get(q) for q in keys}
+        # equal accuracy: the selected bandwidth of every request served on both paths
+        both = [k for k in served_res if k in plain_res]
+        h_rel = max((abs(served_res[k]["h"] - plain_res[k]["h"]) / abs(plain_res[k]["h"]) for k in both),
+                    default=0.0)
+        argmin_diff = sum(served_res[k]["argmin"] != plain_res[k]["argmin"] for k in both
+                          if reqs[k].method == "lscv")
         records.append({"rate": rate, "requests": count, "failures": failures,
+                        "agreement": {"requests": len(both), "max_rel_diff_h": h_rel,
+                                      "lscv_argmin_differs": int(argmin_diff)},
                         "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
                                    "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
                                    "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],

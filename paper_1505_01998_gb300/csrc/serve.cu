@@ -114,6 +114,7 @@ struct Req {
   int phase = P_QUEUED;
   int64_t cursor = 0;             // next item of the current phase
   int pending_finish = 0;         // finish kernel of the phase issued
+  uint64_t finish_step = 0;       // sequence number of the step that holds it
   int in_flight = 0;              // launched steps that reference this request
   bool cancel = false, failed = false, finished = false;
   int fail_status = 0;
@@ -131,6 +132,7 @@ struct Step {
   std::vector<uint64_t> refs;      // requests referenced
   std::vector<uint64_t> complete;  // requests whose last kernel is in this step
   int buf = 0;
+  uint64_t seq = 0;  // launch order (1, 2, ...)
   double evals = 0;
 };
 
@@ -144,9 +146,13 @@ struct kde_server {
   unsigned char* arena = nullptr;
   size_t table_off = 0, params_off[2] = {0, 0}, params_bytes = 0, heap_off = 0;
   Arena heap;
-  cudaStream_t comp = nullptr, copy = nullptr;
-  cudaStream_t side[kSideStreams] = {};
-  cudaEvent_t ev_fork = nullptr, ev_join[kSideStreams] = {};
+  // Steps alternate between two stream sets (by parameter buffer), so the
+  // pair kernels of a step start while the previous step's launches drain.
+  cudaStream_t comp[2] = {}, copy = nullptr;
+  cudaStream_t side[2][kSideStreams] = {};
+  cudaEvent_t ev_fork[2] = {}, ev_join[2][kSideStreams] = {};
+  cudaEvent_t ev_kdone[2] = {};  // a step's pair kernels (and all earlier steps') finished
+  bool have_kdone = false;
   unsigned char* pin_params[2] = {nullptr, nullptr};
   unsigned char* pin_table[2] = {nullptr, nullptr};
   std::mutex mu;
@@ -298,6 +304,7 @@ bool launch_step(kde_server* s, int* err) {
   };
   Step st;
   st.buf = buf;
+  st.seq = s->steps + 1;
   double used = 0;
   std::vector<Req*> new_descs;
   // oldest admitted first
@@ -358,6 +365,7 @@ bool launch_step(kde_server* s, int* err) {
         if (r->phase == P_PSI6) p6_ids[n_p6++] = r->slot;
         if (r->phase == P_PSI4) p4_ids[n_p4++] = r->slot;
         r->pending_finish = 1;
+        r->finish_step = st.seq;
         const bool last = (r->phase == P_PSI4) || (r->phase == P_LSCV && !(r->methods & KDE_METHOD_PLUGIN));
         if (last) st.complete.push_back(r->ticket);
       }
@@ -389,7 +397,7 @@ bool launch_step(kde_server* s, int* err) {
     *err = fail(KDE_EINTERNAL, "serve: parameter block overflow");
     return false;
   }
-  cudaStream_t cs = s->comp;
+  cudaStream_t cs = s->comp[buf];
   auto ck = [&](cudaError_t e, const char* w) {
     if (e != cudaSuccess && !*err) *err = cuda_fail(e, w);
   };
@@ -427,15 +435,21 @@ bool launch_step(kde_server* s, int* err) {
   const PsiCoef c6 = psi_coef(6), c4 = psi_coef(4);
   // One persistent launch per kernel variant, forked over side streams so
   // that the tail of one launch overlaps the work of the others; joined back
-  // before the finishing kernels.
-  ck(cudaEventRecord(s->ev_fork, cs), "fork");
+  // before the finishing kernels.  Nothing orders these launches after the
+  // previous step's: their items are other tile ranges with their own
+  // partial rows, and requests whose phase finished there have no items here.
+  // A request's later items (any step) need its prologue, which ran in the
+  // step that admitted it: every step's fork follows the previous step's fork
+  // (the previous step's uploads and prologues), not its pair kernels.
+  if (s->have_kdone) ck(cudaStreamWaitEvent(cs, s->ev_fork[buf ^ 1], 0), "previous fork wait");
+  ck(cudaEventRecord(s->ev_fork[buf], cs), "fork");
   bool forked[kSideStreams] = {};
   for (size_t i = 0; i < groups.size(); ++i) {
     const G& g = groups[i];
     if (!g.total) continue;
     const int k = (int)(i % kSideStreams);
-    cudaStream_t ss = s->side[k];
-    if (!forked[k]) ck(cudaStreamWaitEvent(ss, s->ev_fork, 0), "fork wait");
+    cudaStream_t ss = s->side[buf][k];
+    if (!forked[k]) ck(cudaStreamWaitEvent(ss, s->ev_fork[buf], 0), "fork wait");
     forked[k] = true;
     Phase ph{table, reinterpret_cast<const int64_t*>(dparams + goff[i].first),
              reinterpret_cast<const int64_t*>(dparams + goff[i].second), S, 0, g.total};
@@ -447,9 +461,15 @@ bool launch_step(kde_server* s, int* err) {
   }
   for (int k = 0; k < kSideStreams; ++k)
     if (forked[k]) {
-      ck(cudaEventRecord(s->ev_join[k], s->side[k]), "join");
-      ck(cudaStreamWaitEvent(cs, s->ev_join[k], 0), "join wait");
+      ck(cudaEventRecord(s->ev_join[buf][k], s->side[buf][k]), "join");
+      ck(cudaStreamWaitEvent(cs, s->ev_join[buf][k], 0), "join wait");
     }
+  // The finishing kernels reduce every item of a request, some launched by
+  // earlier steps: wait for the previous step's pair kernels (whose own
+  // marker covers the steps before it).
+  if (s->have_kdone) ck(cudaStreamWaitEvent(cs, s->ev_kdone[buf ^ 1], 0), "previous step wait");
+  ck(cudaEventRecord(s->ev_kdone[buf], cs), "kernels done");
+  s->have_kdone = true;
   int nh_max = 0;
   for (int k = 0; k < n_lfin; ++k) nh_max = std::max(nh_max, s->reqs[s->slot_owner[lfin_ids[k]]]->geo.n_h_pad);
   ck(launch_lscv_reduce(table, n_lfin, d_lfin, nh_max, cs), "lscv reduce");
@@ -499,7 +519,10 @@ bool reap_step(kde_server* s, bool block) {
     Req* r = s->reqs[t];
     r->in_flight--;
     if (r->failed || r->finished) continue;
-    if (r->pending_finish) {
+    // Only the step that ran the phase's finishing kernels carries its
+    // result: with two steps in flight, the earlier one is reaped after the
+    // later one (holding the finish) was built.
+    if (r->pending_finish && r->finish_step == st.seq) {
       const kde_result& res = tab[r->slot].res;
       r->pending_finish = 0;
       const bool last = (r->phase == P_PSI4) || (r->phase == P_LSCV && !(r->methods & KDE_METHOD_PLUGIN));
@@ -602,15 +625,19 @@ int kde_serve_create(const kde_serve_config* cfg, kde_server** out) {
   }
   s->heap.init(cfg->arena_bytes - o);
   s->slot_owner.assign(S, 0);
-  bool ok = cudaStreamCreateWithFlags(&s->comp, cudaStreamNonBlocking) == cudaSuccess &&
+  bool ok = cudaStreamCreateWithFlags(&s->comp[0], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&s->comp[1], cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking) == cudaSuccess;
   for (int b = 0; b < 2 && ok; ++b)
     ok = cudaMallocHost(&s->pin_params[b], s->params_bytes) == cudaSuccess &&
          cudaMallocHost(&s->pin_table[b], sizeof(DsDev) * S) == cudaSuccess;
-  ok = ok && cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess;
-  for (int k = 0; k < kSideStreams && ok; ++k)
-    ok = cudaStreamCreateWithFlags(&s->side[k], cudaStreamNonBlocking) == cudaSuccess &&
-         cudaEventCreateWithFlags(&s->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  for (int b = 0; b < 2 && ok; ++b) {
+    ok = cudaEventCreateWithFlags(&s->ev_fork[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->ev_kdone[b], cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kSideStreams && ok; ++k)
+      ok = cudaStreamCreateWithFlags(&s->side[b][k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&s->ev_join[b][k], cudaEventDisableTiming) == cudaSuccess;
+  }
   if (!ok) {
     kde_serve_destroy(s);
     return fail(KDE_ECUDA, "serve: streams or pinned staging");
@@ -797,13 +824,16 @@ int kde_serve_destroy(kde_server* s) {
     if (s->pin_params[b]) cudaFreeHost(s->pin_params[b]);
     if (s->pin_table[b]) cudaFreeHost(s->pin_table[b]);
   }
-  if (s->comp) cudaStreamDestroy(s->comp);
   if (s->copy) cudaStreamDestroy(s->copy);
-  for (int k = 0; k < kSideStreams; ++k) {
-    if (s->side[k]) cudaStreamDestroy(s->side[k]);
-    if (s->ev_join[k]) cudaEventDestroy(s->ev_join[k]);
+  for (int b = 0; b < 2; ++b) {
+    if (s->comp[b]) cudaStreamDestroy(s->comp[b]);
+    for (int k = 0; k < kSideStreams; ++k) {
+      if (s->side[b][k]) cudaStreamDestroy(s->side[b][k]);
+      if (s->ev_join[b][k]) cudaEventDestroy(s->ev_join[b][k]);
+    }
+    if (s->ev_fork[b]) cudaEventDestroy(s->ev_fork[b]);
+    if (s->ev_kdone[b]) cudaEventDestroy(s->ev_kdone[b]);
   }
-  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   delete s;
   return KDE_OK;
 }

@@ -78,6 +78,44 @@ def test_results_in_the_mix_equal_alone_bitwise_and_single_calls_within_toleranc
     alone.close()
 
 
+@pytest.mark.parametrize("quantum", [3e8, 2e9])
+def test_phases_spanning_many_steps_match_single_calls(kde, quantum):
+    """Small step budgets split every phase of every request over many steps,
+    two of them in flight: each result (including LSCV + PLUGIN requests,
+    whose PLUGIN phases follow the LSCV phase) must equal the single calls
+    within tolerance -- a phase's result is taken only from the step that ran
+    its finishing kernels."""
+    grid = kde.make_grid(n_h=64)[0]
+    rng = np.random.default_rng(7)
+    reqs = []
+    for k in range(14):
+        n = int(rng.integers(3000, 24000))
+        d = 2 if k % 5 == 4 else 1
+        methods = LSCV if d == 2 else [LSCV, PLUGIN, LSCV | PLUGIN][k % 3]
+        reqs.append((datagen.correlated_mixture(n, d, seed=900 + k), methods))
+    srv = kde.Server(arena(1 << 30), max_slots=16, quantum_evals=quantum)
+    tickets = [srv.submit(x, m, grid) for x, m in reqs]
+    outs = []
+    for t in tickets:
+        rc, r = srv.wait(t, 120000)
+        assert rc == 0, (rc, r)
+        outs.append(r)
+    st = srv.stats()
+    srv.close()
+    assert st["steps"] > 2 * len(reqs)
+    for (x, m), r in zip(reqs, outs):
+        if m & LSCV:
+            s = kde.kde_lscv(dev(x), grid)[0]
+            assert r["argmin"] == s["argmin"], (r, s)
+            assert abs(r["g_min"] - s["g_min"]) <= 1e-5 * abs(s["g_min"])
+        if m & PLUGIN:
+            s = kde.kde_plugin(dev(x))
+            for k in ("psi6", "g2", "psi4", "h_plugin"):
+                assert abs(r[k] - s[k]) <= 1e-5 * abs(s[k]), (k, r[k], s[k])
+            if not (m & LSCV):
+                assert abs(r["h"] - s["h"]) <= 1e-5 * abs(s["h"])
+
+
 def test_admission_under_a_small_budget(kde):
     grid = kde.make_grid(n_h=64)[0]
     reqs = _requests(30, seed=2, lo=2000, hi=30000)
