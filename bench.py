@@ -504,11 +504,16 @@ def run_configs(args):
     oracle.lscv_h(x, h)
     oracle.plugin(x)
     o_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.lscv_h(x, h, threads=1)
+    oracle.plugin(x, threads=1)
+    o1_s = time.perf_counter() - t0
     out.append({"config": "n=1024 FP64 mixture, 64-point LSCV on [0.01, 2] + plug-in", "evals": evals,
                 "selection_ms": sel_ms, "evals_per_s": evals / (sel_ms * 1e-3),
                 "lscv_kernel_ms": kern_ms, "lscv_kernel_evals_per_s": P * 64 / (kern_ms * 1e-3),
                 "lscv_kernel_frac": P * 64 / (kern_ms * 1e-3) / peak, "e2e_ms": e2e_ms,
-                "oracle_full_s": o_s, "oracle_evals_per_s": evals / o_s, "oracle_cores": cores})
+                "oracle_full_s": o_s, "oracle_evals_per_s": evals / o_s, "oracle_cores": cores,
+                "oracle_single_thread_s": o1_s, "oracle_single_thread_evals_per_s": evals / o1_s})
     # d = 2, 3, 4, n = 16,384
     n = 16384
     P = n * (n - 1) // 2
