@@ -10,8 +10,9 @@
 // reduced in fixed order.
 // kde_aqp: for every sample and range, the exact integral of its Gaussian
 // term over the range (normal cdf differences, tails taken from the nearer
-// side), with samples far from the range's ends classified without cdfs and
-// the rest evaluated on compacted full warps; FP64 across threads and CTAs.
+// side); each CTA sorts its chunk of the column so that only the samples near
+// a range's ends are evaluated one by one, the inside ones being counted and
+// summed through prefix sums; FP64 across threads and CTAs.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -233,14 +234,32 @@ __device__ __forceinline__ float cdf_diff(float a, float b) {
 // below the FP32 rounding of a term: that end contributes 0 or 1 to the cdf
 // difference and nothing to the pdf difference.
 constexpr float kAqpFar = 7.f;
-constexpr int kAqpChunk = 11264;  // samples per CTA, held in shared memory (44 KB)
+constexpr int kAqpChunk = 8192;  // samples per CTA, sorted in shared memory (96 KB with the prefix sums)
 
 // Count / Sum terms of one sample and range from the normal cdf and pdf.
-// With one end far (the usual case) one cdf and one pdf suffice: for a far
-// upper end P = Phi(inf) - Phi(a) = erfc(a / sqrt 2) / 2 and only phi(a)
-// remains; for a far lower end P = Phi(b) = erfc(-b / sqrt 2) / 2 and only
-// -phi(b) remains.  Both take the same instructions (t = a or -b), so the
-// warp does not diverge between them.
+// With one end far (the usual case) one tail and one pdf suffice, sharing an
+// exponential: for a far upper end P = Phi(inf) - Phi(a) = Q(a) and only
+// phi(a) remains; for a far lower end P = Phi(b) = Q(-b) and only -phi(b)
+// remains.  Both take the same instructions (t = a or -b), so the warp does
+// not diverge between them.
+// The upper tail Q(t) = erfc(t / sqrt 2) / 2 of the standard normal and the
+// exponential e = exp(-t^2 / 2) of its pdf, sharing that exponential: for
+// u = |t| / sqrt 2, erfc(u) = (a1 s + ... + a5 s^5) exp(-u^2), s = 1 / (1 + p u),
+// the rational approximation of Hastings (Abramowitz & Stegun 7.1.26,
+// absolute error of erfc below 1.5e-7; 3e-7 for Q in FP32), and
+// Q(-t) = 1 - Q(t).
+constexpr float kAsP = 0.3275911f, kAsA1 = 0.254829592f, kAsA2 = -0.284496736f, kAsA3 = 1.421413741f,
+                kAsA4 = -1.453152027f, kAsA5 = 1.061405429f;
+
+__device__ __forceinline__ float normal_upper_tail(float t, float& e) {
+  const float u = fabsf(t) * 0.70710678118654752f;
+  e = expf(-u * u);
+  const float sd = __fdividef(1.f, fmaf(kAsP, u, 1.f));
+  const float poly = sd * fmaf(sd, fmaf(sd, fmaf(sd, fmaf(sd, kAsA5, kAsA4), kAsA3), kAsA2), kAsA1);
+  const float q = 0.5f * poly * e;
+  return t >= 0.f ? q : 1.f - q;
+}
+
 __device__ __forceinline__ void aqp_full(float xi, float lo, float hi, float inv_h, float h_phi,
                                          float& cnt, float& sum) {
   const float a = (lo - xi) * inv_h, b = (hi - xi) * inv_h;
@@ -248,8 +267,8 @@ __device__ __forceinline__ void aqp_full(float xi, float lo, float hi, float inv
   float P, dphi;
   if (up_far || lo_far) {
     const float t = up_far ? a : -b;
-    P = 0.5f * erfcf(t * 0.70710678118654752f);
-    const float e = expf(-0.5f * t * t);
+    float e;
+    P = normal_upper_tail(t, e);
     dphi = up_far ? e : -e;
   } else {
     P = cdf_diff(a, b);
@@ -260,68 +279,172 @@ __device__ __forceinline__ void aqp_full(float xi, float lo, float hi, float inv
   sum += fmaf(xi, P, h_phi * dphi);
 }
 
-// One CTA per chunk of samples (staged in shared memory as FP32), ranges in
-// turn.  Per range every warp classifies its slice of the chunk: samples far
-// inside or outside the range take the closed values; the rest are queued in
-// a per-warp ring (ballot + prefix count) and evaluated 32 at a time, so the
-// cdf work runs on full warps.  Per-range FP32 runs per lane, FP64 across
-// lanes and warps; part[chunk][range][2].
+// Bitonic sort of key[0, n2) in shared memory (n2 a power of two), one
+// compare-exchange stage per barrier.
+__device__ __forceinline__ void bitonic_sort_smem(float* key, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += kThreads) {
+        const int p = i ^ j;
+        if (p > i) {
+          const float u = key[i], v = key[p];
+          if ((u > v) == ((i & k) == 0)) {
+            key[i] = v;
+            key[p] = u;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+// The same network with n2 = PER * kThreads: each thread holds PER
+// consecutive keys in registers; the stages whose partner distance j is
+// below PER stay inside a thread (no barrier), the others go through shared
+// memory.  Same compare-exchanges, same result.
+template <int PER>
+__device__ __forceinline__ void bitonic_sort_regs(float* key, int n2) {
+  const int base = (int)threadIdx.x * PER;
+  float e[PER];
+#pragma unroll
+  for (int a = 0; a < PER; ++a) e[a] = key[base + a];
+  for (int k = 2; k <= n2; k <<= 1) {
+    if ((k >> 1) >= PER) {
+#pragma unroll
+      for (int a = 0; a < PER; ++a) key[base + a] = e[a];
+      __syncthreads();
+      for (int j = k >> 1; j >= PER; j >>= 1) {
+        for (int q = threadIdx.x; q < n2 / 2; q += kThreads) {
+          const int i = (q / j) * 2 * j + (q % j), p = i + j;
+          const float u = key[i], v = key[p];
+          if ((u > v) == ((i & k) == 0)) {
+            key[i] = v;
+            key[p] = u;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int a = 0; a < PER; ++a) e[a] = key[base + a];
+    }
+#pragma unroll
+    for (int j = PER / 2; j >= 1; j >>= 1) {
+      if (j <= (k >> 1)) {
+#pragma unroll
+        for (int a = 0; a < PER; ++a) {
+          const int b = a ^ j;
+          if (b > a) {
+            const float u = e[a], v = e[b];
+            if ((u > v) == (((base + a) & k) == 0)) {
+              e[a] = v;
+              e[b] = u;
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < PER; ++a) key[base + a] = e[a];
+  __syncthreads();
+}
+
+// One CTA per chunk of samples, staged in shared memory as FP32 and sorted
+// (bitonic), with FP64 prefix sums of the sorted values.  Per range, one
+// warp finds by binary search the samples within kAqpFar bandwidths of each
+// end (t1 = lo - 7h, t2 = lo + 7h, t3 = hi - 7h, t4 = hi + 7h): those are
+// evaluated one by one; the samples between the two windows lie inside the
+// range (count: their number, sum: a difference of prefix sums), those
+// beyond them outside.  The work per range is two logarithmic searches plus
+// the samples near its ends, instead of every sample.  Per-lane FP32 runs,
+// FP64 across lanes; part[chunk][range][2].
 template <typename TIN>
 __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int64_t n, float h,
                                                   const float* __restrict__ rng /* [m][2] */, int m,
                                                   int64_t chunk, double* __restrict__ part) {
-  __shared__ float sX[kAqpChunk];
-  __shared__ float sQ[kWarps][64];
-  __shared__ double sRed[kWarps][2];
+  extern __shared__ __align__(16) unsigned char aqp_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i0 = blockIdx.x * chunk;
-  const int cnt_x = (int)min(chunk, n - i0);
-  for (int i = threadIdx.x; i < cnt_x; i += kThreads) sX[i] = (float)x[i0 + i];
+  const int cnt = (int)min(chunk, n - i0);
+  int n2 = 32;
+  while (n2 < cnt) n2 <<= 1;
+  double* pre = reinterpret_cast<double*>(aqp_smem);                          // [cnt + 1]
+  float* key = reinterpret_cast<float*>(aqp_smem + ((size_t)(cnt + 1) * 8 + 15) / 16 * 16);  // [n2]
+  __shared__ double sScan[kWarps];
+  for (int i = threadIdx.x; i < n2; i += kThreads) key[i] = i < cnt ? (float)x[i0 + i] : INFINITY;
+  __syncthreads();
+  // ---- bitonic sort, ascending
+  if (n2 == 8 * kThreads)
+    bitonic_sort_regs<8>(key, n2);
+  else if (n2 == 16 * kThreads)
+    bitonic_sort_regs<16>(key, n2);
+  else if (n2 == 32 * kThreads)
+    bitonic_sort_regs<32>(key, n2);
+  else
+    bitonic_sort_smem(key, n2);
+  // ---- FP64 prefix sums: pre[i] = key[0] + ... + key[i-1]
+  {
+    const int per = (cnt + kThreads - 1) / kThreads;
+    const int b0 = min(cnt, (int)threadIdx.x * per), b1 = min(cnt, b0 + per);
+    double run = 0.0;
+    for (int i = b0; i < b1; ++i) run += (double)key[i];
+    double incl = run;  // inclusive scan of the thread totals within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) sScan[warp] = incl;
+    __syncthreads();
+    double base = incl - run;
+    for (int w = 0; w < warp; ++w) base += sScan[w];
+    if (threadIdx.x == 0) pre[0] = 0.0;
+    for (int i = b0; i < b1; ++i) {
+      base += (double)key[i];
+      pre[i + 1] = base;
+    }
+  }
   __syncthreads();
   const float inv_h = 1.f / h, h_phi = h * 0.39894228040143268f;  // h / sqrt(2 pi)
-  const int slice = (cnt_x + kWarps - 1) / kWarps;
-  const int s0 = min(cnt_x, warp * slice), s1 = min(cnt_x, s0 + slice);
-  const unsigned lt = (1u << lane) - 1u;
-  for (int g = 0; g < m; ++g) {
+  const float fh = kAqpFar * h;
+  for (int g = warp; g < m; g += kWarps) {
     const float lo = rng[2 * g], hi = rng[2 * g + 1];
-    float c_run = 0.f, s_run = 0.f;
-    int qh = 0, qn = 0;  // ring head and fill (warp-uniform)
-    for (int i = s0; i < s1; i += 32) {
-      const bool valid = i + lane < s1;
-      const float xi = valid ? sX[i + lane] : 0.f;
-      const float a = (lo - xi) * inv_h, b = (hi - xi) * inv_h;
-      const bool inside = a <= -kAqpFar && b >= kAqpFar;
-      const bool outside = a >= kAqpFar || b <= -kAqpFar;
-      if (valid && inside) {
-        c_run += 1.f;
-        s_run += xi;
-      }
-      const unsigned need = __ballot_sync(0xffffffffu, valid && !inside && !outside);
-      if (valid && !inside && !outside) sQ[warp][(qh + qn + __popc(need & lt)) & 63] = xi;
-      qn += __popc(need);
-      __syncwarp();
-      if (qn >= 32) {
-        aqp_full(sQ[warp][(qh + lane) & 63], lo, hi, inv_h, h_phi, c_run, s_run);
-        qh = (qh + 32) & 63;
-        qn -= 32;
-        __syncwarp();
-      }
+    // lanes 0..3: first index with key >= t_(lane+1)
+    float t = lo - fh;
+    if (lane == 1) t = lo + fh;
+    if (lane == 2) t = hi - fh;
+    if (lane == 3) t = hi + fh;
+    int lb = 0, ub = cnt;
+    while (lb < ub) {
+      const int mid = (lb + ub) >> 1;
+      if (key[mid] < t) lb = mid + 1; else ub = mid;
     }
-    if (lane < qn) aqp_full(sQ[warp][(qh + lane) & 63], lo, hi, inv_h, h_phi, c_run, s_run);
-    __syncwarp();
+    const int i1 = __shfl_sync(0xffffffffu, lb, 0), i2 = __shfl_sync(0xffffffffu, lb, 1);
+    const int i3 = __shfl_sync(0xffffffffu, lb, 2), i4 = __shfl_sync(0xffffffffu, lb, 3);
+    float c_run = 0.f, s_run = 0.f;
+    double c_in = 0.0, s_in = 0.0;
+    if (lo + fh <= hi - fh) {  // two windows around the ends, the inside between them
+      for (int i = i1 + lane; i < i2; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
+      for (int i = i3 + lane; i < i4; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
+      if (lane == 0 && i3 > i2) {
+        c_in = (double)(i3 - i2);
+        s_in = pre[i3] - pre[i2];
+      }
+    } else {  // a narrow range: one window over both ends
+      for (int i = i1 + lane; i < i4; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
+    }
     const double vc = warp_sum((double)c_run), vs = warp_sum((double)s_run);
     if (lane == 0) {
-      sRed[warp][0] = vc;
-      sRed[warp][1] = vs;
+      part[((int64_t)blockIdx.x * m + g) * 2] = vc + c_in;
+      part[((int64_t)blockIdx.x * m + g) * 2 + 1] = vs + s_in;
     }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += sRed[w][threadIdx.x];
-      part[((int64_t)blockIdx.x * m + g) * 2 + threadIdx.x] = t;
-    }
-    __syncthreads();
   }
+}
+
+size_t aqp_smem_bytes(int64_t chunk) {
+  int n2 = 32;
+  while (n2 < chunk) n2 <<= 1;
+  return ((size_t)(chunk + 1) * 8 + 15) / 16 * 16 + (size_t)n2 * 4;
 }
 
 __global__ void k_aqp_finish(const double* __restrict__ part, int m, int64_t chunks, double* __restrict__ out) {
@@ -400,10 +523,10 @@ struct AqpLayout {
 };
 
 // One CTA per chunk of at most kAqpChunk samples; chunks sized so that the
-// CTAs come in whole waves of 4 per SM (the shared-memory occupancy).
+// CTAs come in whole waves of 2 per SM (the shared-memory occupancy).
 AqpLayout aqp_layout(int64_t n, int m, int sms) {
   AqpLayout L;
-  const int64_t ctas = (int64_t)std::max(1, sms) * 4;
+  const int64_t ctas = (int64_t)std::max(1, sms) * 2;
   const int64_t waves = std::max<int64_t>(1, (n + ctas * kAqpChunk - 1) / (ctas * kAqpChunk));
   L.chunk = std::min<int64_t>(kAqpChunk, ((n + waves * ctas - 1) / (waves * ctas) + 31) / 32 * 32);
   L.chunk = std::max<int64_t>(L.chunk, kThreads);
@@ -517,11 +640,19 @@ int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(rng, r2.data(), sizeof(float) * 2 * m, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = mark_event(0, st);
+  const size_t smem = aqp_smem_bytes(chunk);
+  static bool attr_set = false;
+  if (e == cudaSuccess && !attr_set) {
+    const int mx = (int)aqp_smem_bytes(kAqpChunk);
+    e = cudaFuncSetAttribute(k_aqp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_aqp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    attr_set = e == cudaSuccess;
+  }
   if (e == cudaSuccess) {
     if (dtype == KDE_F64)
-      k_aqp<double><<<(int)chunks, kThreads, 0, st>>>(static_cast<const double*>(x_dev), n, (float)h, rng, m, chunk, part);
+      k_aqp<double><<<(int)chunks, kThreads, smem, st>>>(static_cast<const double*>(x_dev), n, (float)h, rng, m, chunk, part);
     else
-      k_aqp<float><<<(int)chunks, kThreads, 0, st>>>(static_cast<const float*>(x_dev), n, (float)h, rng, m, chunk, part);
+      k_aqp<float><<<(int)chunks, kThreads, smem, st>>>(static_cast<const float*>(x_dev), n, (float)h, rng, m, chunk, part);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = mark_event(1, st);

@@ -175,3 +175,24 @@ def test_autotune_cache_text_roundtrip(kde, tmp_path):
     kde.kde_autotune_clear()
     with pytest.raises(kde.KdeError):
         kde.kde_autotune_load(tmp_path / "missing.txt")
+
+
+def test_normal_tail_approximation_of_the_range_aggregates():
+    """The upper normal tail used by kde_aqp (Hastings' rational approximation,
+    Abramowitz & Stegun 7.1.26, absolute error 7.5e-8 in exact arithmetic),
+    replayed in numpy FP32 with the constants read from the CUDA source:
+    within 4e-7 of erfc(t/sqrt 2)/2 for every t (the FP32 rounding of 1 - q
+    near 1 adds up to 6e-8)."""
+    erfc = pytest.importorskip("scipy.special").erfc
+    src = open(os.path.join(ROOT, "paper_1505_01998_gb300", "csrc", "eval.cu")).read()
+    c = {k: np.float32(v) for k, v in re.findall(r"kAs(P|A\d) = (-?[0-9.]+)f", src)}
+    assert sorted(c) == ["A1", "A2", "A3", "A4", "A5", "P"]
+    t = np.linspace(-12.0, 12.0, 400_001).astype(np.float32)
+    u = (np.abs(t) * np.float32(0.70710678118654752)).astype(np.float32)
+    e = np.exp(-(u * u)).astype(np.float32)
+    sd = (np.float32(1.0) / (c["P"] * u + np.float32(1.0))).astype(np.float32)
+    poly = sd * (c["A1"] + sd * (c["A2"] + sd * (c["A3"] + sd * (c["A4"] + sd * c["A5"]))))
+    q = (np.float32(0.5) * poly.astype(np.float32) * e).astype(np.float32)
+    Q = np.where(t >= 0, q, np.float32(1.0) - q).astype(np.float64)
+    ref = 0.5 * erfc(t.astype(np.float64) / np.sqrt(2.0))
+    assert np.abs(Q - ref).max() < 4e-7
