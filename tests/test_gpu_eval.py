@@ -205,6 +205,29 @@ def test_aqp_full_size(kde):
     aqp_ok(kde, x, 0.02 * x64.std(), lo, hi)
 
 
+@pytest.mark.parametrize("n", [2, 300, 456000, 912000])
+def test_aqp_chunk_sizes(kde, n):
+    """Sizes whose per-CTA chunks take each sort path on a 152-SM GPU: the
+    shared-memory network (2 .. 1,024 keys) and the register-stage network
+    with 8 and 16 keys per thread (2,048 and 4,096 keys per chunk)."""
+    x = datagen.mixture_1d(n, seed=40 + n % 97)
+    x64 = same(x)[0]
+    g = datagen.rng(41)
+    lo = np.quantile(x64, g.uniform(0, 1, 24)) - 0.5
+    hi = lo + g.uniform(0, 3, 24)
+    aqp_ok(kde, x, 0.15, lo, hi)
+
+
+def test_aqp_many_ranges(kde):
+    """The maximum number of ranges (1,024) over a small column."""
+    x = datagen.mixture_1d(3000, seed=44)
+    x64 = same(x)[0]
+    g = datagen.rng(45)
+    lo = g.uniform(x64.min() - 1, x64.max(), 1024)
+    hi = lo + g.uniform(0, 2, 1024)
+    aqp_ok(kde, x, 0.2, lo, hi)
+
+
 def test_aqp_errors(kde):
     x = dev(datagen.mixture_1d(100, seed=1))
     for lo, hi, h in (([1.0], [0.0], 0.1), ([np.nan], [1.0], 0.1), ([0.0], [1.0], 0.0)):
