@@ -279,6 +279,11 @@ __device__ __forceinline__ void aqp_full(float xi, float lo, float hi, float inv
   sum += fmaf(xi, P, h_phi * dphi);
 }
 
+// Sorted keys live in shared memory with one padding slot after every 32
+// (element i at i + i/32), so that the per-thread blocks of 8..32 consecutive
+// keys of the register stages are read and written without bank conflicts.
+__device__ __forceinline__ int kp(int i) { return i + (i >> 5); }
+
 // Bitonic sort of key[0, n2) in shared memory (n2 a power of two), one
 // compare-exchange stage per barrier.
 __device__ __forceinline__ void bitonic_sort_smem(float* key, int n2) {
@@ -287,10 +292,10 @@ __device__ __forceinline__ void bitonic_sort_smem(float* key, int n2) {
       for (int i = threadIdx.x; i < n2; i += kThreads) {
         const int p = i ^ j;
         if (p > i) {
-          const float u = key[i], v = key[p];
+          const float u = key[kp(i)], v = key[kp(p)];
           if ((u > v) == ((i & k) == 0)) {
-            key[i] = v;
-            key[p] = u;
+            key[kp(i)] = v;
+            key[kp(p)] = u;
           }
         }
       }
@@ -307,25 +312,25 @@ __device__ __forceinline__ void bitonic_sort_regs(float* key, int n2) {
   const int base = (int)threadIdx.x * PER;
   float e[PER];
 #pragma unroll
-  for (int a = 0; a < PER; ++a) e[a] = key[base + a];
+  for (int a = 0; a < PER; ++a) e[a] = key[kp(base + a)];
   for (int k = 2; k <= n2; k <<= 1) {
     if ((k >> 1) >= PER) {
 #pragma unroll
-      for (int a = 0; a < PER; ++a) key[base + a] = e[a];
+      for (int a = 0; a < PER; ++a) key[kp(base + a)] = e[a];
       __syncthreads();
       for (int j = k >> 1; j >= PER; j >>= 1) {
         for (int q = threadIdx.x; q < n2 / 2; q += kThreads) {
           const int i = (q / j) * 2 * j + (q % j), p = i + j;
-          const float u = key[i], v = key[p];
+          const float u = key[kp(i)], v = key[kp(p)];
           if ((u > v) == ((i & k) == 0)) {
-            key[i] = v;
-            key[p] = u;
+            key[kp(i)] = v;
+            key[kp(p)] = u;
           }
         }
         __syncthreads();
       }
 #pragma unroll
-      for (int a = 0; a < PER; ++a) e[a] = key[base + a];
+      for (int a = 0; a < PER; ++a) e[a] = key[kp(base + a)];
     }
 #pragma unroll
     for (int j = PER / 2; j >= 1; j >>= 1) {
@@ -345,7 +350,7 @@ __device__ __forceinline__ void bitonic_sort_regs(float* key, int n2) {
     }
   }
 #pragma unroll
-  for (int a = 0; a < PER; ++a) key[base + a] = e[a];
+  for (int a = 0; a < PER; ++a) key[kp(base + a)] = e[a];
   __syncthreads();
 }
 
@@ -369,9 +374,9 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
   int n2 = 32;
   while (n2 < cnt) n2 <<= 1;
   double* pre = reinterpret_cast<double*>(aqp_smem);                          // [cnt + 1]
-  float* key = reinterpret_cast<float*>(aqp_smem + ((size_t)(cnt + 1) * 8 + 15) / 16 * 16);  // [n2]
+  float* key = reinterpret_cast<float*>(aqp_smem + ((size_t)(cnt + 1) * 8 + 15) / 16 * 16);  // [n2 + n2/32], padded
   __shared__ double sScan[kWarps];
-  for (int i = threadIdx.x; i < n2; i += kThreads) key[i] = i < cnt ? (float)x[i0 + i] : INFINITY;
+  for (int i = threadIdx.x; i < n2; i += kThreads) key[kp(i)] = i < cnt ? (float)x[i0 + i] : INFINITY;
   __syncthreads();
   // ---- bitonic sort, ascending
   if (n2 == 8 * kThreads)
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
     const int per = (cnt + kThreads - 1) / kThreads;
     const int b0 = min(cnt, (int)threadIdx.x * per), b1 = min(cnt, b0 + per);
     double run = 0.0;
-    for (int i = b0; i < b1; ++i) run += (double)key[i];
+    for (int i = b0; i < b1; ++i) run += (double)key[kp(i)];
     double incl = run;  // inclusive scan of the thread totals within the warp
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
     for (int w = 0; w < warp; ++w) base += sScan[w];
     if (threadIdx.x == 0) pre[0] = 0.0;
     for (int i = b0; i < b1; ++i) {
-      base += (double)key[i];
+      base += (double)key[kp(i)];
       pre[i + 1] = base;
     }
   }
@@ -417,21 +422,21 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
     int lb = 0, ub = cnt;
     while (lb < ub) {
       const int mid = (lb + ub) >> 1;
-      if (key[mid] < t) lb = mid + 1; else ub = mid;
+      if (key[kp(mid)] < t) lb = mid + 1; else ub = mid;
     }
     const int i1 = __shfl_sync(0xffffffffu, lb, 0), i2 = __shfl_sync(0xffffffffu, lb, 1);
     const int i3 = __shfl_sync(0xffffffffu, lb, 2), i4 = __shfl_sync(0xffffffffu, lb, 3);
     float c_run = 0.f, s_run = 0.f;
     double c_in = 0.0, s_in = 0.0;
     if (lo + fh <= hi - fh) {  // two windows around the ends, the inside between them
-      for (int i = i1 + lane; i < i2; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
-      for (int i = i3 + lane; i < i4; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
+      for (int i = i1 + lane; i < i2; i += 32) aqp_full(key[kp(i)], lo, hi, inv_h, h_phi, c_run, s_run);
+      for (int i = i3 + lane; i < i4; i += 32) aqp_full(key[kp(i)], lo, hi, inv_h, h_phi, c_run, s_run);
       if (lane == 0 && i3 > i2) {
         c_in = (double)(i3 - i2);
         s_in = pre[i3] - pre[i2];
       }
     } else {  // a narrow range: one window over both ends
-      for (int i = i1 + lane; i < i4; i += 32) aqp_full(key[i], lo, hi, inv_h, h_phi, c_run, s_run);
+      for (int i = i1 + lane; i < i4; i += 32) aqp_full(key[kp(i)], lo, hi, inv_h, h_phi, c_run, s_run);
     }
     const double vc = warp_sum((double)c_run), vs = warp_sum((double)s_run);
     if (lane == 0) {
@@ -444,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
 size_t aqp_smem_bytes(int64_t chunk) {
   int n2 = 32;
   while (n2 < chunk) n2 <<= 1;
-  return ((size_t)(chunk + 1) * 8 + 15) / 16 * 16 + (size_t)n2 * 4;
+  return ((size_t)(chunk + 1) * 8 + 15) / 16 * 16 + (size_t)(n2 + n2 / 32) * 4;
 }
 
 __global__ void k_aqp_finish(const double* __restrict__ part, int m, int64_t chunks, double* __restrict__ out) {
