@@ -63,7 +63,9 @@ def set_n(n):
     EVALS_LSCV = pairs(N) * N_H
     EVALS_PSI = 2 * pairs(N)
     EVALS_STEP = EVALS_LSCV + EVALS_PSI
-LAUNCHES_PER_STEP = 5 + 6  # LSCV: setup, prep, pairs, reduce, finish; PLUGIN: setup, prep, 2 x (pairs, finish)
+# LSCV: setup, prologue statistics, whitening, pairs, reduce, finish;
+# PLUGIN: setup, prologue statistics, whitening, 2 x (pairs, finish)
+LAUNCHES_PER_STEP = 6 + 7
 
 
 def profiled_lscv_traffic():
