@@ -797,7 +797,7 @@ def run_gpu(args, world, rank, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": LAUNCHES_PER_STEP * K,
+            "gpu_launches": LAUNCHES_PER_STEP * K * world,  # all ranks
             "roofline": roofline, "clocks": clocks,
             "alu_probe": probe,
             "result": {"lscv_argmin": r_l["argmin"], "lscv_h": r_l["h"], "plugin_h": r_p["h"]}}
