@@ -55,6 +55,30 @@ EVALS_PSI = 2 * pairs(N)
 EVALS_STEP = EVALS_LSCV + EVALS_PSI
 
 
+def lscv_per_clk(probe, d, octave):
+    """ALU bound of the LSCV pair kernel in evaluations per clock and SM.
+    Direct grids: one ex2 and 3 FP32 lane-operations per evaluation (the
+    squared distance, 2d lanes per pair, is shared by 16 bandwidths and left
+    out).  Octave grids: 1/4 ex2, 2.25 packed multiply/add lanes (2 scalings,
+    7 squarings and 9 running sums per 16 evaluations, per residue pair) and
+    2d/16 FMA lanes for the squared distance per evaluation."""
+    if not octave:
+        return min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
+    fp32 = 1.0 / (2.25 / probe["fmul2_fadd2_lanes_per_clk_sm"] + (2.0 * d / 16.0) / probe["ffma_lanes_per_clk_sm"])
+    return min(probe["mufu_ex2_per_clk_sm"] / 0.25, fp32)
+
+
+def lscv_basis(probe, d, octave, mhz):
+    if not octave:
+        return (f"min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM, FP32 lanes "
+                f"{probe['ffma_lanes_per_clk_sm']:.1f}/clk/SM / 3 per eval) x {probe['sm_count']} SMs x "
+                f"{mhz:.0f} MHz")
+    return (f"octave grid: min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM / 0.25 per eval, "
+            f"1 / (2.25 / {probe['fmul2_fadd2_lanes_per_clk_sm']:.1f} packed mul/add lanes + "
+            f"{2 * d}/16 / {probe['ffma_lanes_per_clk_sm']:.1f} FFMA lanes) per eval) x "
+            f"{probe['sm_count']} SMs x {mhz:.0f} MHz")
+
+
 def set_n(n):
     global N, EVALS_LSCV, EVALS_PSI, EVALS_STEP, WORKLOAD
     if n != N:
@@ -459,8 +483,7 @@ def run_configs(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     probe = gbkde.kde_probe_alu()
-    per_clk = min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
-    peak = per_clk * probe["sm_count"] * 2070.0 * 1e6
+    peak = lscv_per_clk(probe, 1, False) * probe["sm_count"] * 2070.0 * 1e6  # explicit log grid
     cores = oracle.openmp_threads() or 1
     K = max(3, args.steps)
     sampler = ClockSampler(0)
@@ -522,7 +545,8 @@ def run_configs(args):
     for d in (2, 3, 4):
         x = datagen.correlated_mixture(n, d, seed=3 + d)
         xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
-        grid, _keep = gbkde.make_grid(n_h=128)
+        grid, _keep = gbkde.make_grid(n_h=128)  # default grid: 16 points per octave of 1/h^2
+        peak_d = lscv_per_clk(probe, d, True) * probe["sm_count"] * 2070.0 * 1e6
         ws = gbkde.workspace(gbkde.kde_workspace_size(n, d, 128))
         sel_ms, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True)
         xh = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).pin_memory().numpy()
@@ -537,7 +561,8 @@ def run_configs(args):
         out.append({"config": f"d={d} n=16384 correlated mixture, 128-point LSCV over Z(h0)",
                     "evals": P * 128, "selection_ms": sel_ms, "evals_per_s": P * 128 / (sel_ms * 1e-3),
                     "lscv_kernel_ms": kern_ms, "lscv_kernel_evals_per_s": P * 128 / (kern_ms * 1e-3),
-                    "lscv_kernel_frac": P * 128 / (kern_ms * 1e-3) / peak, "e2e_ms": e2e_ms,
+                    "lscv_kernel_frac": P * 128 / (kern_ms * 1e-3) / peak_d,
+                    "lscv_roofline_evals_per_s": peak_d, "e2e_ms": e2e_ms,
                     "oracle_evals_per_s": o_pairs * 128 / o_s, "oracle_cores": cores,
                     "oracle_sample": f"rows 0..{rows - 1} of the pair triangle ({o_pairs} pairs, {o_s:.1f} s)"})
     clocks = sampler.stop()
@@ -769,7 +794,7 @@ def run_gpu(args, world, rank, local):
 
     # ---- roofline of the dominant kernel (all-pairs LSCV)
     sm_mhz = (clocks or {}).get("sm_mhz") or probe["sm_mhz"]
-    per_clk = min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
+    per_clk = lscv_per_clk(probe, 1, True)  # the default 256-point grid: 32 points per octave
     peak = per_clk * probe["sm_count"] * sm_mhz * 1e6 / 1e9
     achieved = EVALS_LSCV / (lscv_ms * 1e-3) / 1e9
     peak_max = per_clk * probe["sm_count"] * 2070.0 * 1e6 / 1e9
@@ -777,10 +802,8 @@ def run_gpu(args, world, rank, local):
                 "frac": achieved / peak, "traffic": profiled_lscv_traffic(),
                 "kernel": "k_lscv (all-pairs, all-bandwidths LSCV)",
                 "kernel_ms": lscv_ms, "evals_per_launch": EVALS_LSCV,
-                "peak_basis": (f"min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM, FP32 lanes "
-                               f"{probe['ffma_lanes_per_clk_sm']:.1f}/clk/SM / 3 per eval) x "
-                               f"{probe['sm_count']} SMs x {sm_mhz:.0f} MHz (median SM clock sampled "
-                               "during the timed region); unit counts measured by kde_probe_alu"),
+                "peak_basis": (lscv_basis(probe, 1, True, sm_mhz) + " (median SM clock sampled during "
+                               "the timed region); unit counts measured by kde_probe_alu"),
                 "peak_at_max_clock": peak_max, "frac_at_max_clock": achieved / peak_max,
                 "psi_kernel_ms": psi_ms,
                 "psi_geval_s": pairs(N) / (psi_ms * 1e-3) / 1e9}

@@ -67,7 +67,7 @@ extern "C" {
 #define KDE_FP32_PLAIN 1
 
 /* bandwidth grid kinds */
-#define KDE_GRID_DEFAULT_Z 0 /* n_h log-spaced points over Z(h0) = [h0/4, 4 h0] */
+#define KDE_GRID_DEFAULT_Z 0 /* h_k = (h0/4) 16^(k/n_h), k < n_h: log-spaced over Z(h0) = [h0/4, 4 h0) */
 #define KDE_GRID_EXPLICIT 1  /* the n_h values in h[] (need not be sorted)       */
 #define KDE_GRID_LOG 2       /* n_h log-spaced points over [h_min, h_max]        */
 
@@ -528,12 +528,14 @@ int kde_set_kernel_events(void* lscv_begin, void* lscv_end, void* psi_begin, voi
 
 /* Sustained per-SM throughput of the units the pair kernels are bound by,
  * measured with clock64() on the current device: MUFU ex2 results, FP32 FMA
- * lanes (scalar FFMA) and packed FP32x2 FMA lanes, each per SM per clock.
- * Also returns the SM count and the effective SM clock (MHz) seen by the
- * probe.  Device-synchronous; allocates nothing (uses the workspace). */
+ * lanes (scalar FFMA), packed FP32x2 FMA lanes, and packed FP32x2
+ * multiply-then-add lanes (the squaring and accumulation of the octave-grid
+ * kernel), each per SM per clock.  Also returns the SM count and the
+ * effective SM clock (MHz) seen by the probe.  Device-synchronous; allocates
+ * nothing (uses the workspace). */
 int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu_ex2_per_clk_sm,
                   double* ffma_lanes_per_clk_sm, double* ffma2_lanes_per_clk_sm,
-                  int* sm_count, double* sm_mhz);
+                  double* fmul2_fadd2_lanes_per_clk_sm, int* sm_count, double* sm_mhz);
 
 #ifdef __cplusplus
 }

@@ -76,6 +76,7 @@ def _load():
             "kdeo_plugin": (I, [P, L, I, P]),
             "kdeo_h0": (D, [L, I]),
             "kdeo_grid_log": (None, [D, D, I, P]),
+            "kdeo_grid_default": (None, [L, I, I, P]),
             "kdeo_lscv_sums_block": (I, [P, L, I, P, I, L, L, L, L, P, P, P, I]),
             "kdeo_lscv_h": (I, [P, L, I, P, I, P, P, P, P, I]),
             "kdeo_lscv_H": (I, [P, L, I, P, P, I]),
@@ -202,9 +203,11 @@ def grid_log(hmin: float, hmax: float, n_h: int) -> np.ndarray:
 
 
 def grid_default(n: int, d: int, n_h: int) -> np.ndarray:
-    """Log-spaced grid over Z(h0) = [h0/4, 4 h0] (Eq. LSCV-Zh0)."""
-    z = h0(n, d)
-    return grid_log(z / 4.0, 4.0 * z, n_h)
+    """Log-spaced grid over Z(h0) = [h0/4, 4 h0) (Eq. LSCV-Zh0):
+    h_k = (h0/4) 16^(k/n_h), k = 0 .. n_h-1."""
+    out = np.zeros(n_h)
+    _load().kdeo_grid_default(int(n), int(d), int(n_h), _p(out))
+    return out
 
 
 def lscv_sums(x, h, block=None, threads: int = 0):

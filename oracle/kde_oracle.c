@@ -289,6 +289,15 @@ double kdeo_h0(long n, int d) {
   return pow(4.0 / ((double)(d + 2) * (double)n), 1.0 / (double)(d + 4));
 }
 
+/* The default grid over Z(h0) = [h0/4, 4 h0) (Eq. LSCV-Zh0): n_h log-spaced
+ * points h_k = (h0/4) 16^(k/n_h), k = 0 .. n_h-1 (reading R6: Sec. 7.1 gives
+ * the number of points, not their spacing).  With n_h a multiple of 8 there
+ * are n_h/8 points per octave of 1/h^2. */
+void kdeo_grid_default(long n, int d, int n_h, double *h) {
+  const double z = kdeo_h0(n, d);
+  for (int k = 0; k < n_h; ++k) h[k] = 0.25 * z * pow(16.0, (double)k / (double)n_h);
+}
+
 /* n_h log-spaced points from hmin to hmax inclusive (the search range of
  * Eq. LSCV-Zh0 sampled at a fixed number of points, Sec. 7.1). */
 void kdeo_grid_log(double hmin, double hmax, int n_h, double *h) {

@@ -111,6 +111,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->cv_loo = (o && o->cv == KDE_CV_LOO) ? 1 : 0;
   const int cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : 2;
   g->ctas = std::max(1, sms) * cps;
+  g->oct_P = 0;
   // LSCV
   g->T = (o && o->tile) ? o->tile : (n <= 2048 ? 32 : 128);
   if (g->dk > 4) g->T = 32;  // one row per lane keeps the d > 4 coordinates in registers
@@ -199,16 +200,16 @@ int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h) {
       for (int k = 0; k < grid->n_h; ++k) (*h)[k] = grid->h[k];
       break;
     case KDE_GRID_DEFAULT_Z: {
-      // h0 = (4 / ((d+2) n))^(1/(d+4)) (Eq. LSCV-h0, normal scale), Z = [h0/4, 4 h0]
+      // h0 = (4 / ((d+2) n))^(1/(d+4)) (Eq. LSCV-h0, normal scale); n_h points
+      // h_k = (h0/4) 16^(k/n_h) over Z = [h0/4, 4 h0): log-spaced, and with n_h
+      // a multiple of 8, n_h/8 points per octave of 1/h^2
       const double h0 = std::pow(4.0 / ((double)(d + 2) * (double)n), 1.0 / (double)(d + 4));
-      lo = h0 / 4.0;
-      hi = h0 * 4.0;
-    }  // fall through
+      for (int k = 0; k < grid->n_h; ++k) (*h)[k] = 0.25 * h0 * std::pow(16.0, (double)k / (double)grid->n_h);
+      break;
+    }
     case KDE_GRID_LOG:
-      if (grid->kind == KDE_GRID_LOG) {
-        lo = grid->h_min;
-        hi = grid->h_max;
-      }
+      lo = grid->h_min;
+      hi = grid->h_max;
       if (!(lo > 0) || !(hi >= lo) || !std::isfinite(hi))
         return fail(KDE_EINVAL, "grid range [%g, %g] invalid", lo, hi);
       for (int k = 0; k < grid->n_h; ++k)
@@ -221,6 +222,19 @@ int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h) {
   for (double v : *h)
     if (!(v > 0) || !std::isfinite(v)) return fail(KDE_EINVAL, "grid value %g invalid", v);
   return KDE_OK;
+}
+
+void apply_octave(Geometry* g, const std::vector<double>& h) {
+  g->oct_P = 0;
+  const int nh = (int)h.size();
+  if (g->B != 16 || nh < 16 || nh % 16 != 0 || g->n_h_pad != nh) return;
+  const int P = nh / 8;
+  for (int k = P; k < nh; ++k) {
+    // c_(k-P) = 2 c_k with c = 1/h^2, i.e. h_k^2 = 2 h_(k-P)^2
+    const double r = (h[k] * h[k]) / (h[k - P] * h[k - P]);
+    if (!(std::fabs(r - 2.0) <= 1e-12)) return;
+  }
+  g->oct_P = P;
 }
 
 // Descriptor for one selection on workspace `ws` laid out by `g`.
@@ -238,6 +252,7 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
   s.y = reinterpret_cast<float*>(ws + g.off_y);
   s.xc = g.d == 1 ? reinterpret_cast<float*>(ws + g.off_xc) : nullptr;
   s.prep_parts = g.prep_parts;
+  s.oct_P = g.oct_P;
   s.prep_part = reinterpret_cast<double*>(ws + g.off_prep);
   s.prep_count = 0;
   s.n_h = g.n_h;
@@ -400,6 +415,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   if (rc) return rc;
   Geometry g;
   { const int grc = make_geometry(n, d, (int)h.size(), opts, device_sms(), &g); if (grc) return grc; }
+  apply_octave(&g, h);
   if (ws_bytes < g.total)
     return fail(KDE_ENOMEM, "workspace %zu bytes < %zu needed", ws_bytes, g.total);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -419,7 +435,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   Phase ph{ds, off, nullptr, 1, 0, g.items};
   const int grid = (int)std::min<int64_t>(g.items, g.ctas);
   CK(mark(0, st));
-  CK(launch_lscv(ph, g.dk, g.B, g.R, g.kahan, std::max(grid, 1), st));
+  CK(launch_lscv(ph, g.dk, g.B, g.R, g.kahan, g.oct_P > 0, std::max(grid, 1), st));
   CK(mark(1, st));
   CK(launch_lscv_reduce(ds, 1, nullptr, g.n_h_pad, st));
   CK(launch_lscv_finish(ds, 1, nullptr, st));
@@ -653,21 +669,21 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpi
 // ------------------------------------------------------------- probe
 
 int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu, double* ffma,
-                  double* ffma2, int* sm_count, double* sm_mhz) {
+                  double* ffma2, double* fmul2_fadd2, int* sm_count, double* sm_mhz) {
   const int sms = device_sms();
   if (sms <= 0) return fail(KDE_ECUDA, "no CUDA device");
   const int grid = sms;  // one 1024-thread CTA per SM (the probe's shared memory forces it)
   if (!ws || ws_bytes < sizeof(double) * 2 * grid) return fail(KDE_ENOMEM, "probe needs %zu bytes", sizeof(double) * 2 * grid);
   cudaStream_t st = (cudaStream_t)stream;
   double* dout = static_cast<double*>(ws);
-  const int iters[3] = {1000, 4000, 4000};
-  const double lanes_per_op[3] = {1.0, 1.0, 2.0};
-  double rate[3] = {0, 0, 0}, mhz = 0;
+  const int iters[4] = {1000, 4000, 4000, 4000};
+  const double lanes_per_op[4] = {1.0, 1.0, 2.0, 2.0};  // modes 2, 3: packed FP32x2 instructions
+  double rate[4] = {0, 0, 0, 0}, mhz = 0;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   std::vector<double> cyc(grid);
-  for (int mode = 0; mode < 3; ++mode) {
+  for (int mode = 0; mode < 4; ++mode) {
     CK(launch_probe_mode(mode, dout, iters[mode] / 4, grid, st));  // warm-up
     CK(cudaEventRecord(e0, st));
     CK(launch_probe_mode(mode, dout, iters[mode], grid, st));
@@ -688,6 +704,7 @@ int kde_probe_alu(void* ws, size_t ws_bytes, void* stream, double* mufu, double*
   if (mufu) *mufu = rate[0];
   if (ffma) *ffma = rate[1];
   if (ffma2) *ffma2 = rate[2];
+  if (fmul2_fadd2) *fmul2_fadd2 = rate[3];
   if (sm_count) *sm_count = sms;
   if (sm_mhz) *sm_mhz = mhz;
   return KDE_OK;

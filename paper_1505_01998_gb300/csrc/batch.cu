@@ -32,6 +32,7 @@ struct kde_batch_plan {
   struct Group {
     int d, B, R, Rp;
     bool kahan;
+    bool oct;  // octave-grid LSCV variant
     int64_t total;
     std::vector<int64_t> off;  // [n_req + 1]
   };
@@ -69,7 +70,7 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
   p->grids.resize(n_req);
   p->lscv_group.assign(n_req, -1);
   p->psi_group.assign(n_req, -1);
-  std::map<std::tuple<int, int, int, bool>, int> lkey;
+  std::map<std::tuple<int, int, int, bool, bool>, int> lkey;
   std::map<std::tuple<int, bool>, int> pkey;
   for (int r = 0; r < n_req; ++r) {
     const kde_request& q = reqs[r];
@@ -91,11 +92,12 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
     rc = make_geometry(q.n, q.d, n_h, opts, p->sms, &g);
     if (rc) return rc;
     if (q.methods & KDE_METHOD_LSCV) {
-      auto k = std::make_tuple(g.dk, g.B, g.R, g.kahan);
+      apply_octave(&g, p->grids[r]);
+      auto k = std::make_tuple(g.dk, g.B, g.R, g.kahan, g.oct_P > 0);
       auto it = lkey.find(k);
       if (it == lkey.end()) {
         it = lkey.emplace(k, (int)p->lscv_groups.size()).first;
-        p->lscv_groups.push_back({g.dk, g.B, g.R, 0, g.kahan, 0, {}});
+        p->lscv_groups.push_back({g.dk, g.B, g.R, 0, g.kahan, g.oct_P > 0, 0, {}});
       }
       p->lscv_group[r] = it->second;
       p->n_h_pad_max = std::max(p->n_h_pad_max, g.n_h_pad);
@@ -105,7 +107,7 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
       auto it = pkey.find(k);
       if (it == pkey.end()) {
         it = pkey.emplace(k, (int)p->psi_groups.size()).first;
-        p->psi_groups.push_back({1, 0, 0, g.Rp, g.kahan, 0, {}});
+        p->psi_groups.push_back({1, 0, 0, g.Rp, g.kahan, false, 0, {}});
       }
       p->psi_group[r] = it->second;
     }
@@ -254,7 +256,7 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
   BK(mark_event(0, st));
   for (auto& G : p->lscv_groups) {
     Phase ph{ds, offs + k * (n + 1), nullptr, n, 0, G.total};
-    BK(launch_lscv(ph, G.d, G.B, G.R, G.kahan, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, ctas)), st));
+    BK(launch_lscv(ph, G.d, G.B, G.R, G.kahan, G.oct, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, ctas)), st));
     ++k;
   }
   BK(mark_event(1, st));
@@ -285,7 +287,7 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
 
 int batch_prepare_kernels(kde_batch_plan* p) {
   for (auto& G : p->lscv_groups) {
-    cudaError_t e = prepare_lscv(G.d, G.B, G.R, G.kahan);
+    cudaError_t e = prepare_lscv(G.d, G.B, G.R, G.kahan, G.oct);
     if (e != cudaSuccess) return cuda_fail(e, "prepare_lscv");
   }
   return KDE_OK;

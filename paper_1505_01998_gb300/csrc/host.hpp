@@ -27,6 +27,7 @@ struct Geometry {
   int64_t ptiles, prows;
   // workspace offsets (bytes)
   int prep_parts;  // CTAs of the prologue (prep_parts_for(n))
+  int oct_P;       // > 0: octave grid with this many points per octave (apply_octave)
   size_t off_ds, off_off, off_h, off_nc, off_g, off_sum, off_x, off_y, off_xc, off_lpart,
       off_ppart, off_prep, total;
 };
@@ -43,6 +44,10 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
                   double max_item_evals = 0);
 int build_grid(const kde_grid* grid, int64_t n, int d, std::vector<double>* h);
 DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsigned char* ws);
+// Marks g for the octave-grid kernel when the grid h (ascending) has n_h a
+// multiple of 16 (n_h / 8 points per octave of 1/h^2, to 1e-12) and g already
+// takes 16 bandwidths per thread; the workspace layout does not change.
+void apply_octave(Geometry* g, const std::vector<double>& h);
 PsiCoef psi_coef(int r);
 
 // Records the caller's timing event k (kde_set_kernel_events) on `st`, if set.

@@ -56,7 +56,7 @@ struct DsDev {
   int32_t prep_parts;      // CTAs of the prologue: the samples are cut into this many ranges
   double* prep_part;       // [prep_parts][kPrepRecord] per-range count, mean, centred moments
   uint32_t prep_count;     // ranges finished (the last CTA combines them and resets it to 0)
-  int32_t pad1;
+  int32_t oct_P;           // > 0: the grid is P points per octave of 1/h^2 (octave kernel)
   // ---- statistics (written on the device)
   double mean[KDE_MAX_D];
   double cov[KDE_MAX_D * KDE_MAX_D];
@@ -192,11 +192,12 @@ inline int prep_parts_for(int64_t n) {
 // ids: optional list of dataset indices into ds (one CTA each); NULL = ds[0..n_ds)
 // parts_max: the largest prep_parts among the datasets launched
 cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st);
-cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
+// oct: the octave-grid variant (B = 16; every dataset of the phase has oct_P > 0)
+cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, bool oct, int grid,
                         cudaStream_t st);
-size_t lscv_smem_bytes(int d, int B, int R, bool kahan);
+size_t lscv_smem_bytes(int d, int B, int R, bool kahan, bool oct);
 // sets the kernel's shared-memory attribute without launching (call before a graph capture)
-cudaError_t prepare_lscv(int d, int B, int R, bool kahan);
+cudaError_t prepare_lscv(int d, int B, int R, bool kahan, bool oct);
 cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, cudaStream_t st);
 cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, const int* ids, cudaStream_t st);
 cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef& cf, int grid,

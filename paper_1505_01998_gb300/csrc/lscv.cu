@@ -38,8 +38,8 @@ struct DPad {
 // Measured at n = 16,384 with 128 bandwidths: d = 4 +2 %; d = 3 no change and
 // d = 2 -2.4 % (its scalar path walks two columns per 16-byte load), so only
 // d = 4 takes it.
-template <int D, int R>
-constexpr bool kPackedQ = (R == 4 && D == 4);
+template <int D, int R, bool OCT = false>
+constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT);
 
 // Columns [j_lo, j_hi) of one tile for this lane's R rows and B bandwidths.
 // Bandwidths are processed in pairs with packed FP32x2 arithmetic.
@@ -141,11 +141,73 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
   }
 }
 
-template <int D, int B, int R, bool KAHAN>
+// Octave grids (the bandwidths come in octaves of 1/h^2: with P points per
+// octave, c_(k-P) = 2 c_k for c = 1/h^2, so e_(k-P) = e_k^2 for every pair).
+// A thread owns two residues r, r+1 (mod P) and their 8 octaves: per pair and
+// residue two exponentials (octaves 7 and 3) by MUFU ex2, the other six
+// octaves by squaring down (at most three squarings from an exponential),
+// plus one more square below octave 0.  Since S2(k) = sum e_k^2 = S1(k-P),
+// the nine running sums (octaves 0..7 and "octave -1") give S1 and S2 of all
+// 16 bandwidths: per evaluation 1/4 ex2 and about 2 FP32 lane-operations.
+template <int D, int R, bool EDGE>
+__device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, int j_lo, int j_hi,
+                                                 const float (&y)[R][D], const float2 (&nca)[2],
+                                                 float2 (&acc)[9], int64_t i0, int64_t jg0, int64_t n) {
+  constexpr int DP = DPad<D>::value;
+  constexpr int CPI = DP <= 4 ? 4 / DP : 1;  // columns per iteration
+  constexpr int NV = CPI * DP / 4;           // 16-byte shared-memory loads per iteration
+#pragma unroll 1
+  for (int jj = j_lo; jj < j_hi; jj += CPI) {
+    float vv[4 * NV];
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(sF + jj * DP + 4 * u);
+      vv[4 * u] = v.x;
+      vv[4 * u + 1] = v.y;
+      vv[4 * u + 2] = v.z;
+      vv[4 * u + 3] = v.w;
+    }
+#pragma unroll
+    for (int c = 0; c < CPI; ++c) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        float qv = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float dl = y[r][k] - vv[c * DP + k];
+          qv = fmaf(dl, dl, qv);
+        }
+        if (EDGE) {
+          const int64_t i = i0 + 32 * r, j = jg0 + jj + c;
+          if (!(i < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
+        }
+        const float2 q2 = make_float2(qv, qv);
+        const float2 a7 = __fmul2_rn(q2, nca[0]), a3 = __fmul2_rn(q2, nca[1]);
+        const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
+        const float2 e3 = make_float2(ex2(a3.x), ex2(a3.y));
+        const float2 e6 = __fmul2_rn(e7, e7), e2 = __fmul2_rn(e3, e3);
+        const float2 e5 = __fmul2_rn(e6, e6), e1 = __fmul2_rn(e2, e2);
+        const float2 e4 = __fmul2_rn(e5, e5), e0 = __fmul2_rn(e1, e1);
+        const float2 em = __fmul2_rn(e0, e0);
+        acc[7] = __fadd2_rn(acc[7], e7);
+        acc[6] = __fadd2_rn(acc[6], e6);
+        acc[5] = __fadd2_rn(acc[5], e5);
+        acc[4] = __fadd2_rn(acc[4], e4);
+        acc[3] = __fadd2_rn(acc[3], e3);
+        acc[2] = __fadd2_rn(acc[2], e2);
+        acc[1] = __fadd2_rn(acc[1], e1);
+        acc[0] = __fadd2_rn(acc[0], e0);
+        acc[8] = __fadd2_rn(acc[8], em);
+      }
+    }
+  }
+}
+
+template <int D, int B, int R, bool KAHAN, bool OCT>
 __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
   constexpr int T = 32 * R;
   constexpr int DP = DPad<D>::value;
-  constexpr int FB = T * DP * (kPackedQ<D, R> ? 8 : 4);  // column tile bytes
+  constexpr int FB = T * DP * (kPackedQ<D, R, OCT> ? 8 : 4);  // column tile bytes
   extern __shared__ __align__(16) unsigned char smem[];
   float* sF = reinterpret_cast<float*>(smem);                                 // [T][DP] (pairs if packed)
   double* sRed = reinterpret_cast<double*>(smem + FB);                        // [8][B][2]
@@ -172,11 +234,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     const int hbase = (hg * kWarps + my_chunk) * B;
 
     float2 nc2[B / 2], t1[B / 2], t2[B / 2];
+    // octave grids: residues rb, rb + 1 of P; anchors at octaves 7 and 3; 9 running sums
+    const int P = OCT ? ds->oct_P : 0;
+    const int rb = 2 * (hg * kWarps + my_chunk);
+    float2 nca[2], oacc[9];
+    if constexpr (OCT) {
+      nca[0] = make_float2(ds->nc[rb + 7 * P], ds->nc[rb + 1 + 7 * P]);
+      nca[1] = make_float2(ds->nc[rb + 3 * P], ds->nc[rb + 1 + 3 * P]);
 #pragma unroll
-    for (int bp = 0; bp < B / 2; ++bp) {
-      nc2[bp] = make_float2(ds->nc[hbase + 2 * bp], ds->nc[hbase + 2 * bp + 1]);
-      t1[bp] = make_float2(0.f, 0.f);
-      t2[bp] = make_float2(0.f, 0.f);
+      for (int j = 0; j < 9; ++j) oacc[j] = make_float2(0.f, 0.f);
+    } else {
+#pragma unroll
+      for (int bp = 0; bp < B / 2; ++bp) {
+        nc2[bp] = make_float2(ds->nc[hbase + 2 * bp], ds->nc[hbase + 2 * bp + 1]);
+        t1[bp] = make_float2(0.f, 0.f);
+        t2[bp] = make_float2(0.f, 0.f);
+      }
     }
     if (KAHAN) {
 #pragma unroll
@@ -195,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
         for (int idx = threadIdx.x; idx < T * DP; idx += kThreads) {
           const int jj = idx / DP, k = idx - jj * DP;
           const float v = (k < D) ? Y[(int64_t)k * n_pad + l * T + jj] : 0.f;
-          if constexpr (kPackedQ<D, R>)
+          if constexpr (kPackedQ<D, R, OCT>)
             reinterpret_cast<float2*>(sF)[idx] = make_float2(-v, -v);
           else
             sF[idx] = v;
@@ -210,11 +283,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
         for (int k = 0; k < D; ++k) y[r][k] = Y[(int64_t)k * n_pad + q * T + lane + 32 * r];
       const bool edge = (q == l) || ((l + 1) * T > n);
       const int64_t i0 = q * T + lane, jg0 = l * T;
-      if (edge)
-        lscv_columns<D, B, R, true>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
-      else
-        lscv_columns<D, B, R, false>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
-      if (KAHAN && ++run >= flush_every) {
+      if constexpr (OCT) {
+        if (edge)
+          lscv_columns_oct<D, R, true>(sF, j_lo, j_hi, y, nca, oacc, i0, jg0, n);
+        else
+          lscv_columns_oct<D, R, false>(sF, j_lo, j_hi, y, nca, oacc, i0, jg0, n);
+      } else {
+        if (edge)
+          lscv_columns<D, B, R, true>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
+        else
+          lscv_columns<D, B, R, false>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
+      }
+      if (KAHAN && OCT && ++run >= flush_every) {
+        // slot j: (s, c) of residue rb and of rb + 1 for running sum j
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          float4 k0 = sK[(warp * B + j) * 32 + lane];
+          kahan_add(k0.x, k0.y, oacc[j].x);
+          kahan_add(k0.z, k0.w, oacc[j].y);
+          sK[(warp * B + j) * 32 + lane] = k0;
+          oacc[j] = make_float2(0.f, 0.f);
+        }
+        run = 0;
+      }
+      if (KAHAN && !OCT && ++run >= flush_every) {
 #pragma unroll
         for (int bp = 0; bp < B / 2; ++bp) {
           float4 k0 = sK[(warp * B + 2 * bp) * 32 + lane];
@@ -237,8 +329,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     }
     // ---- item total: lanes (FP64 butterfly), then column slices in fixed order
     __syncthreads();
+    if constexpr (OCT) {
+      // running sums j = 0..8 per residue; local bandwidth b = residue + 2 * octave
+      double vs[9][2];
 #pragma unroll
-    for (int bp = 0; bp < B / 2; ++bp) {
+      for (int j = 0; j < 9; ++j) {
+        double v0, v1;
+        if (KAHAN) {
+          float4 k = sK[(warp * B + j) * 32 + lane];
+          kahan_add(k.x, k.y, oacc[j].x);  // unflushed tail of the run
+          kahan_add(k.z, k.w, oacc[j].y);
+          v0 = (double)k.x - (double)k.y;
+          v1 = (double)k.z - (double)k.w;
+        } else {
+          v0 = oacc[j].x;
+          v1 = oacc[j].y;
+        }
+        if (!active) v0 = v1 = 0.0;
+        vs[j][0] = warp_sum(v0);
+        vs[j][1] = warp_sum(v1);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int oc = 0; oc < 8; ++oc)
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr) {
+            const int b = rr + 2 * oc;
+            sRed[(warp * B + b) * 2] = vs[oc][rr];                        // S1 at octave oc
+            sRed[(warp * B + b) * 2 + 1] = vs[oc == 0 ? 8 : oc - 1][rr];  // S2 = S1 an octave below
+          }
+      }
+    }
+#pragma unroll
+    for (int bp = 0; bp < B / 2 && !OCT; ++bp) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int b = 2 * bp + half;
@@ -265,12 +388,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
       }
     }
     __syncthreads();
-    double* out = ds->lscv_part + row * (2 * (int64_t)ds->n_h_pad) + (int64_t)hg * kWarps * B * 2;
+    double* out = ds->lscv_part + row * (2 * (int64_t)ds->n_h_pad) + (OCT ? 0 : (int64_t)hg * kWarps * B * 2);
     for (int o = threadIdx.x; o < cg * B * 2; o += kThreads) {
       const int c = o / (2 * B), rem = o - c * 2 * B;
       double s = 0.0;
       for (int sl = 0; sl < S; ++sl) s += sRed[(sl * cg + c) * B * 2 + rem];
-      out[o] = s;
+      if constexpr (OCT) {
+        // local bandwidth b = residue + 2 * octave of chunk c -> grid index
+        const int b = rem >> 1;
+        const int k = 2 * (hg * kWarps + c) + (b & 1) + P * (b >> 1);
+        out[2 * k + (rem & 1)] = s;
+      } else {
+        out[o] = s;
+      }
     }
   }
 }
@@ -345,71 +475,76 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
   }
 }
 
-template <int D, int B, int R, bool KAHAN>
+template <int D, int B, int R, bool KAHAN, bool OCT>
 cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
-  const size_t smem = lscv_smem_bytes(D, B, R, KAHAN);
+  const size_t smem = lscv_smem_bytes(D, B, R, KAHAN, OCT);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN>,
+    cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN, OCT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
-  k_lscv<D, B, R, KAHAN><<<grid, kThreads, smem, st>>>(ph);
+  k_lscv<D, B, R, KAHAN, OCT><<<grid, kThreads, smem, st>>>(ph);
   return cudaGetLastError();
 }
 
 template <int D, int B, int R>
-cudaError_t launch_k(const Phase& ph, bool kahan, int grid, cudaStream_t st) {
-  return kahan ? launch_t<D, B, R, true>(ph, grid, st) : launch_t<D, B, R, false>(ph, grid, st);
+cudaError_t launch_k(const Phase& ph, bool kahan, bool oct, int grid, cudaStream_t st) {
+  if constexpr (B == 16) {
+    if (oct) return kahan ? launch_t<D, B, R, true, true>(ph, grid, st) : launch_t<D, B, R, false, true>(ph, grid, st);
+  } else {
+    if (oct) return cudaErrorInvalidValue;  // octave grids take 16 bandwidths per thread
+  }
+  return kahan ? launch_t<D, B, R, true, false>(ph, grid, st) : launch_t<D, B, R, false, false>(ph, grid, st);
 }
 
 template <int D, int B>
-cudaError_t launch_r(const Phase& ph, int R, bool kahan, int grid, cudaStream_t st) {
+cudaError_t launch_r(const Phase& ph, int R, bool kahan, bool oct, int grid, cudaStream_t st) {
   switch (R) {
-    case 1: return launch_k<D, B, 1>(ph, kahan, grid, st);
+    case 1: return launch_k<D, B, 1>(ph, kahan, oct, grid, st);
     case 4:
-      if constexpr (D <= 4) return launch_k<D, B, 4>(ph, kahan, grid, st);
+      if constexpr (D <= 4) return launch_k<D, B, 4>(ph, kahan, oct, grid, st);
       return cudaErrorInvalidValue;  // d > 4 walks one row per lane
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int D>
-cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, int grid, cudaStream_t st) {
+cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, bool oct, int grid, cudaStream_t st) {
   switch (B) {
-    case 8: return launch_r<D, 8>(ph, R, kahan, grid, st);
-    case 16: return launch_r<D, 16>(ph, R, kahan, grid, st);
+    case 8: return launch_r<D, 8>(ph, R, kahan, oct, grid, st);
+    case 16: return launch_r<D, 16>(ph, R, kahan, oct, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 }  // namespace
 
-size_t lscv_smem_bytes(int d, int B, int R, bool kahan) {
+size_t lscv_smem_bytes(int d, int B, int R, bool kahan, bool oct) {
   const int dp = (d == 3) ? 4 : d;
-  const bool packed = (R == 4 && d == 4);  // kPackedQ: the column tile holds pairs
+  const bool packed = (R == 4 && d == 4 && !oct);  // kPackedQ: the column tile holds pairs
   return (size_t)32 * R * dp * (packed ? 8 : 4) + (size_t)kWarps * B * 16 +
          (kahan ? (size_t)kWarps * B * 32 * 16 : 0);
 }
 
-cudaError_t prepare_lscv(int d, int B, int R, bool kahan) {
+cudaError_t prepare_lscv(int d, int B, int R, bool kahan, bool oct) {
   Phase ph{nullptr, nullptr, nullptr, 0, 0, 0};
-  return launch_lscv(ph, d, B, R, kahan, 0, nullptr);
+  return launch_lscv(ph, d, B, R, kahan, oct, 0, nullptr);
 }
 
-cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, int grid,
+cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, bool oct, int grid,
                         cudaStream_t st) {
   if (ph.total <= 0 && grid > 0) return cudaSuccess;
   switch (d) {
-    case 1: return launch_b<1>(ph, B, R, kahan, grid, st);
-    case 2: return launch_b<2>(ph, B, R, kahan, grid, st);
-    case 3: return launch_b<3>(ph, B, R, kahan, grid, st);
-    case 4: return launch_b<4>(ph, B, R, kahan, grid, st);
-    case 8: return launch_b<8>(ph, B, R, kahan, grid, st);
-    case 12: return launch_b<12>(ph, B, R, kahan, grid, st);
-    case 16: return launch_b<16>(ph, B, R, kahan, grid, st);
+    case 1: return launch_b<1>(ph, B, R, kahan, oct, grid, st);
+    case 2: return launch_b<2>(ph, B, R, kahan, oct, grid, st);
+    case 3: return launch_b<3>(ph, B, R, kahan, oct, grid, st);
+    case 4: return launch_b<4>(ph, B, R, kahan, oct, grid, st);
+    case 8: return launch_b<8>(ph, B, R, kahan, oct, grid, st);
+    case 12: return launch_b<12>(ph, B, R, kahan, oct, grid, st);
+    case 16: return launch_b<16>(ph, B, R, kahan, oct, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

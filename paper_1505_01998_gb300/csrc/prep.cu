@@ -528,7 +528,8 @@ constexpr int kProbeThreads = 1024;
 constexpr int kProbeSmem = 160 * 1024;  // > half an SM's shared memory: one CTA per SM
 
 // ALU probe: `iters` rounds of 8 independent dependency chains per thread.
-// mode 0: MUFU ex2; mode 1: scalar FFMA; mode 2: packed FP32x2 FMA.
+// mode 0: MUFU ex2; mode 1: scalar FFMA; mode 2: packed FP32x2 FMA; mode 3:
+// packed FP32x2 multiplies and adds (independent chains, half each).
 // Each CTA records its clock64() span; out[blockIdx.x] = cycles.
 template <int MODE>
 __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters, float seed) {
@@ -550,6 +551,13 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
         if (MODE == 0) a[k] = ex2(-a[k]);
         if (MODE == 1) a[k] = fmaf(a[k], 0.9999f, 1e-6f);
         if (MODE == 2) p[k] = __ffma2_rn(p[k], m2, c2);
+        // two independent chains (a product and a sum): nothing to contract into an FMA
+        if (MODE == 3) {
+          if (k & 1)
+            p[k] = __fadd2_rn(p[k], c2);
+          else
+            p[k] = __fmul2_rn(p[k], m2);
+        }
       }
     }
   }
@@ -593,12 +601,14 @@ cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaSt
     if ((e = cudaFuncSetAttribute(k_probe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_probe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_probe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_probe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
     attr = true;
   }
   switch (mode) {
     case 0: k_probe<0><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
     case 1: k_probe<1><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
-    default: k_probe<2><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
+    case 2: k_probe<2><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
+    default: k_probe<3><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
   }
   return cudaGetLastError();
 }

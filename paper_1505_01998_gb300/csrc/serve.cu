@@ -286,7 +286,7 @@ bool launch_step(kde_server* s, int* err) {
   int n_prep = 0, n_lfin = 0, n_p6 = 0, n_p4 = 0, prep_parts_max = 1;
   struct G {
     int kind, d, B, R, Rp, r;
-    bool kahan;
+    bool kahan, oct;
     std::vector<int64_t> take, base;
     int64_t total = 0;
   };
@@ -296,10 +296,11 @@ bool launch_step(kde_server* s, int* err) {
     const int rr = kind == P_LSCV ? 0 : (kind == P_PSI6 ? 6 : 4);
     for (auto& x : groups)
       if (x.kind == kind && x.kahan == g.kahan &&
-          (kind == P_LSCV ? (x.d == g.dk && x.B == g.B && x.R == g.R) : (x.Rp == g.Rp && x.r == rr)))
+          (kind == P_LSCV ? (x.d == g.dk && x.B == g.B && x.R == g.R && x.oct == (g.oct_P > 0))
+                          : (x.Rp == g.Rp && x.r == rr)))
         return x;
-    groups.push_back({kind, g.dk, g.B, g.R, g.Rp, rr, g.kahan, std::vector<int64_t>(S, 0),
-                      std::vector<int64_t>(S, 0), 0});
+    groups.push_back({kind, g.dk, g.B, g.R, g.Rp, rr, g.kahan, kind == P_LSCV && g.oct_P > 0,
+                      std::vector<int64_t>(S, 0), std::vector<int64_t>(S, 0), 0});
     return groups.back();
   };
   Step st;
@@ -455,7 +456,7 @@ bool launch_step(kde_server* s, int* err) {
              reinterpret_cast<const int64_t*>(dparams + goff[i].second), S, 0, g.total};
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total, ctas));
     if (g.kind == P_LSCV)
-      ck(launch_lscv(ph, g.d, g.B, g.R, g.kahan, grid, ss), "lscv");
+      ck(launch_lscv(ph, g.d, g.B, g.R, g.kahan, g.oct, grid, ss), "lscv");
     else
       ck(launch_psi(ph, g.r, g.Rp, g.kahan, g.r == 6 ? c6 : c4, grid, ss), "psi");
   }
@@ -647,7 +648,10 @@ int kde_serve_create(const kde_serve_config* cfg, kde_server** out) {
     for (int B : {8, 16})
       for (int R : {1, 4})
         for (int k = 0; k < 2; ++k)
-          if (d <= 4 || R == 1) prepare_lscv(d, B, R, k == 0);
+          if (d <= 4 || R == 1) {
+            prepare_lscv(d, B, R, k == 0, false);
+            if (B == 16) prepare_lscv(d, B, R, k == 0, true);
+          }
   s->worker = std::thread(worker_main, s);
   *out = s;
   return KDE_OK;
@@ -684,6 +688,7 @@ int kde_serve_submit(kde_server* s, const kde_request* q, uint64_t* ticket) {
     delete r;
     return rc;
   }
+  if (n_h) apply_octave(&r->geo, r->grid);
   r->region_bytes = r->geo.total;
   if (n_h) {
     r->nc.assign(r->geo.n_h_pad, -1.0f);

@@ -92,7 +92,7 @@ SIGNATURES = {
     "kde_set_kernel_events": (_I, [_P, _P, _P, _P]),
     "kde_psi_tile_sums": (_I, [_P, _I, _L, _I, _D, _L, _L, ctypes.POINTER(kde_opts), _P, _S, _P, _DP]),
     "kde_psi_tile_edge": (_I, [_L, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int)]),
-    "kde_probe_alu": (_I, [_P, _S, _P, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), _DP]),
+    "kde_probe_alu": (_I, [_P, _S, _P, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), _DP]),
     "kde_lscv_H_workspace_size": (_I, [_L, _I, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(_S)]),
     "kde_lscv_H": (_I, [_P, _I, _L, _I, _DP, _I, ctypes.POINTER(kde_opts), _P, _S, _P, _DP]),
     "kde_batch_plan_create": (_I, [ctypes.POINTER(kde_request), _I, ctypes.POINTER(kde_opts),
@@ -547,12 +547,13 @@ def kde_probe_alu(ws=None, stream=None) -> dict:
     if ws is None:
         ws = workspace(1 << 20)
     wp, wn = _ws(ws)
-    m, f, f2, mhz = (np.zeros(1) for _ in range(4))
+    m, f, f2, ma, mhz = (np.zeros(1) for _ in range(5))
     sms = ctypes.c_int(0)
-    _check(lib().kde_probe_alu(wp, wn, _stream_handle(stream), _dp(m), _dp(f), _dp(f2),
+    _check(lib().kde_probe_alu(wp, wn, _stream_handle(stream), _dp(m), _dp(f), _dp(f2), _dp(ma),
                                ctypes.byref(sms), _dp(mhz)))
     return {"mufu_ex2_per_clk_sm": float(m[0]), "ffma_lanes_per_clk_sm": float(f[0]),
-            "ffma2_lanes_per_clk_sm": float(f2[0]), "sm_count": sms.value, "sm_mhz": float(mhz[0])}
+            "ffma2_lanes_per_clk_sm": float(f2[0]), "fmul2_fadd2_lanes_per_clk_sm": float(ma[0]),
+            "sm_count": sms.value, "sm_mhz": float(mhz[0])}
 
 
 def read_ws_result(ws, n_h: int = 0):

@@ -423,3 +423,31 @@ def test_prologue_statistics_across_ranges(kde, n, d, dtype):
     assert (np.abs(S - S_ref) / scale).max() < 1e-6
     logdet = kde.kde_lscv_logdet(xd)
     assert abs(logdet - np.linalg.slogdet(S_ref)[1]) < 1e-5 * max(1.0, abs(np.linalg.slogdet(S_ref)[1])) * d
+
+
+@pytest.mark.parametrize("d,n,n_h", [(1, 3001, 128), (2, 2050, 256), (5, 1500, 96), (1, 700, 16 * 8)])
+def test_octave_kernel_against_direct_kernel_and_oracle(kde, d, n, n_h):
+    """On an octave grid (the default grid: n_h/8 points per octave of 1/h^2)
+    the LSCV kernel squares exponentials down the octaves instead of calling
+    ex2 for each; 8 bandwidths per thread keep the direct kernel.  Both against
+    the oracle, and against each other."""
+    x = datagen.correlated_mixture(n, d, seed=600 + d) if d > 1 else datagen.mixture_1d(n, seed=601)
+    x64 = host64(x)
+    h = oracle.grid_default(n, d, n_h)
+    c = 1.0 / h ** 2
+    P = n_h // 8
+    assert np.allclose(c[:-P] / c[P:], 2.0, rtol=1e-12)
+    grid, _ = kde.make_grid(n_h=n_h)
+    res_o, g_o, hh = kde.kde_lscv(dev(x), grid)                                       # octave kernel
+    res_d, g_d, _ = kde.kde_lscv(dev(x), grid, kde.make_opts(bw_per_thread=8))        # direct kernel
+    assert np.allclose(hh, h, rtol=1e-14)
+    ref = oracle.lscv_h(x64, h)
+    A = lscv_A(x64)
+    for g in (g_o, g_d):
+        assert g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, A).max() < TOL
+    assert g_err(g_o, g_d, ref["s_kk"], ref["s_k"], h, n, d, A).max() < TOL
+    tiles = kde.kde_tile_count(n, 128 if n > 2048 else 32)
+    s1, s2 = kde.kde_lscv_tile_sums(dev(x), h, 0, tiles)
+    npairs = n * (n - 1) // 2
+    assert s_err(s1, ref["s_kk"], npairs).max() < TOL
+    assert s_err(s2, ref["s_k"], npairs).max() < TOL

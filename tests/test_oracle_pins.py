@@ -104,11 +104,19 @@ def test_h0_matches_paper_constants_at_d1_and_normal_scale():
 
 
 def test_default_grid_spans_search_range():
+    """Log-spaced over Z(h0) = [h0/4, 4 h0) (Eq. LSCV-Zh0): first point at the
+    lower end, the step one n_h-th of the range's log-width, so the point after
+    the last is the upper end; with n_h a multiple of 8, 1/h^2 halves every
+    n_h/8 points."""
     g = oracle.grid_default(1000, 1, 150)
     z = oracle.h0(1000, 1)
     assert g[0] == pytest.approx(z * GOLD["search_range"]["lo_factor"], rel=1e-14)
-    assert g[-1] == pytest.approx(z * GOLD["search_range"]["hi_factor"], rel=1e-14)
-    assert np.allclose(np.diff(np.log(g)), np.log(16) / 149, rtol=1e-12)
+    step = np.log(GOLD["search_range"]["hi_factor"] / GOLD["search_range"]["lo_factor"]) / 150
+    assert np.allclose(np.diff(np.log(g)), step, rtol=1e-12)
+    assert g[-1] * np.exp(step) == pytest.approx(z * GOLD["search_range"]["hi_factor"], rel=1e-13)
+    g = oracle.grid_default(65536, 1, 256)
+    c = 1.0 / g ** 2
+    assert np.allclose(c[:-32] / c[32:], 2.0, rtol=1e-13)
 
 
 # ------------------------------------------------------------- stats
