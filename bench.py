@@ -12,8 +12,9 @@ rank): P = n(n-1)/2 pairs, 258 P evaluations per step.
   e2e       the same selections through the host-buffer entry points:
             pinned host samples in, results out, host wall clock
   roofline  the all-pairs LSCV kernel timed live with CUDA events around its
-            launch, against the ALU roofline min(MUFU ex2/clk, FP32 lanes/3)
-            x SMs x the SM clock sampled during the timed region
+            launch, against its ALU roofline (MUFU ex2 and FP32 lanes per
+            evaluation, unit rates measured by kde_probe_alu) x SMs x the SM
+            clock sampled during the timed region
   cpu_baseline  the FP64 oracle on a bounded sample (rows of the pair
             triangle, the same 256-point grid) on the host's cores
 
@@ -59,13 +60,15 @@ def lscv_per_clk(probe, d, octave):
     """ALU bound of the LSCV pair kernel in evaluations per clock and SM.
     Direct grids: one ex2 and 3 FP32 lane-operations per evaluation (the
     squared distance, 2d lanes per pair, is shared by 16 bandwidths and left
-    out).  Octave grids: 1/4 ex2, 2.25 packed multiply/add lanes (2 scalings,
-    7 squarings and 9 running sums per 16 evaluations, per residue pair) and
-    2d/16 FMA lanes for the squared distance per evaluation."""
+    out).  Octave grids, per 16 evaluations (one pair, two residues, eight
+    octaves): 6 ex2; 3 scalings, 3 squarings and 6 running sums in FMUL2/FADD2
+    (24 lanes); 3 squarings fused with their running sums in FFMA2 (6 lanes);
+    and 2d FMA lanes for the squared distance."""
     if not octave:
         return min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
-    fp32 = 1.0 / (2.25 / probe["fmul2_fadd2_lanes_per_clk_sm"] + (2.0 * d / 16.0) / probe["ffma_lanes_per_clk_sm"])
-    return min(probe["mufu_ex2_per_clk_sm"] / 0.25, fp32)
+    fp32 = 1.0 / (1.5 / probe["fmul2_fadd2_lanes_per_clk_sm"] + 0.375 / probe["ffma2_lanes_per_clk_sm"]
+                  + (2.0 * d / 16.0) / probe["ffma_lanes_per_clk_sm"])
+    return min(probe["mufu_ex2_per_clk_sm"] / 0.375, fp32)
 
 
 def lscv_basis(probe, d, octave, mhz):
@@ -73,9 +76,10 @@ def lscv_basis(probe, d, octave, mhz):
         return (f"min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM, FP32 lanes "
                 f"{probe['ffma_lanes_per_clk_sm']:.1f}/clk/SM / 3 per eval) x {probe['sm_count']} SMs x "
                 f"{mhz:.0f} MHz")
-    return (f"octave grid: min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM / 0.25 per eval, "
-            f"1 / (2.25 / {probe['fmul2_fadd2_lanes_per_clk_sm']:.1f} packed mul/add lanes + "
-            f"{2 * d}/16 / {probe['ffma_lanes_per_clk_sm']:.1f} FFMA lanes) per eval) x "
+    return (f"octave grid: min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM / 0.375 per eval, "
+            f"1 / (1.5 / {probe['fmul2_fadd2_lanes_per_clk_sm']:.1f} FMUL2/FADD2 lanes + 0.375 / "
+            f"{probe['ffma2_lanes_per_clk_sm']:.1f} FFMA2 lanes + {2 * d}/16 / "
+            f"{probe['ffma_lanes_per_clk_sm']:.1f} FFMA lanes) per eval) x "
             f"{probe['sm_count']} SMs x {mhz:.0f} MHz")
 
 

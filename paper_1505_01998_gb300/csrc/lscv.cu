@@ -144,14 +144,17 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
 // Octave grids (the bandwidths come in octaves of 1/h^2: with P points per
 // octave, c_(k-P) = 2 c_k for c = 1/h^2, so e_(k-P) = e_k^2 for every pair).
 // A thread owns two residues r, r+1 (mod P) and their 8 octaves: per pair and
-// residue two exponentials (octaves 7 and 3) by MUFU ex2, the other six
-// octaves by squaring down (at most three squarings from an exponential),
-// plus one more square below octave 0.  Since S2(k) = sum e_k^2 = S1(k-P),
-// the nine running sums (octaves 0..7 and "octave -1") give S1 and S2 of all
-// 16 bandwidths: per evaluation 1/4 ex2 and about 2 FP32 lane-operations.
+// residue three exponentials (octaves 7, 4 and 1) by MUFU ex2, the other
+// octaves by squaring down (at most two squarings from an exponential, which
+// also bounds the growth of the ex2 error to 4x), including one square below
+// octave 0.  Since S2(k) = sum e_k^2 = S1(k-P), the nine running sums
+// (octaves 0..7 and "octave -1") give S1 and S2 of all 16 bandwidths.  Per
+// evaluation: 3/8 ex2 and 15/8 packed FP32 lane-operations (3/8 of them in
+// FFMA2), which balances the FP32 pipe (about 124 lanes/clk/SM) against the
+// MUFU pipe (32 ex2/clk/SM).
 template <int D, int R, bool EDGE>
 __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, int j_lo, int j_hi,
-                                                 const float (&y)[R][D], const float2 (&nca)[2],
+                                                 const float (&y)[R][D], const float2 (&nca)[3],
                                                  float2 (&acc)[9], int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
   constexpr int CPI = DP <= 4 ? 4 / DP : 1;  // columns per iteration
@@ -181,23 +184,23 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
           const int64_t i = i0 + 32 * r, j = jg0 + jj + c;
           if (!(i < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
         }
+        // three chains per residue, each one ex2 and two squarings down: 7 -> 6 -> 5, 4 -> 3 -> 2,
+        // 1 -> 0 -> (one octave below 0); the last square of a chain feeds only its sum (FFMA2)
         const float2 q2 = make_float2(qv, qv);
-        const float2 a7 = __fmul2_rn(q2, nca[0]), a3 = __fmul2_rn(q2, nca[1]);
+        const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
         const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
-        const float2 e3 = make_float2(ex2(a3.x), ex2(a3.y));
-        const float2 e6 = __fmul2_rn(e7, e7), e2 = __fmul2_rn(e3, e3);
-        const float2 e5 = __fmul2_rn(e6, e6), e1 = __fmul2_rn(e2, e2);
-        const float2 e4 = __fmul2_rn(e5, e5), e0 = __fmul2_rn(e1, e1);
-        const float2 em = __fmul2_rn(e0, e0);
+        const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
+        const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
+        const float2 e6 = __fmul2_rn(e7, e7), e3 = __fmul2_rn(e4, e4), e0 = __fmul2_rn(e1, e1);
         acc[7] = __fadd2_rn(acc[7], e7);
         acc[6] = __fadd2_rn(acc[6], e6);
-        acc[5] = __fadd2_rn(acc[5], e5);
+        acc[5] = __ffma2_rn(e6, e6, acc[5]);
         acc[4] = __fadd2_rn(acc[4], e4);
         acc[3] = __fadd2_rn(acc[3], e3);
-        acc[2] = __fadd2_rn(acc[2], e2);
+        acc[2] = __ffma2_rn(e3, e3, acc[2]);
         acc[1] = __fadd2_rn(acc[1], e1);
         acc[0] = __fadd2_rn(acc[0], e0);
-        acc[8] = __fadd2_rn(acc[8], em);
+        acc[8] = __ffma2_rn(e0, e0, acc[8]);
       }
     }
   }
@@ -234,13 +237,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     const int hbase = (hg * kWarps + my_chunk) * B;
 
     float2 nc2[B / 2], t1[B / 2], t2[B / 2];
-    // octave grids: residues rb, rb + 1 of P; anchors at octaves 7 and 3; 9 running sums
+    // octave grids: residues rb, rb + 1 of P; ex2 at octaves 7, 4 and 1; 9 running sums
     const int P = OCT ? ds->oct_P : 0;
     const int rb = 2 * (hg * kWarps + my_chunk);
-    float2 nca[2], oacc[9];
+    float2 nca[3], oacc[9];
     if constexpr (OCT) {
       nca[0] = make_float2(ds->nc[rb + 7 * P], ds->nc[rb + 1 + 7 * P]);
-      nca[1] = make_float2(ds->nc[rb + 3 * P], ds->nc[rb + 1 + 3 * P]);
+      nca[1] = make_float2(ds->nc[rb + 4 * P], ds->nc[rb + 1 + 4 * P]);
+      nca[2] = make_float2(ds->nc[rb + P], ds->nc[rb + 1 + P]);
 #pragma unroll
       for (int j = 0; j < 9; ++j) oacc[j] = make_float2(0.f, 0.f);
     } else {
