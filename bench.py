@@ -331,7 +331,7 @@ def run_serve(args):
     for rate in args.rates:
         count = args.serve_count
         reqs = datagen.serving_requests(rate, count, seed=5)
-        srv = gbkde.Server(arena, max_slots=256)
+        srv = gbkde.Server(arena, max_slots=256, quantum_evals=args.serve_quantum)
         t0 = time.perf_counter()
         tickets = []
         for r in reqs:
@@ -398,7 +398,8 @@ def run_serve(args):
     best_plain = max(r["plain"]["requests_per_s"] for r in records)
     print(json.dumps({"workload": "serve", "metric": "served selections/s", "unit": "requests/s",
                       "value": best, "plain_path_value": best_plain,
-                      "budget_bytes": args.serve_budget_gb << 30, "rates": records}), flush=True)
+                      "budget_bytes": args.serve_budget_gb << 30, "quantum_evals": args.serve_quantum,
+                      "rates": records}), flush=True)
     return 0
 
 
@@ -681,6 +682,8 @@ def main():
                     help="batch workload: tune the small-size buckets before planning")
     ap.add_argument("--serve-count", type=int, default=120)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-quantum", type=float, default=0.0,
+                    help="work per scheduling step in direct-kernel evaluations (0 = the library default)")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
     args = ap.parse_args()
     set_n(args.n)

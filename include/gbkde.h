@@ -367,7 +367,9 @@ typedef struct kde_serve_config {
   size_t arena_bytes;     /* HBM budget                                              */
   int max_slots;          /* requests resident at once, 1 .. 1024                    */
   int max_queue;          /* waiting requests before submit returns KDE_EBUSY (0 = unbounded) */
-  double quantum_evals;   /* pair evaluations per scheduling step (0 = 2.4e11, ~27 ms) */
+  double quantum_evals;   /* work per scheduling step, in evaluations of the direct
+                             LSCV kernel: an octave-grid LSCV evaluation counts 0.55,
+                             a psi_6 / psi_4 evaluation 1.65 / 1.35 (0 = 1.3e11, ~14 ms) */
   int step_deadline_ms;   /* a step still running after this fails its requests with
                              KDE_ETIMEDOUT (host-side detection; 0 = no deadline)     */
   int device;             /* CUDA device index                                       */

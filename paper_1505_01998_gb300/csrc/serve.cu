@@ -178,11 +178,21 @@ struct kde_server {
 
 namespace {
 
-// Pair evaluations per scheduling step (default 2.4e11: about 27 ms of the
-// all-pairs kernels on a GB300, long against the ~0.1 ms launch overhead and
-// the item tails of a step, short against the latency of a large request).
+// Work per scheduling step, in evaluations of the direct LSCV kernel
+// (default 1.3e11: about 14 ms of the all-pairs kernels on a GB300, long
+// against the ~0.1 ms launch overhead and the item tails of a step, short
+// against the latency of a large request).
 double step_budget(const kde_server* s) {
-  return s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 2.4e11;
+  return s->cfg.quantum_evals > 0 ? s->cfg.quantum_evals : 1.3e11;
+}
+
+// Cost of one evaluation relative to one of the direct LSCV kernel, from the
+// kernels' measured rates on a GB300 (direct LSCV 9.3e12 evaluations/s,
+// octave-grid LSCV 17.1e12, psi_6 5.6e12, psi_4 6.9e12), so that a step
+// takes about the same time whatever mix of kernels it runs.
+double eval_cost(const Req* r) {
+  if (r->phase == P_LSCV) return r->geo.oct_P > 0 ? 0.55 : 1.0;
+  return r->phase == P_PSI6 ? 1.65 : 1.35;
 }
 
 void finish_req(kde_server* s, Req* r, int status) {
@@ -306,7 +316,7 @@ bool launch_step(kde_server* s, int* err) {
   Step st;
   st.buf = buf;
   st.seq = s->steps + 1;
-  double used = 0;
+  double used = 0, step_evals = 0;  // work in direct-kernel evaluations; evaluations run
   std::vector<Req*> new_descs;
   // oldest admitted first
   std::vector<Req*> active;
@@ -317,7 +327,7 @@ bool launch_step(kde_server* s, int* err) {
   // remaining work first (short requests finish within a few steps even
   // while long ones run), then any remainder back to the oldest.
   auto remaining = [](const Req* r) {
-    return (double)(phase_items(r) - r->cursor) * item_evals(r);
+    return (double)(phase_items(r) - r->cursor) * item_evals(r) * eval_cost(r);
   };
   std::sort(active.begin(), active.end(), [](const Req* a, const Req* b) { return a->t_admit < b->t_admit; });
   if (active.size() > 2)
@@ -350,15 +360,16 @@ bool launch_step(kde_server* s, int* err) {
     const int64_t left = total - r->cursor;
     const double cap = (oi == 0 && order.size() > 2) ? 0.25 * budget : budget;
     if (left > 0 && (used < cap || st.refs.empty())) {
-      const double per = item_evals(r);
-      int64_t take = (int64_t)std::max(1.0, std::floor((cap - used) / per));
+      const double per = item_evals(r), cost = per * eval_cost(r);
+      int64_t take = (int64_t)std::max(1.0, std::floor((cap - used) / cost));
       take = std::min(take, left);
       G& g = group_of(r->phase, r);
       if (g.take[r->slot] == 0) g.base[r->slot] = r->cursor;  // a second pass extends the range
       g.take[r->slot] += take;
       g.total += take;
       r->cursor += take;
-      used += take * per;
+      used += take * cost;
+      step_evals += take * per;
       r->evals += take * per;
       referenced = true;
       if (r->cursor == total) {
@@ -481,7 +492,7 @@ bool launch_step(kde_server* s, int* err) {
   if (!st.done) ck(cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming), "event");
   ck(cudaEventRecord(st.done, cs), "event record");
   st.launched = Clock::now();
-  st.evals = used;
+  st.evals = step_evals;
   s->inflight.push_back(st);
   s->next_buf ^= 1;
   s->steps++;

@@ -136,7 +136,10 @@ def test_cancel_queued_and_running(kde):
     grid = kde.make_grid(n_h=256)[0]
     big = datagen.skewed_column(65536, seed=9)
     small = datagen.mixture_1d(3000, seed=3).astype(np.float32)
-    srv = kde.Server(arena(1 << 30), max_slots=1)  # one slot: the second request queues
+    # one slot: the second request queues.  A cancel takes effect at the next
+    # step boundary (the two steps in flight run to their end), so the step
+    # budget keeps the big request (5.5e11 evaluations) spread over ~6 steps.
+    srv = kde.Server(arena(1 << 30), max_slots=1, quantum_evals=5e10)
     t_big = srv.submit(big, LSCV, grid)
     t_q = srv.submit(small, LSCV, grid)
     t_ok = srv.submit(small, PLUGIN)
