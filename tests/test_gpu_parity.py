@@ -425,6 +425,26 @@ def test_prologue_statistics_across_ranges(kde, n, d, dtype):
     assert abs(logdet - np.linalg.slogdet(S_ref)[1]) < 1e-5 * max(1.0, abs(np.linalg.slogdet(S_ref)[1])) * d
 
 
+def test_octave_kernel_input_types_precisions_and_grid_shapes(kde):
+    """The octave kernel with FP64 samples, with plain FP32 sums, with the
+    smallest octave grid (16 points, 2 per octave), and a grid of that shape
+    given explicitly (bitwise the default grid's result).  A grid one part in
+    1e9 off the octave shape takes the direct kernel, also within tolerance."""
+    x = datagen.mixture_1d(4000, seed=611)
+    h = oracle.grid_default(4000, 1, 128)
+    _lscv_check(kde, x, h, dtype="float64")
+    _lscv_check(kde, x, h, opts=kde.make_opts(precision=kde.KDE_FP32_PLAIN))
+    x3 = datagen.correlated_mixture(1800, 3, seed=612)
+    _lscv_check(kde, x3, oracle.grid_default(1800, 3, 16))
+    grid, _ = kde.make_grid(n_h=128)
+    _, g_default, h_default = kde.kde_lscv(dev(x), grid)
+    _, g_explicit, _ = kde.kde_lscv(dev(x), _explicit(kde, h_default))
+    assert np.array_equal(g_default, g_explicit)
+    off = h.copy()
+    off[37] *= 1 + 1e-9
+    _lscv_check(kde, x, off)
+
+
 @pytest.mark.parametrize("d,n,n_h", [(1, 3001, 128), (2, 2050, 256), (5, 1500, 96), (1, 700, 16 * 8)])
 def test_octave_kernel_against_direct_kernel_and_oracle(kde, d, n, n_h):
     """On an octave grid (the default grid: n_h/8 points per octave of 1/h^2)
