@@ -97,7 +97,8 @@ typedef struct kde_grid {
 typedef struct kde_opts {
   int precision;      /* KDE_FP32_KAHAN (0) or KDE_FP32_PLAIN                  */
   int tile;           /* LSCV pair tile edge T: 32 or 128 samples               */
-  int bw_per_thread;  /* LSCV bandwidths per thread B: 8 or 16                  */
+  int bw_per_thread;  /* LSCV bandwidths per thread B: 2, 8 or 16 (0: 2 for grids
+                         of 1 or 2 points, else the tuner's or the default rule) */
   int tiles_per_item; /* tiles per work item K (1 .. 4096)                      */
   int ctas_per_sm;    /* resident CTAs per SM of the persistent pair kernels    */
   int cv;             /* LSCV weights: KDE_CV_PAPER (0) or KDE_CV_LOO           */

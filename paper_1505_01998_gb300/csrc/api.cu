@@ -53,8 +53,8 @@ int check_opts(const kde_opts* o) {
     return fail(KDE_EINVAL, "opts.precision %d invalid", o->precision);
   if (o->tile != 0 && o->tile != 32 && o->tile != 128)
     return fail(KDE_EINVAL, "opts.tile %d invalid (0, 32 or 128)", o->tile);
-  if (o->bw_per_thread != 0 && o->bw_per_thread != 8 && o->bw_per_thread != 16)
-    return fail(KDE_EINVAL, "opts.bw_per_thread %d invalid (0, 8 or 16)", o->bw_per_thread);
+  if (o->bw_per_thread != 0 && o->bw_per_thread != 2 && o->bw_per_thread != 8 && o->bw_per_thread != 16)
+    return fail(KDE_EINVAL, "opts.bw_per_thread %d invalid (0, 2, 8 or 16)", o->bw_per_thread);
   if (o->tiles_per_item < 0 || o->tiles_per_item > 4096)
     return fail(KDE_EINVAL, "opts.tiles_per_item %d invalid", o->tiles_per_item);
   if (o->ctas_per_sm < 0 || o->ctas_per_sm > 8)
@@ -91,6 +91,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   // dimension and size bucket (throughput tuning first), else the fixed rules.
   kde_opts eff{};
   if (o) eff = *o;
+  const int B_given = eff.bw_per_thread;
   int kscale = 1;
   kde_opts t;
   if (n_h > 0 && (!eff.tile || !eff.bw_per_thread || !eff.ctas_per_sm || !eff.tiles_per_item) &&
@@ -116,7 +117,15 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->T = (o && o->tile) ? o->tile : (n <= 2048 ? 32 : 128);
   if (g->dk > 4) g->T = 32;  // one row per lane keeps the d > 4 coordinates in registers
   g->R = g->T / 32;
-  g->B = (o && o->bw_per_thread) ? o->bw_per_thread : (n_h <= 64 ? 8 : 16);
+  // a one- or two-point grid (one g(H) of LSCV_H is a one-point grid) takes 2
+  // bandwidths per thread unless the caller asked otherwise, whatever the
+  // tuner chose for its size bucket: 8 would evaluate 6 padding bandwidths
+  if (B_given)
+    g->B = B_given;
+  else if (n_h <= 2)
+    g->B = 2;
+  else
+    g->B = o->bw_per_thread ? o->bw_per_thread : (n_h <= 64 ? 8 : 16);
   const int nh = std::max(n_h, 1);
   g->n_h_pad = (nh + g->B - 1) / g->B * g->B;
   g->n_chunks = g->n_h_pad / g->B;
@@ -126,7 +135,9 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   if (o && o->tiles_per_item) {
     g->K = o->tiles_per_item;
   } else {
-    const int64_t target = 4 * (int64_t)g->ctas;
+    // block items: about 4 per CTA; warp items (equal tile counts, one per
+    // warp) keep the partial rows, and so the reduction, short
+    const int64_t target = lscv_warp_items(g->dk, g->B) ? (int64_t)g->ctas * kWarps : 4 * (int64_t)g->ctas;
     g->K = (int)std::min<int64_t>(4096, kscale * std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
   }
   if (max_item_evals > 0 && !(o && o->tiles_per_item)) {
@@ -275,6 +286,12 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
   s.psi_rows = g.prows;
   s.psi_t0 = 0;
   s.psi_part = reinterpret_cast<double*>(ws + g.off_ppart);
+  // the constant factors of A (Eqs. LSCV-Kx, LSCV-KKx) and of the pilot g1 (Eqs.
+  // PLUGIN-Psi8Estimate, PLUGIN-g1) in FP64 on the host
+  const double pi = 3.14159265358979323846;
+  const double k6_0 = -15.0 / std::sqrt(2.0 * pi);
+  s.c_A = std::pow(4.0 * pi, -0.5 * g.d);
+  s.c_g1 = std::pow(-2.0 * k6_0 * 32.0 * std::sqrt(pi) / (105.0 * (double)g.n), 1.0 / 9.0);
   s.res.status = KDE_OK;
   return s;
 }

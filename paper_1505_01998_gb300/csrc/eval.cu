@@ -438,10 +438,10 @@ __global__ void __launch_bounds__(kThreads) k_aqp(const TIN* __restrict__ x, int
     } else {  // a narrow range: one window over both ends
       for (int i = i1 + lane; i < i4; i += 32) aqp_full(key[kp(i)], lo, hi, inv_h, h_phi, c_run, s_run);
     }
-    const double vc = warp_sum((double)c_run), vs = warp_sum((double)s_run);
+    const float2 vc = warp_sum_ff(c_run, 0.f), vs = warp_sum_ff(s_run, 0.f);
     if (lane == 0) {
-      part[((int64_t)blockIdx.x * m + g) * 2] = vc + c_in;
-      part[((int64_t)blockIdx.x * m + g) * 2 + 1] = vs + s_in;
+      part[((int64_t)blockIdx.x * m + g) * 2] = ff_value(vc) + c_in;
+      part[((int64_t)blockIdx.x * m + g) * 2 + 1] = ff_value(vs) + s_in;
     }
   }
 }

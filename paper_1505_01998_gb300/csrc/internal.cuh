@@ -63,6 +63,8 @@ struct DsDev {
   double logdet;
   double sigma;
   double A;                // (4 pi)^(-d/2) |S|^(-1/2)
+  double c_A;              // (4 pi)^(-d/2), from the host
+  double c_g1;             // g1 / sigma of the PLUGIN pilot, (-2 K6(0) 32 sqrt(pi) / (105 n))^(1/9), from the host
   float M[KDE_MAX_D * KDE_MAX_D];  // sqrt(log2(e)/4) L^-1, row-major, lower triangular
   kde_result res;
 };
@@ -108,6 +110,12 @@ __host__ __device__ inline void tile_coords(int64_t bx, int64_t& l, int64_t& q) 
 // cg (1..8) chunks of B bandwidths: the chunk it evaluates and the slice of
 // the tile's columns it walks.  S = kWarps / cg slices per chunk, so
 // S * cg <= kWarps; warps with slice >= S idle.
+// Pair-kernel shapes whose items are walked by single warps (k_lscv_warp):
+// wide samples (d > 4, padded to 8/12/16 coordinates) with 2 bandwidths per
+// thread (grids of one or two points).  The geometry sizes their items for
+// 8 times as many workers.
+__host__ __device__ constexpr bool lscv_warp_items(int dk, int B) { return dk > 4 && B == 2; }
+
 struct WarpRole {
   int chunk, slice, S;
   bool active;
@@ -156,6 +164,29 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Warp sum of values hi + lo carried as FP32 pairs (double-float): at every
+// butterfly step the two heads are added by Knuth's TwoSum, whose rounding
+// error joins the tails, and the pair is renormalised by Dekker's Fast2Sum.
+// The result carries about 44 bits; FP32 arithmetic only, since the FP64
+// pipe of this part runs at a small fraction of the FP32 rate.  Every lane
+// ends with the same pair (each step is symmetric in its two operands).
+__device__ __forceinline__ float2 warp_sum_ff(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = __fadd_rn(hi, h2);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+    const float t = __fadd_rn(__fadd_rn(lo, l2), e);
+    hi = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(hi, s));
+  }
+  return make_float2(hi, lo);
+}
+
+__device__ __forceinline__ double ff_value(float2 p) { return (double)p.x + (double)p.y; }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll

@@ -97,6 +97,49 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
     }
     return;
   }
+  if constexpr (D > 4) {
+    // wide samples, one row per lane: sF holds -v.  Two columns per
+    // iteration, each squared distance in packed FP32x2 over coordinate
+    // pairs (two independent chains joined by one add), so that a warp has
+    // four chains in flight instead of one.  Slices of columns are even.
+    static_assert(R == 1 && DP % 4 == 0, "wide path: one row per lane");
+    float2 y2[DP / 2];
+#pragma unroll
+    for (int k = 0; k < DP / 2; ++k)
+      y2[k] = make_float2(2 * k < D ? y[0][2 * k] : 0.f, 2 * k + 1 < D ? y[0][2 * k + 1] : 0.f);
+#pragma unroll 1
+    for (int jj = j_lo; jj < j_hi; jj += 2) {
+      float2 q2[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < DP / 4; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(sF + (jj + c) * DP + 4 * u);
+          const float2 d0 = __fadd2_rn(y2[2 * u], make_float2(v.x, v.y));
+          const float2 d1 = __fadd2_rn(y2[2 * u + 1], make_float2(v.z, v.w));
+          acc = __ffma2_rn(d0, d0, acc);
+          acc = __ffma2_rn(d1, d1, acc);
+        }
+        float qv = __fadd_rn(acc.x, acc.y);
+        if (EDGE) {
+          const int64_t j = jg0 + jj + c;
+          if (!(i0 < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
+        }
+        q2[c] = make_float2(qv, qv);
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int bp = 0; bp < B / 2; ++bp) {
+          const float2 a = __fmul2_rn(q2[c], nc2[bp]);
+          const float2 e = make_float2(ex2(a.x), ex2(a.y));
+          t1[bp] = __fadd2_rn(t1[bp], e);
+          t2[bp] = __ffma2_rn(e, e, t2[bp]);
+        }
+    }
+    return;
+  }
   constexpr int CPI = DP <= 4 ? 4 / DP : 1;  // columns per iteration
   constexpr int NV = CPI * DP / 4;           // 16-byte shared-memory loads per iteration
 #pragma unroll 1
@@ -206,6 +249,99 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
   }
 }
 
+// Wide samples (d > 4) on a grid of one or two points, e.g. one g(H) of
+// LSCV_H: one warp per item.  With a single chunk of bandwidths the block
+// kernel splits each 32 x 32 tile among its 8 warps, four columns each, and a
+// warp's share of a tile is small against the tile's fixed costs.  Here each
+// warp walks the K tiles of its own item with all 32 columns, staging the
+// column samples (negated) in its own slice of shared memory; only warp-level
+// synchronisation.  Items are numbered as in the block kernel (one group), so
+// the partial rows and their reduction are the same.
+template <int D, bool KAHAN>
+__global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
+  constexpr int T = 32, B = 2, DP = DPad<D>::value;
+  static_assert(D > 4 && DP % 4 == 0, "wide samples only");
+  __shared__ __align__(16) float sFw[kWarps][T * DP];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* sF = sFw[warp];
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  for (int64_t it = (int64_t)blockIdx.x * kWarps + warp; it < ph.total; it += nw) {
+    const int di = find_ds(ph.off, ph.n_ds, it);
+    const DsDev* ds = ph.ds + di;
+    if (ds->res.status != KDE_OK) continue;
+    const int64_t row = it - ph.off[di] + (ph.base ? ph.base[di] : 0);
+    const int64_t tb = ds->lscv_t0 + row * ds->lscv_K;
+    const int64_t te = min(tb + (int64_t)ds->lscv_K, ds->lscv_tiles);
+    const float2 nc2[1] = {make_float2(ds->nc[0], ds->nc[1])};
+    float2 t1[1] = {make_float2(0.f, 0.f)}, t2[1] = {make_float2(0.f, 0.f)};
+    float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};  // Kahan (s, c): S1 b0, S1 b1, S2 b0, S2 b1
+    const int64_t n = ds->n, n_pad = ds->n_pad;
+    const float* __restrict__ Y = ds->y;
+    int64_t l, q;
+    tile_coords(tb, l, q);
+    int64_t l_loaded = -1;
+    float yn[1][D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) yn[0][k] = Y[(int64_t)k * n_pad + q * T + lane];
+    int run = 0;
+    for (int64_t t = tb; t < te; ++t) {
+      if (l != l_loaded) {
+        __syncwarp();
+        for (int idx = lane; idx < T * DP; idx += 32) {
+          const int jj = idx / DP, k = idx - jj * DP;
+          sF[idx] = (k < D) ? -Y[(int64_t)k * n_pad + l * T + jj] : 0.f;
+        }
+        __syncwarp();
+        l_loaded = l;
+      }
+      float y[1][D];
+      const int64_t qn = (q + 1 > l) ? 0 : q + 1;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        y[0][k] = yn[0][k];
+        if (t + 1 < te) yn[0][k] = Y[(int64_t)k * n_pad + qn * T + lane];
+      }
+      const bool edge = (q == l) || ((l + 1) * T > n);
+      const int64_t i0 = q * T + lane, jg0 = l * T;
+      if (edge)
+        lscv_columns<D, B, 1, true>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+      else
+        lscv_columns<D, B, 1, false>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+      if (KAHAN && ++run >= 8) {  // runs of 256 terms
+        kahan_add(ks[0], kc[0], t1[0].x);
+        kahan_add(ks[1], kc[1], t1[0].y);
+        kahan_add(ks[2], kc[2], t2[0].x);
+        kahan_add(ks[3], kc[3], t2[0].y);
+        t1[0] = t2[0] = make_float2(0.f, 0.f);
+        run = 0;
+      }
+      if (++q > l) {
+        ++l;
+        q = 0;
+      }
+    }
+    float2 tot[4];
+    const float tail[4] = {t1[0].x, t1[0].y, t2[0].x, t2[0].y};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (KAHAN) {
+        kahan_add(ks[m], kc[m], tail[m]);
+        tot[m] = warp_sum_ff(ks[m], -kc[m]);
+      } else {
+        tot[m] = warp_sum_ff(tail[m], 0.f);
+      }
+    }
+    if (lane == 0) {
+      // row layout of the block kernel: (S1, S2) of bandwidth 0, then of bandwidth 1
+      double* out = ds->lscv_part + row * (2 * (int64_t)ds->n_h_pad);
+      out[0] = ff_value(tot[0]);
+      out[1] = ff_value(tot[2]);
+      out[2] = ff_value(tot[1]);
+      out[3] = ff_value(tot[3]);
+    }
+  }
+}
+
 template <int D, int B, int R, bool KAHAN, bool OCT>
 __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
   constexpr int T = 32 * R;
@@ -266,6 +402,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     tile_coords(tb, l, q);
     int64_t l_loaded = -1;
     int run = 0;
+    // wide samples (d > 4, one row per lane, few columns per warp and tile):
+    // the rows of the next tile are loaded while the current one is evaluated
+    constexpr bool kPrefetch = D > 4;
+    float yn[kPrefetch ? R : 1][kPrefetch ? D : 1];
+    if constexpr (kPrefetch) {
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < D; ++k) yn[r][k] = Y[(int64_t)k * n_pad + q * T + lane + 32 * r];
+    }
     for (int64_t t = tb; t < te; ++t) {
       if (l != l_loaded) {
         __syncthreads();
@@ -274,6 +420,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
           const float v = (k < D) ? Y[(int64_t)k * n_pad + l * T + jj] : 0.f;
           if constexpr (kPackedQ<D, R, OCT>)
             reinterpret_cast<float2*>(sF)[idx] = make_float2(-v, -v);
+          else if constexpr (D > 4 && !OCT)
+            sF[idx] = -v;  // the wide path adds -v
           else
             sF[idx] = v;
         }
@@ -281,10 +429,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
         l_loaded = l;
       }
       float y[R][D];
+      if constexpr (kPrefetch) {
+        const int64_t qn = (q + 1 > l) ? 0 : q + 1;
 #pragma unroll
-      for (int r = 0; r < R; ++r)
+        for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int k = 0; k < D; ++k) y[r][k] = Y[(int64_t)k * n_pad + q * T + lane + 32 * r];
+          for (int k = 0; k < D; ++k) {
+            y[r][k] = yn[r][k];
+            if (t + 1 < te) yn[r][k] = Y[(int64_t)k * n_pad + qn * T + lane + 32 * r];
+          }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int k = 0; k < D; ++k) y[r][k] = Y[(int64_t)k * n_pad + q * T + lane + 32 * r];
+      }
       const bool edge = (q == l) || ((l + 1) * T > n);
       const int64_t i0 = q * T + lane, jg0 = l * T;
       if constexpr (OCT) {
@@ -331,27 +490,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
         q = 0;
       }
     }
-    // ---- item total: lanes (FP64 butterfly), then column slices in fixed order
+    // ---- item total: lanes (double-float butterfly in FP32), then column
+    // slices in fixed order (FP64)
     __syncthreads();
     if constexpr (OCT) {
       // running sums j = 0..8 per residue; local bandwidth b = residue + 2 * octave
-      double vs[9][2];
+      float2 vs[9][2];
 #pragma unroll
       for (int j = 0; j < 9; ++j) {
-        double v0, v1;
+        float h0, l0, h1, l1;
         if (KAHAN) {
           float4 k = sK[(warp * B + j) * 32 + lane];
           kahan_add(k.x, k.y, oacc[j].x);  // unflushed tail of the run
           kahan_add(k.z, k.w, oacc[j].y);
-          v0 = (double)k.x - (double)k.y;
-          v1 = (double)k.z - (double)k.w;
+          h0 = k.x, l0 = -k.y, h1 = k.z, l1 = -k.w;
         } else {
-          v0 = oacc[j].x;
-          v1 = oacc[j].y;
+          h0 = oacc[j].x, l0 = 0.f, h1 = oacc[j].y, l1 = 0.f;
         }
-        if (!active) v0 = v1 = 0.0;
-        vs[j][0] = warp_sum(v0);
-        vs[j][1] = warp_sum(v1);
+        if (!active) h0 = l0 = h1 = l1 = 0.f;
+        vs[j][0] = warp_sum_ff(h0, l0);
+        vs[j][1] = warp_sum_ff(h1, l1);
       }
       if (lane == 0) {
 #pragma unroll
@@ -359,8 +517,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
 #pragma unroll
           for (int rr = 0; rr < 2; ++rr) {
             const int b = rr + 2 * oc;
-            sRed[(warp * B + b) * 2] = vs[oc][rr];                        // S1 at octave oc
-            sRed[(warp * B + b) * 2 + 1] = vs[oc == 0 ? 8 : oc - 1][rr];  // S2 = S1 an octave below
+            sRed[(warp * B + b) * 2] = ff_value(vs[oc][rr]);                        // S1 at octave oc
+            sRed[(warp * B + b) * 2 + 1] = ff_value(vs[oc == 0 ? 8 : oc - 1][rr]);  // S2 = S1 an octave below
           }
       }
     }
@@ -369,25 +527,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int b = 2 * bp + half;
-        double v1, v2;
+        float h1, l1, h2, l2;
         if (KAHAN) {
           float4 k = sK[(warp * B + b) * 32 + lane];
           const float r1 = half ? t1[bp].y : t1[bp].x;  // unflushed tail of the run
           const float r2 = half ? t2[bp].y : t2[bp].x;
           kahan_add(k.x, k.y, r1);
           kahan_add(k.z, k.w, r2);
-          v1 = (double)k.x - (double)k.y;
-          v2 = (double)k.z - (double)k.w;
+          h1 = k.x, l1 = -k.y, h2 = k.z, l2 = -k.w;
         } else {
-          v1 = half ? t1[bp].y : t1[bp].x;
-          v2 = half ? t2[bp].y : t2[bp].x;
+          h1 = half ? t1[bp].y : t1[bp].x, l1 = 0.f;
+          h2 = half ? t2[bp].y : t2[bp].x, l2 = 0.f;
         }
-        if (!active) v1 = v2 = 0.0;
-        v1 = warp_sum(v1);
-        v2 = warp_sum(v2);
+        if (!active) h1 = l1 = h2 = l2 = 0.f;
+        const float2 v1 = warp_sum_ff(h1, l1), v2 = warp_sum_ff(h2, l2);
         if (lane == 0) {
-          sRed[(warp * B + b) * 2] = v1;
-          sRed[(warp * B + b) * 2 + 1] = v2;
+          sRed[(warp * B + b) * 2] = ff_value(v1);
+          sRed[(warp * B + b) * 2 + 1] = ff_value(v2);
         }
       }
     }
@@ -409,40 +565,58 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
   }
 }
 
-// Sum of the per-item partial rows, one 32-column strip per CTA: warp w adds
-// rows w, w+8, ... in that order; the 8 warp sums are added in order.  The
-// loads of 8 consecutive rows of a warp are issued before their adds (the
+// Sum of the per-item partial rows, one strip of up to 32 columns per CTA.
+// With wc columns in the strip, thread t takes column t % wc and row part
+// t / wc of P = 256 / wc parts: it adds rows part, part + P, ... in that
+// order, and the P part sums of a column are added in order.  A full strip
+// (wc = 32) is warp w adding rows w, w + 8, ...; a narrow one (a grid of one
+// or two points has 4 columns) spreads its rows over all 256 threads.  The
+// loads of 8 consecutive rows of a part are issued before their adds (the
 // addition order is unchanged), so the loop is not bound by load latency.
 __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
-  __shared__ double s[kWarps][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double s[kThreads];
   if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
   const int W = 2 * ds->n_h_pad;
-  const int col = blockIdx.y * 32 + lane;
+  const int c0 = blockIdx.y * 32;
+  if (c0 >= W) return;
+  const int wc = min(32, W - c0);
+  const int P = kThreads / wc;
+  const int t = threadIdx.x;
   double acc = 0.0;
-  if (col < W) {
-    const double* p = ds->lscv_part + col;
+  if (t < P * wc) {
+    const double* p = ds->lscv_part + c0 + t % wc;
     const int64_t rows = ds->lscv_rows;
     constexpr int U = 8;
-    int64_t r = warp;
-    for (; r + (U - 1) * kWarps < rows; r += U * kWarps) {
+    int64_t r = t / wc;
+    for (; r + (U - 1) * P < rows; r += U * P) {
       double v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = p[(r + u * kWarps) * W];
+      for (int u = 0; u < U; ++u) v[u] = p[(r + (int64_t)u * P) * W];
 #pragma unroll
       for (int u = 0; u < U; ++u) acc += v[u];
     }
-    for (; r < rows; r += kWarps) acc += p[r * W];
+    for (; r < rows; r += P) acc += p[r * W];
   }
-  s[warp][lane] = acc;
+  s[t] = acc;
   __syncthreads();
-  if (warp == 0 && col < W) {
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += s[w][lane];
-    ds->lscv_sum[col] = t;
+  if (t < wc) {
+    double tot = 0.0;
+    for (int part = 0; part < P; ++part) tot += s[part * wc + t];
+    ds->lscv_sum[c0 + t] = tot;
   }
+}
+
+// Order of (value, index) candidates for a first-index argmin: a number
+// before NaN, a smaller number first, equal values (or two NaNs) by index;
+// index -1 marks no candidate.
+__device__ __forceinline__ bool argmin_before(double g, int k, double h, int j) {
+  if (k < 0) return false;
+  if (j < 0) return true;
+  const bool gn = g != g, hn = h != h;
+  if (gn != hn) return hn;
+  if (!gn && g != h) return g < h;
+  return k < j;
 }
 
 // g(h) on the grid and its first-index argmin (Eqs. LSCV-gh, LSCV-finalH).
@@ -454,19 +628,51 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
   const double c2 = exp2(1.0 + 0.5 * d);
   // K-term weight: the paper's n^-2 (Eq. LSCV-gh) or exact leave-one-out 1/(n(n-1))
   const double wk = ds->cv_loo ? 2.0 / (n * (n - 1.0)) : 2.0 / (n * n);
+  // g(h_k) per thread (h^-d by d multiplications and one division), and the
+  // first index of the minimum: per thread over its k, then lexicographic
+  // (g, k) minima across lanes and warps (NaN ranks above every number)
+  __shared__ double sg[kWarps];
+  __shared__ int sk[kWarps];
+  double gb = 0.0;
+  int best = -1;
   for (int k = threadIdx.x; k < n_h; k += blockDim.x) {
     const double s1 = ds->lscv_sum[2 * k], s2 = ds->lscv_sum[2 * k + 1];
-    ds->g[k] = pow(ds->h[k], -(double)d) * ds->A * (2.0 / (n * n) * s1 - wk * c2 * s2 + 1.0 / n);
+    const double hk = ds->h[k];
+    double hd = 1.0;
+    for (int i = 0; i < d; ++i) hd *= hk;
+    const double gk = ds->A / hd * (2.0 / (n * n) * s1 - wk * c2 * s2 + 1.0 / n);
+    ds->g[k] = gk;
+    if (argmin_before(gk, k, gb, best)) {
+      gb = gk;
+      best = k;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double og = __shfl_xor_sync(0xffffffffu, gb, o);
+    const int ok = __shfl_xor_sync(0xffffffffu, best, o);
+    if (argmin_before(og, ok, gb, best)) {
+      gb = og;
+      best = ok;
+    }
+  }
+  if (lane == 0) {
+    sg[warp] = gb;
+    sk[warp] = best;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int best = 0;
-    double gb = ds->g[0];
-    for (int k = 1; k < n_h; ++k)
-      if (ds->g[k] < gb) {
-        gb = ds->g[k];
-        best = k;
+    gb = sg[0];
+    best = sk[0];
+    for (int w = 1; w < kWarps; ++w) {
+      const double og = sg[w];
+      const int ok = sk[w];
+      if (argmin_before(og, ok, gb, best)) {
+        gb = og;
+        best = ok;
       }
+    }
     kde_result& r = ds->res;
     r.method |= KDE_METHOD_LSCV;
     r.argmin = best;
@@ -481,17 +687,23 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
 
 template <int D, int B, int R, bool KAHAN, bool OCT>
 cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
-  const size_t smem = lscv_smem_bytes(D, B, R, KAHAN, OCT);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN, OCT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
+  if constexpr (lscv_warp_items(D, B)) {  // static shared memory: no attribute to set
+    if (grid <= 0) return cudaSuccess;
+    k_lscv_warp<D, KAHAN><<<grid, kThreads, 0, st>>>(ph);
+    return cudaGetLastError();
+  } else {
+    const size_t smem = lscv_smem_bytes(D, B, R, KAHAN, OCT);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN, OCT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
+    k_lscv<D, B, R, KAHAN, OCT><<<grid, kThreads, smem, st>>>(ph);
+    return cudaGetLastError();
   }
-  if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
-  k_lscv<D, B, R, KAHAN, OCT><<<grid, kThreads, smem, st>>>(ph);
-  return cudaGetLastError();
 }
 
 template <int D, int B, int R>
@@ -518,6 +730,7 @@ cudaError_t launch_r(const Phase& ph, int R, bool kahan, bool oct, int grid, cud
 template <int D>
 cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, bool oct, int grid, cudaStream_t st) {
   switch (B) {
+    case 2: return launch_r<D, 2>(ph, R, kahan, oct, grid, st);
     case 8: return launch_r<D, 8>(ph, R, kahan, oct, grid, st);
     case 16: return launch_r<D, 16>(ph, R, kahan, oct, grid, st);
     default: return cudaErrorInvalidValue;

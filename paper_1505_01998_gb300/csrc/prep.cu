@@ -1,6 +1,7 @@
 // Prologue kernels: descriptor setup, sample statistics, Cholesky whitening
 // and the first links of the PLUGIN chain; plus the ALU throughput probe.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -8,30 +9,34 @@ namespace gbkde {
 
 namespace {
 
-constexpr double kLog2e = 1.4426950408889634074;
-constexpr double kPi = 3.14159265358979323846;
+constexpr double kSqrtPi = 1.7724538509055159;           // sqrt(pi) in FP64
+constexpr double kSqrtHalfLog2e = 0.8493218002880191;     // sqrt(log2(e) / 2) in FP64
+constexpr double kSqrtQuarterLog2e = 0.6005612043932249;  // sqrt(log2(e) / 4) in FP64
 constexpr int kPrepThreads = 512;
 
+constexpr int kDsWords = (int)(sizeof(DsDev) / sizeof(uint64_t));
+static_assert(sizeof(DsDev) % sizeof(uint64_t) == 0, "descriptor copied as 8-byte words");
+
 struct SetupParams {
-  DsDev init;
+  uint64_t init[kDsWords];  // the host-built descriptor, as words
   int64_t off[4];
   int32_t n_off;
-  int32_t n_h;
+  int32_t n_h, n_h_pad;
+  double* h_dst;            // the descriptor's h[] and nc[]
+  float* nc_dst;
   double h[KDE_MAX_NH];
+  float nc[KDE_MAX_NH];     // -1/h^2 (FP64, rounded to FP32; padding entries -1)
 };
 
-// Copies the host-built descriptor into device memory and expands the grid:
-// h[k] and nc[k] = -1/h_k^2 (padded chunk entries get -1).
+// Copies the host-built descriptor into device memory, one word per thread,
+// and the grid's h[k] and nc[k] = -1/h_k^2 into its arrays.
 __global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams p) {
-  if (threadIdx.x == 0) *dst = p.init;
+  uint64_t* d64 = reinterpret_cast<uint64_t*>(dst);
+  for (int i = threadIdx.x; i < kDsWords; i += blockDim.x) d64[i] = p.init[i];
   if (threadIdx.x < p.n_off) off_dst[threadIdx.x] = p.off[threadIdx.x];
-  for (int k = threadIdx.x; k < p.init.n_h_pad; k += blockDim.x) {
-    if (k < p.n_h) {
-      p.init.h[k] = p.h[k];
-      p.init.nc[k] = (float)(-1.0 / (p.h[k] * p.h[k]));
-    } else {
-      p.init.nc[k] = -1.0f;
-    }
+  for (int k = threadIdx.x; k < p.n_h_pad; k += blockDim.x) {
+    if (k < p.n_h) p.h_dst[k] = p.h[k];
+    p.nc_dst[k] = p.nc[k];
   }
 }
 
@@ -44,22 +49,34 @@ struct Acc<float> {
   float s = 0.f, c = 0.f;
   __device__ void add(float v) { kahan_add(s, c, v); }
   __device__ double get() const { return (double)s - (double)c; }
+  // the lane's total as a double-float pair (value s - c)
+  __device__ float2 lane() const { return make_float2(s, -c); }
 };
 template <>
 struct Acc<double> {
   double s = 0.0;
   __device__ void add(double v) { s += v; }
   __device__ double get() const { return s; }
+  __device__ double lane() const { return s; }
 };
 
-// Block-wide FP64 sum of `cnt` values per thread, deterministic order;
-// results land in out[0..cnt) (shared memory) for every thread.
-__device__ void block_sum(double* v, int cnt, double (*scratch)[kNPairs], double* out) {
+// Warp total of one value per lane into *dst (lane 0): FP64 lanes by an FP64
+// butterfly; double-float lanes (FP32 input) in FP32 arithmetic.
+__device__ __forceinline__ void warp_total(double v, double* dst, int lane) {
+  v = warp_sum(v);
+  if (lane == 0) *dst = v;
+}
+__device__ __forceinline__ void warp_total(float2 v, double* dst, int lane) {
+  const float2 t = warp_sum_ff(v.x, v.y);
+  if (lane == 0) *dst = ff_value(t);
+}
+
+// Block-wide sum of `cnt` values per thread, deterministic order; results
+// land in out[0..cnt) (shared memory, FP64) for every thread.
+template <typename V>
+__device__ void block_sum(const V* v, int cnt, double (*scratch)[kNPairs], double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = 0; k < cnt; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) scratch[warp][k] = s;
-  }
+  for (int k = 0; k < cnt; ++k) warp_total(v[k], &scratch[warp][k], lane);
   __syncthreads();
   if (threadIdx.x < cnt) {
     double t = 0.0;
@@ -125,9 +142,9 @@ __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int6
             if (k < d) a1[k].add(v[u][k]);
         }
     }
-    double v[D];
+    decltype(a1[0].lane()) v[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) v[k] = a1[k].get();
+    for (int k = 0; k < D; ++k) v[k] = a1[k].lane();
     block_sum(v, d, sm.scratch, sm.sv);
   }
   if (threadIdx.x < d) {
@@ -136,6 +153,11 @@ __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int6
   }
   __syncthreads();
   const int npairs = d * (d + 1) / 2;
+  if (ds->given_H) {  // whitening by a given bandwidth matrix: no sample covariance
+    if (threadIdx.x < npairs) sm.sv[threadIdx.x] = 0.0;
+    __syncthreads();
+    return;
+  }
   if constexpr (D <= 4) {
     constexpr int NP = D * (D + 1) / 2;
     Acc<TIN> a2[NP];
@@ -166,14 +188,14 @@ __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int6
             }
         }
     }
-    double v[NP];
+    decltype(a2[0].lane()) v[NP];
     {
       int m = 0, mo = 0;
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) {
-          if (b < d) v[mo++] = a2[m].get();
+          if (b < d) v[mo++] = a2[m].lane();
           ++m;
         }
     }
@@ -232,10 +254,10 @@ __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int6
 // sum_b [M_b + n_b (u v^T + v u^T + v v^T)], u = m_b - c_b, v = c_b - mu
 // (c_b the centre M_b was taken about), which equals the two-pass
 // sum (x - mu)(x - mu)^T (Eq. LSCV-covariance / PLUGIN-VarianceEstimator
-// evaluated two-pass, reading R7) -- and then, on one thread in FP64:
-// Cholesky S = L L^T, log|S|, the whitening matrix M = sqrt(log2 e / 4) L^-1,
-// sigma, A and, for the PLUGIN method, psi_8^NS (Eq. PLUGIN-Psi8Estimate)
-// and g1 (Eq. PLUGIN-g1).
+// evaluated two-pass, reading R7) -- and then, in FP64 across the CTA's
+// threads: Cholesky S = L L^T, log|S|, the whitening matrix
+// M = sqrt(log2 e / 4) L^-1, sigma, A and, for the PLUGIN method, psi_8^NS
+// (Eq. PLUGIN-Psi8Estimate) and g1 (Eq. PLUGIN-g1).
 template <typename TIN, int D>
 __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   const int parts = ds->prep_parts;
@@ -289,7 +311,7 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   if (threadIdx.x < d) sMean[threadIdx.x] = tmean / (double)n;
   __syncthreads();
   double tpair = 0.0;
-  for (int r0 = 0; r0 < parts; r0 += kChunk) {
+  for (int r0 = 0; r0 < parts && !ds->given_H; r0 += kChunk) {  // a given H needs no S
     const int nr = min(kChunk, parts - r0);
     if (parts > kChunk || r0 > 0) {  // one chunk: still cached from the mean pass
       __syncthreads();
@@ -312,8 +334,8 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   if (threadIdx.x < npairs) sv[threadIdx.x] = tpair;
   if (threadIdx.x == 0) ds->prep_count = 0u;  // ready for the next run of this descriptor
   __syncthreads();
-  // ---- factorisation, FP64, shared by the CTA's threads (the operation order
-  // of every entry is that of the textbook serial loops)
+  // ---- factorisation, FP64, shared by the CTA's threads (the textbook
+  // loops; the inverse multiplies by the reciprocal of each diagonal entry)
   double(*S)[KDE_MAX_D] = reinterpret_cast<double(*)[KDE_MAX_D]>(&sm.scratch[0][0]);
   double(*L)[KDE_MAX_D] = S + KDE_MAX_D;
   double(*W)[KDE_MAX_D] = S + 2 * KDE_MAX_D;
@@ -343,7 +365,12 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     for (int a2 = 0; a2 < d; ++a2) ds->mean[a2] = sMean[a2];
   }
   for (int t = threadIdx.x; t < d * d; t += kPrepThreads) ds->cov[t] = S[t / d][t % d];
-  // Cholesky S = L L^T, column by column
+  // Cholesky S = L L^T, column by column; the pivot's reciprocal square root
+  // scales the column (FP64 divisions and square roots are long sequences on
+  // this part, and they sit on the critical path of every column)
+  double* rdiag = &W[KDE_MAX_D - 1][0] + KDE_MAX_D;  // [KDE_MAX_D] 1 / L_jj, after W
+  double* ldiag = rdiag + KDE_MAX_D;                 // [KDE_MAX_D] log of the pivots L_jj^2
+  double* piv = ldiag + KDE_MAX_D;                   // [KDE_MAX_D] the pivots
   if (threadIdx.x == 0) sm.last = finite ? 1 : 0;  // reused as the "positive definite so far" flag
   __syncthreads();
   for (int j = 0; j < d && sm.last; ++j) {
@@ -354,10 +381,14 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
       // 1e-6 of the variance (the whitened coordinate would be rounding noise),
       // or a spread below 1e-5 of the magnitude of the values.
       const double mag = ds->given_H ? 0.0 : 1e-5 * fabs(sMean[j]);
-      if (!(sj > 1e-300) || !(sj > 1e-6 * S[j][j]) || !(S[j][j] > mag * mag))
+      if (!(sj > 1e-300) || !(sj > 1e-6 * S[j][j]) || !(S[j][j] > mag * mag)) {
         sm.last = 0;
-      else
-        L[j][j] = sqrt(sj);
+      } else {
+        const double r = rsqrt(sj);
+        L[j][j] = sj * r;
+        rdiag[j] = r;
+        piv[j] = sj;
+      }
     }
     __syncthreads();
     if (!sm.last) break;
@@ -365,7 +396,7 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     if (i < d) {
       double t = S[i][j];
       for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
-      L[i][j] = t / L[j][j];
+      L[i][j] = t * rdiag[j];
     }
     __syncthreads();
   }
@@ -374,43 +405,52 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     if (threadIdx.x == 0) res.status = finite ? KDE_EDEGENERATE : KDE_EINVAL;
     return;
   }
-  // W = L^-1, one column per thread (forward substitution)
+  // W = L^-1, one column per thread (forward substitution, scaled by the
+  // reciprocals of the diagonal); the log of each pivot alongside
+  // (log|S| = sum_i log L_ii^2, summed in order below)
+  if (threadIdx.x < d) ldiag[threadIdx.x] = log(piv[threadIdx.x]);
   if (threadIdx.x < d) {
     const int j = threadIdx.x;
-    for (int i = j; i < d; ++i) {
-      if (i == j) {
-        W[i][j] = 1.0 / L[i][i];
-      } else {
-        double t = 0.0;
-        for (int k = j; k < i; ++k) t += L[i][k] * W[k][j];
-        W[i][j] = -t / L[i][i];
-      }
+    W[j][j] = rdiag[j];
+    for (int i = j + 1; i < d; ++i) {
+      double t = 0.0;
+      for (int k = j; k < i; ++k) t += L[i][k] * W[k][j];
+      W[i][j] = -t * rdiag[i];
     }
   }
   __syncthreads();
-  const double sl = sqrt(0.25 * kLog2e);
+  const double sl = kSqrtQuarterLog2e;
   for (int t = threadIdx.x; t < KDE_MAX_D * KDE_MAX_D; t += kPrepThreads) {
     const int i = t / KDE_MAX_D, j = t % KDE_MAX_D;
     const float mv = (i < d && j <= i) ? (float)(sl * W[i][j]) : 0.f;
     ds->M[t] = mv;
     sM[t] = mv;
   }
+  // the scalar chains on two threads, without FP64 pow/exp: log|S| and
+  // A = (4 pi)^(-d/2) |S|^(-1/2) = c_A prod_i 1 / L_ii; sigma and the PLUGIN
+  // pilot, psi_8^NS = 105 / (32 sqrt(pi) sigma^9) and
+  // g1 = (-2 K6(0) / (psi_8^NS n))^(1/9) = sigma c_g1, with the constants
+  // c_A (of d) and c_g1 (of n) from the host
   if (threadIdx.x == 0) {
-    double logdet = 0.0;
-    for (int i = 0; i < d; ++i) logdet += 2.0 * log(L[i][i]);
+    double logdet = 0.0, a = ds->c_A;
+    for (int i = 0; i < d; ++i) {
+      logdet += ldiag[i];
+      a *= rdiag[i];
+    }
     ds->logdet = logdet;
     res.logdet_S = logdet;
-    ds->A = pow(4.0 * kPi, -0.5 * d) * exp(-0.5 * logdet);
-    ds->sigma = sqrt(S[0][0]);
-    if (d == 1) res.sigma = ds->sigma;
+    ds->A = a;
+  } else if (threadIdx.x == 32) {
+    const double sg = sqrt(S[0][0]);
+    ds->sigma = sg;
+    if (d == 1) res.sigma = sg;
     if ((ds->methods & KDE_METHOD_PLUGIN) && d == 1) {
-      const double sg = ds->sigma;
-      const double psi8 = 105.0 / (32.0 * sqrt(kPi) * pow(sg, 9.0));
-      const double k6_0 = -15.0 / sqrt(2.0 * kPi);
-      const double g1 = pow(-2.0 * k6_0 / (psi8 * (double)n), 1.0 / 9.0);
+      const double s2 = sg * sg, s4 = s2 * s2, s8 = s4 * s4;
+      const double psi8 = 105.0 / (32.0 * kSqrtPi * (s8 * sg));
+      const double g1 = sg * ds->c_g1;
       res.psi8_ns = psi8;
       res.g1 = g1;
-      ds->psi_scale = (float)(sqrt(0.5 * kLog2e) / g1);
+      ds->psi_scale = (float)(kSqrtHalfLog2e / g1);
     }
   }
 }
@@ -575,11 +615,17 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
 cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
                          int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams p;
-  p.init = init;
+  memcpy(p.init, &init, sizeof(DsDev));
   p.n_off = n_off;
   for (int k = 0; k < 4; ++k) p.off[k] = k < n_off ? off_src[k] : 0;
-  p.n_h = n_h;
-  for (int k = 0; k < n_h && k < KDE_MAX_NH; ++k) p.h[k] = h[k];
+  p.n_h = std::min(n_h, KDE_MAX_NH);
+  p.n_h_pad = std::min(init.n_h_pad, KDE_MAX_NH);
+  p.h_dst = init.h;
+  p.nc_dst = init.nc;
+  for (int k = 0; k < p.n_h_pad; ++k) {
+    p.h[k] = k < p.n_h ? h[k] : 0.0;
+    p.nc[k] = k < p.n_h ? (float)(-1.0 / (h[k] * h[k])) : -1.0f;
+  }
   k_setup<<<1, 256, 0, st>>>(dst, off_dst, p);
   return cudaGetLastError();
 }

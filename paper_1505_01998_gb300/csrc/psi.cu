@@ -25,7 +25,7 @@ namespace gbkde {
 
 namespace {
 
-constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kSqrtHalfLog2e = 0.8493218002880191;  // sqrt(log2(e) / 2) in FP64
 constexpr double kPi = 3.14159265358979323846;
 
 template <int RD, int R, bool EDGE>
@@ -133,18 +133,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
         q = 0;
       }
     }
-    double v;
+    float vh, vl;  // the lane's total as a double-float pair
     if (KAHAN) {
-      v = (double)s - (double)c;
+      vh = s, vl = -c;
     } else {
       float run = 0.f;
 #pragma unroll
       for (int p = 0; p < R / 2; ++p) run += acc[p].x + acc[p].y;
-      v = (double)run;
+      vh = run, vl = 0.f;
     }
-    v = warp_sum(v);
+    const float2 v = warp_sum_ff(vh, vl);
     __syncthreads();
-    if (lane == 0) sRed[warp] = v;
+    if (lane == 0) sRed[warp] = ff_value(v);
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0.0;
@@ -179,8 +179,12 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
   P *= post;  // sum of p_r(y) 2^-y from the kernel's sum of q(w) 2^-w
   const double kappa = 2.0 * 0.69314718055994530942;
   const double inv_sqrt_2pi = 0.39894228040143267794;
-  // sum_{i<j} K^(r)((x_i - x_j)/g) = kappa^(r/2) P / sqrt(2 pi)
-  const double sumK = pow(kappa, 0.5 * r) * P * inv_sqrt_2pi;
+  // sum_{i<j} K^(r)((x_i - x_j)/g) = kappa^(r/2) P / sqrt(2 pi); integer
+  // powers by multiplication (FP64 pow is a long sequence on this part), the
+  // two real roots of the chain by pow
+  double kr = 1.0;
+  for (int m = 0; m < r / 2; ++m) kr *= kappa;
+  const double sumK = kr * P * inv_sqrt_2pi;
   kde_result& res = ds->res;
   if (stage == 0) {
     res.g_min = sumK;
@@ -191,7 +195,8 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
     const double k6_0 = -15.0 * inv_sqrt_2pi;  // K^(6)(0), Eq. PLUGIN-g1
     const double k4_0 = 3.0 * inv_sqrt_2pi;    // K^(4)(0), Eq. PLUGIN-g2
     const double g1 = res.g1;
-    const double psi6 = (2.0 * sumK + n * k6_0) / (n * n * pow(g1, 7.0));
+    const double g1s = g1 * g1, g1q = g1s * g1s;
+    const double psi6 = (2.0 * sumK + n * k6_0) / (n * n * (g1q * g1s * g1));
     res.psi6 = psi6;
     if (!(psi6 < 0.0)) {
       res.status = KDE_EDEGENERATE;
@@ -199,11 +204,12 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
     }
     const double g2 = pow(-2.0 * k4_0 / (psi6 * n), 1.0 / 7.0);
     res.g2 = g2;
-    ds->psi_scale = (float)(sqrt(0.5 * kLog2e) / g2);
+    ds->psi_scale = (float)(kSqrtHalfLog2e / g2);
   } else {
     const double k4_0 = 3.0 * inv_sqrt_2pi;
     const double g2 = res.g2;
-    const double psi4 = (2.0 * sumK + n * k4_0) / (n * n * pow(g2, 5.0));
+    const double g2s = g2 * g2;
+    const double psi4 = (2.0 * sumK + n * k4_0) / (n * n * (g2s * g2s * g2));
     res.psi4 = psi4;
     if (!(psi4 > 0.0)) {
       res.status = KDE_EDEGENERATE;

@@ -656,7 +656,7 @@ int kde_serve_create(const kde_serve_config* cfg, kde_server** out) {
   }
   // every kernel variant's shared-memory attribute up front
   for (int d : {1, 2, 3, 4, 8, 12, 16})
-    for (int B : {8, 16})
+    for (int B : {2, 8, 16})
       for (int R : {1, 4})
         for (int k = 0; k < 2; ++k)
           if (d <= 4 || R == 1) {

@@ -179,6 +179,16 @@ def test_lscv_dims_sizes_grids(kde, d, n, n_h):
     _lscv_check(kde, x, h)
 
 
+@pytest.mark.parametrize("d", [1, 3, 6, 16])
+@pytest.mark.parametrize("n,n_h", [(1100, 1), (2000, 2)])
+def test_lscv_one_and_two_point_grids(kde, d, n, n_h):
+    """Grids of one or two points take 2 bandwidths per thread (one g(H) of
+    LSCV_H is such a grid); d = 6 and 16 also prefetch the next tile's rows."""
+    x = datagen.correlated_mixture(n, d, seed=500 + d + n)
+    h = oracle.grid_default(n, d, 8)[3:3 + n_h]
+    _lscv_check(kde, x, h)
+
+
 @pytest.mark.parametrize("d", [5, 7, 8, 9, 12, 13, 16])
 @pytest.mark.parametrize("n,n_h", [(450, 32), (1300, 100)])
 def test_lscv_high_dimensions(kde, d, n, n_h):
@@ -204,7 +214,8 @@ def test_lscv_H_high_dimensions(kde, d):
 
 
 @pytest.mark.parametrize("opts", [dict(precision=1), dict(tile=128), dict(tile=32, bw_per_thread=16),
-                                  dict(bw_per_thread=8, tiles_per_item=3), dict(ctas_per_sm=1)])
+                                  dict(bw_per_thread=8, tiles_per_item=3), dict(ctas_per_sm=1),
+                                  dict(bw_per_thread=2), dict(tile=32, bw_per_thread=2, precision=1)])
 def test_lscv_option_paths(kde, opts):
     x = datagen.correlated_mixture(1800, 2, seed=99)
     h = oracle.grid_default(1800, 2, 96)
