@@ -105,11 +105,11 @@ def profiled_lscv_traffic():
     src = os.path.join(ROOT, "paper_1505_01998_gb300", "csrc", "lscv.cu")
     try:
         text = open(prof).read()
-        want = re.search(r"sha256 prefix `([0-9a-f]{16})`", text).group(1)
+        want = re.search(r"sha256 prefix\s+`([0-9a-f]{16})`", text).group(1)
         have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if want != have or N != 65536:
             return None
-        return int(re.search(r"traffic = ([0-9,]+) bytes", text).group(1).replace(",", ""))
+        return int(re.search(r"traffic\s+=\s+([0-9,]+)\s+bytes", text).group(1).replace(",", ""))
     except Exception:
         return None
 

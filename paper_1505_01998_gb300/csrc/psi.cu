@@ -38,13 +38,16 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
 #pragma unroll
   for (int m = 0; m < M - 1; ++m) cc[m] = make_float2(cf.c[m], cf.c[m]);
   const float2 sh2 = make_float2(cf.shift, cf.shift);
+  // sF holds each column sample as the pair (-v, -v): two columns per 16 bytes
 #pragma unroll 1
   for (int jj = j_lo; jj < j_hi; jj += 4) {
-    const float4 v = *reinterpret_cast<const float4*>(sF + jj);
-    const float vv[4] = {v.x, v.y, v.z, v.w};
+    const float4 v01 = *reinterpret_cast<const float4*>(sF + 2 * jj);
+    const float4 v23 = *reinterpret_cast<const float4*>(sF + 2 * jj + 4);
+    const float2 nfs[4] = {make_float2(v01.x, v01.y), make_float2(v01.z, v01.w),
+                           make_float2(v23.x, v23.y), make_float2(v23.z, v23.w)};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const float2 nf = make_float2(-vv[c], -vv[c]);
+      const float2 nf = nfs[c];
 #pragma unroll
       for (int p = 0; p < R / 2; ++p) {
         const float2 dl = __fadd2_rn(z[p], nf);
@@ -67,7 +70,7 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
 template <int RD, int R, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
   constexpr int T = 32 * R;
-  __shared__ __align__(16) float sF[T];
+  __shared__ __align__(16) float sF[2 * T];  // (-v, -v) per column
   __shared__ double sRed[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int cols = T / kWarps;
@@ -99,7 +102,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
     for (int64_t t = t0; t < t1; ++t) {
       if (l != l_loaded) {
         __syncthreads();
-        for (int jj = threadIdx.x; jj < T; jj += kThreads) sF[jj] = X[l * T + jj] * sc;
+        for (int jj = threadIdx.x; jj < T; jj += kThreads) {
+          const float v = X[l * T + jj] * sc;
+          reinterpret_cast<float2*>(sF)[jj] = make_float2(-v, -v);
+        }
         __syncthreads();
         l_loaded = l;
       }
