@@ -526,6 +526,15 @@ def run_configs(args):
     P = n * (n - 1) // 2
     evals = P * (64 + 2)
     sel_ms, _ = median_ms(lambda: (gbkde.kde_lscv(xd, grid, None, ws, stream), gbkde.kde_plugin(xd, None, ws, stream)))
+    # both selections as one replayed batch plan (one prologue, one graph launch)
+    req, req_keep = gbkde.make_request(xd, gbkde.KDE_METHOD_LSCV | gbkde.KDE_METHOD_PLUGIN, grid)
+    plan = gbkde.BatchPlan([req], keepalive=[req_keep])
+    ws_plan = gbkde.workspace(plan.ws_bytes)
+    plan_ms, _ = median_ms(lambda: plan.run(ws_plan, stream))
+    plan_res = plan.run(ws_plan, stream)[0]
+    sep_l = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
+    sep_p = gbkde.kde_plugin(xd, None, ws, stream)
+    plan_same = plan_res["h"] == sep_l["h"] and plan_res["h_plugin"] == sep_p["h"]
     _, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True)
     xh = torch.from_numpy(x).pin_memory().numpy()
     e2e_ms, _ = median_ms(lambda: (gbkde.kde_lscv_host(xh, grid, None, ws, stream),
@@ -540,6 +549,7 @@ def run_configs(args):
     o1_s = time.perf_counter() - t0
     out.append({"config": "n=1024 FP64 mixture, 64-point LSCV on [0.01, 2] + plug-in", "evals": evals,
                 "selection_ms": sel_ms, "evals_per_s": evals / (sel_ms * 1e-3),
+                "selection_plan_ms": plan_ms, "plan_results_equal": plan_same,
                 "lscv_kernel_ms": kern_ms, "lscv_kernel_evals_per_s": P * 64 / (kern_ms * 1e-3),
                 "lscv_kernel_frac": P * 64 / (kern_ms * 1e-3) / peak, "e2e_ms": e2e_ms,
                 "oracle_full_s": o_s, "oracle_evals_per_s": evals / o_s, "oracle_cores": cores,
