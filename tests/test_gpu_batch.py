@@ -73,6 +73,38 @@ def test_batch_equals_single_calls_bitwise(kde):
             assert r["h"] == r["h_plugin"]
 
 
+def test_batch_wide_samples_and_one_point_grids(kde):
+    """Datasets of d = 1, 4, 6, 12, 16 with grids of 1, 2, 8 and 150 points in
+    one plan: the one- and two-point grids of wide samples walk their items
+    warp by warp, the others in blocks, in the same launches.  Bitwise equal
+    to single calls, and within tolerance of the oracle."""
+    rng = np.random.default_rng(77)
+    reqs, keep, meta = [], [], []
+    for k, (d, n_h) in enumerate([(16, 1), (6, 2), (1, 150), (12, 1), (4, 2), (16, 8), (6, 1), (1, 1)]):
+        n = int(rng.integers(300, 2600))
+        x = datagen.correlated_mixture(n, d, seed=700 + k)
+        h = oracle.grid_default(n, d, 8)[2:2 + n_h] if n_h <= 8 else oracle.grid_default(n, d, n_h)
+        grid, hk = kde.make_grid(h=h)
+        xd = dev(x)
+        req, rk = kde.make_request(xd, LSCV, grid)
+        reqs.append(req)
+        keep += [hk, rk, xd]
+        meta.append((x, xd, grid, h))
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    ws = kde.workspace(plan.ws_bytes)
+    out = plan.run(ws)
+    for k, (x, xd, grid, h) in enumerate(meta):
+        assert out[k]["status"] == 0, (k, out[k])
+        single, g1, _ = kde.kde_lscv(xd, grid)
+        gb = plan.g(ws, k, len(h))
+        assert np.array_equal(gb, g1), k
+        assert out[k]["argmin"] == single["argmin"]
+        x64 = np.asarray(x, dtype=np.float32).astype(np.float64)
+        ref = oracle.lscv_h(x64, h)
+        d, n = x64.shape
+        assert g_err(gb, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, lscv_A(x64)).max() < TOL, k
+
+
 def test_batch_graph_replay_and_in_place_update(kde):
     import torch
     reqs, keep, meta = _mixed_requests(kde, count=10, seed=3)

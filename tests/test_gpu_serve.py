@@ -8,6 +8,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_1505_01998_gb300 import datagen
 from tests._helpers import built_lib
 
@@ -76,6 +77,33 @@ def test_results_in_the_mix_equal_alone_bitwise_and_single_calls_within_toleranc
             for k in ("psi6", "g2", "psi4", "h"):
                 assert abs(r[k] - s[k]) <= 1e-5 * abs(s[k]), (k, r[k], s[k])
     alone.close()
+
+
+def test_wide_samples_on_one_and_two_point_grids_in_the_mix(kde):
+    """Requests of d = 6 and 16 on one- and two-point grids (warp items) served
+    beside d = 1 requests on the default grid, with steps small enough that
+    every request spans several: each result equals the single call's."""
+    rng = np.random.default_rng(31)
+    mix = []
+    for k in range(12):
+        d = [16, 6, 1][k % 3]
+        n = int(rng.integers(900, 5000))
+        x = datagen.correlated_mixture(n, d, seed=900 + k)
+        if d == 1:
+            grid, hk = kde.make_grid(n_h=128)
+        else:
+            h = oracle.grid_default(n, d, 8)[3:3 + 1 + k % 2]
+            grid, hk = kde.make_grid(h=h)
+        mix.append((x, grid, hk))
+    srv = kde.Server(arena(1 << 30), max_slots=16, quantum_evals=2e8)
+    tickets = [srv.submit(x, LSCV, grid) for x, grid, _ in mix]
+    for t, (x, grid, _) in zip(tickets, mix):
+        rc, r = srv.wait(t, 60000)
+        assert rc == 0, (rc, r)
+        s = kde.kde_lscv(dev(x), grid)[0]
+        assert r["argmin"] == s["argmin"] and r["h"] == s["h"]
+        assert abs(r["g_min"] - s["g_min"]) <= 1e-5 * abs(s["g_min"])
+    srv.close()
 
 
 @pytest.mark.parametrize("quantum", [3e8, 2e9])
