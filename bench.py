@@ -784,6 +784,27 @@ def run_gpu(args, world, rank, local):
     ms_per_step = total_ms / K
     value = EVALS_STEP * world / (ms_per_step * 1e-3)
 
+    # ---- the same selection on the 256-point log grid over the closed interval
+    # [h0/4, 4 h0] (not octave-shaped: the direct kernel), LSCV kernel timed alone
+    h0 = (4.0 / (3.0 * N)) ** 0.2  # normal-scale h0 for d = 1, in units of sigma
+    grid_c, _keep_c = gbkde.make_grid(n_h=N_H, h_min=h0 / 4.0, h_max=4.0 * h0)
+    for _ in range(2):
+        gbkde.kde_lscv_async(xd, grid_c, opts, ws_l, stream)
+    torch.cuda.synchronize()
+    closed_ms = []
+    for k in range(max(3, K // 2)):
+        flush.zero_()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        gbkde.kde_set_kernel_events(c0, c1)
+        gbkde.kde_lscv_async(xd, grid_c, opts, ws_l, stream)
+        gbkde.kde_set_kernel_events()
+        torch.cuda.synchronize()
+        closed_ms.append(c0.elapsed_time(c1))
+    closed_kernel_ms = statistics.median(closed_ms)
+
     # ---- end to end: pinned host samples in, results out, through the public API
     x_pin = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
     xh = x_pin.numpy()
@@ -823,7 +844,14 @@ def run_gpu(args, world, rank, local):
                                "the timed region); unit counts measured by kde_probe_alu"),
                 "peak_at_max_clock": peak_max, "frac_at_max_clock": achieved / peak_max,
                 "psi_kernel_ms": psi_ms,
-                "psi_geval_s": pairs(N) / (psi_ms * 1e-3) / 1e9}
+                "psi_geval_s": pairs(N) / (psi_ms * 1e-3) / 1e9,
+                "closed_grid": {
+                    "grid": "256-point log grid over the closed [h0/4, 4 h0] (direct kernel: one ex2 per evaluation)",
+                    "kernel_ms": closed_kernel_ms,
+                    "geval_s": EVALS_LSCV / (closed_kernel_ms * 1e-3) / 1e9,
+                    "peak": lscv_per_clk(probe, 1, False) * probe["sm_count"] * sm_mhz * 1e6 / 1e9,
+                    "frac": EVALS_LSCV / (closed_kernel_ms * 1e-3) / 1e9
+                    / (lscv_per_clk(probe, 1, False) * probe["sm_count"] * sm_mhz * 1e6 / 1e9)}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
