@@ -122,7 +122,7 @@ template <typename TIN, int D>
 __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int64_t lo, int64_t hi) {
   const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
   const int64_t n = ds->n;
-  const int d = ds->d;
+  const int d = D <= 4 ? D : ds->d;  // dk = d for d <= 4: a compile-time bound there
   const int64_t cnt = hi - lo;
   {
     Acc<TIN> a1[D];
@@ -263,7 +263,7 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   const int parts = ds->prep_parts;
   if (b >= parts) return;
   const int64_t n = ds->n;
-  const int d = ds->d;
+  const int d = D <= 4 ? D : ds->d;  // dk = d for d <= 4: a compile-time bound there
   int64_t lo, hi;
   prep_range(n, parts, b, lo, hi);
   prep_moments<TIN, D>(ds, sm, lo, hi);
@@ -470,7 +470,7 @@ __device__ __forceinline__ void prep_whiten(const DsDev* ds, WhitenSmem& sm, int
   if (b >= parts || ds->res.status != KDE_OK) return;
   const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
   const int64_t n = ds->n, n_pad = ds->n_pad;
-  const int d = ds->d, dk = ds->dk;
+  const int d = D <= 4 ? D : ds->d, dk = D <= 4 ? D : ds->dk;  // compile-time for d <= 4
   for (int k = threadIdx.x; k < KDE_MAX_D * KDE_MAX_D; k += kPrepThreads) sm.sM[k] = ds->M[k];
   if (threadIdx.x < KDE_MAX_D) {
     sm.sMean[threadIdx.x] = threadIdx.x < d ? ds->mean[threadIdx.x] : 0.0;
