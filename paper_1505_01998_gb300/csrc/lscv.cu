@@ -200,6 +200,55 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
                                                  const float (&y)[R][D], const float2 (&nca)[3],
                                                  float2 (&acc)[9], int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
+  if constexpr (D > 4) {
+    // wide samples, one row per lane (sF holds -v): two columns per
+    // iteration, each squared distance in packed FP32x2 over coordinate
+    // pairs (two chains joined by one add), as in the direct kernel
+    static_assert(R == 1 && DP % 4 == 0, "wide path: one row per lane");
+    float2 y2[DP / 2];
+#pragma unroll
+    for (int k = 0; k < DP / 2; ++k) y2[k] = make_float2(y[0][2 * k], y[0][2 * k + 1]);
+#pragma unroll 1
+    for (int jj = j_lo; jj < j_hi; jj += 2) {
+      float qv[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < DP / 4; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(sF + (jj + c) * DP + 4 * u);
+          const float2 d0 = __fadd2_rn(y2[2 * u], make_float2(v.x, v.y));
+          const float2 d1 = __fadd2_rn(y2[2 * u + 1], make_float2(v.z, v.w));
+          s2 = __ffma2_rn(d0, d0, s2);
+          s2 = __ffma2_rn(d1, d1, s2);
+        }
+        qv[c] = __fadd_rn(s2.x, s2.y);
+        if (EDGE) {
+          const int64_t j = jg0 + jj + c;
+          if (!(i0 < j && j < n)) qv[c] = __int_as_float(0x7f800000);  // +inf -> e = 0
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const float2 q2 = make_float2(qv[c], qv[c]);
+        const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
+        const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
+        const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
+        const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
+        const float2 e6 = __fmul2_rn(e7, e7), e3 = __fmul2_rn(e4, e4), e0 = __fmul2_rn(e1, e1);
+        acc[7] = __fadd2_rn(acc[7], e7);
+        acc[6] = __fadd2_rn(acc[6], e6);
+        acc[5] = __ffma2_rn(e6, e6, acc[5]);
+        acc[4] = __fadd2_rn(acc[4], e4);
+        acc[3] = __fadd2_rn(acc[3], e3);
+        acc[2] = __ffma2_rn(e3, e3, acc[2]);
+        acc[1] = __fadd2_rn(acc[1], e1);
+        acc[0] = __fadd2_rn(acc[0], e0);
+        acc[8] = __ffma2_rn(e0, e0, acc[8]);
+      }
+    }
+    return;
+  }
   constexpr int CPI = DP <= 4 ? 4 / DP : 1;  // columns per iteration
   constexpr int NV = CPI * DP / 4;           // 16-byte shared-memory loads per iteration
 #pragma unroll 1
@@ -420,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
           const float v = (k < D) ? Y[(int64_t)k * n_pad + l * T + jj] : 0.f;
           if constexpr (kPackedQ<D, R, OCT>)
             reinterpret_cast<float2*>(sF)[idx] = make_float2(-v, -v);
-          else if constexpr (D > 4 && !OCT)
-            sF[idx] = -v;  // the wide path adds -v
+          else if constexpr (D > 4)
+            sF[idx] = -v;  // the wide paths add -v
           else
             sF[idx] = v;
         }
