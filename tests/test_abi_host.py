@@ -1,5 +1,6 @@
 """C ABI and host logic of libgbkde (CPU only: no kernel is launched)."""
 import ctypes
+import math
 import os
 import re
 
@@ -113,6 +114,47 @@ def test_workspace_size_monotone_and_bad_args(kde):
         kde.kde_workspace_size(100, 17, 64)
     with pytest.raises(kde.KdeError):
         kde.kde_workspace_size(100, 1, 64, kde.make_opts(tile=48))
+
+
+def test_bandwidths_per_thread_options(kde):
+    """2, 8 and 16 bandwidths per thread are accepted; anything else is an
+    argument error before any launch."""
+    for b in (0, 2, 8, 16):
+        assert kde.kde_workspace_size(3000, 4, 64, kde.make_opts(bw_per_thread=b)) > 0
+    for b in (1, 4, 12, 32):
+        with pytest.raises(kde.KdeError) as e:
+            kde.kde_workspace_size(3000, 4, 64, kde.make_opts(bw_per_thread=b))
+        assert e.value.status == kde.KDE_EINVAL
+
+
+def test_double_float_butterfly_replayed_on_the_host():
+    """The item totals of the pair kernels are warp sums of FP32 (hi, lo) pairs
+    by a butterfly with Knuth's TwoSum at each step and Dekker's Fast2Sum to
+    renormalise (warp_sum_ff).  Replayed here in numpy float32 with the same
+    operation order: every lane ends with the same pair (the steps are
+    symmetric), and the pair carries the exact sum to about 44 bits."""
+    f = np.float32
+    rng = np.random.default_rng(5)
+    for trial in range(200):
+        scale = 10.0 ** rng.uniform(-6, 9)
+        hi = (rng.lognormal(0, 2, 32) * scale).astype(f)
+        lo = (hi * rng.uniform(-1, 1, 32) * 2.0 ** -25).astype(f)  # Kahan tails: below an ulp of hi
+        h, l = hi.copy(), lo.copy()
+        o = 16
+        while o:
+            idx = np.arange(32) ^ o
+            h2, l2 = h[idx], l[idx]
+            s = f(h + h2)
+            bb = f(s - h)
+            e = f(f(h - f(s - bb)) + f(h2 - bb))
+            t = f(f(l + l2) + e)
+            h = f(s + t)
+            l = f(t - f(h - s))
+            o >>= 1
+        assert np.all(h == h[0]) and np.all(l == l[0])
+        exact = math.fsum([float(v) for v in hi] + [float(v) for v in lo])
+        got = float(h[0]) + float(l[0])
+        assert abs(got - exact) <= 2.0 ** -43 * abs(exact), (trial, got, exact)
 
 
 def test_entry_points_reject_bad_arguments_before_any_launch(kde):
