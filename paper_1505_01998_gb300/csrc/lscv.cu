@@ -41,6 +41,45 @@ struct DPad {
 template <int D, int R, bool OCT = false>
 constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT);
 
+// Wide samples (d > 4, one row per lane; the column tile holds -v): the
+// squared distance to column `col` in packed FP32x2 over coordinate pairs,
+// two independent chains joined by one add.
+template <int DP>
+__device__ __forceinline__ float wide_q(const float* __restrict__ sF, int col, const float2 (&y2)[DP / 2]) {
+  float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int u = 0; u < DP / 4; ++u) {
+    const float4 v = *reinterpret_cast<const float4*>(sF + col * DP + 4 * u);
+    const float2 d0 = __fadd2_rn(y2[2 * u], make_float2(v.x, v.y));
+    const float2 d1 = __fadd2_rn(y2[2 * u + 1], make_float2(v.z, v.w));
+    s2 = __ffma2_rn(d0, d0, s2);
+    s2 = __ffma2_rn(d1, d1, s2);
+  }
+  return __fadd_rn(s2.x, s2.y);
+}
+
+// The octave grid's 16 terms of one pair (two residues x 8 octaves) from its
+// squared distance qv: three chains per residue, each one ex2 and two
+// squarings down (7 -> 6 -> 5, 4 -> 3 -> 2, 1 -> 0 -> one octave below 0);
+// the last square of a chain feeds only its sum (FFMA2).
+__device__ __forceinline__ void octave_terms(float qv, const float2 (&nca)[3], float2 (&acc)[9]) {
+  const float2 q2 = make_float2(qv, qv);
+  const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
+  const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
+  const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
+  const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
+  const float2 e6 = __fmul2_rn(e7, e7), e3 = __fmul2_rn(e4, e4), e0 = __fmul2_rn(e1, e1);
+  acc[7] = __fadd2_rn(acc[7], e7);
+  acc[6] = __fadd2_rn(acc[6], e6);
+  acc[5] = __ffma2_rn(e6, e6, acc[5]);
+  acc[4] = __fadd2_rn(acc[4], e4);
+  acc[3] = __fadd2_rn(acc[3], e3);
+  acc[2] = __ffma2_rn(e3, e3, acc[2]);
+  acc[1] = __fadd2_rn(acc[1], e1);
+  acc[0] = __fadd2_rn(acc[0], e0);
+  acc[8] = __ffma2_rn(e0, e0, acc[8]);
+}
+
 // Columns [j_lo, j_hi) of one tile for this lane's R rows and B bandwidths.
 // Bandwidths are processed in pairs with packed FP32x2 arithmetic.
 template <int D, int B, int R, bool EDGE>
@@ -105,23 +144,13 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
     static_assert(R == 1 && DP % 4 == 0, "wide path: one row per lane");
     float2 y2[DP / 2];
 #pragma unroll
-    for (int k = 0; k < DP / 2; ++k)
-      y2[k] = make_float2(2 * k < D ? y[0][2 * k] : 0.f, 2 * k + 1 < D ? y[0][2 * k + 1] : 0.f);
+    for (int k = 0; k < DP / 2; ++k) y2[k] = make_float2(y[0][2 * k], y[0][2 * k + 1]);
 #pragma unroll 1
     for (int jj = j_lo; jj < j_hi; jj += 2) {
       float2 q2[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < DP / 4; ++u) {
-          const float4 v = *reinterpret_cast<const float4*>(sF + (jj + c) * DP + 4 * u);
-          const float2 d0 = __fadd2_rn(y2[2 * u], make_float2(v.x, v.y));
-          const float2 d1 = __fadd2_rn(y2[2 * u + 1], make_float2(v.z, v.w));
-          acc = __ffma2_rn(d0, d0, acc);
-          acc = __ffma2_rn(d1, d1, acc);
-        }
-        float qv = __fadd_rn(acc.x, acc.y);
+        float qv = wide_q<DP>(sF, jj + c, y2);
         if (EDGE) {
           const int64_t j = jg0 + jj + c;
           if (!(i0 < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
@@ -213,39 +242,14 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
       float qv[2];
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < DP / 4; ++u) {
-          const float4 v = *reinterpret_cast<const float4*>(sF + (jj + c) * DP + 4 * u);
-          const float2 d0 = __fadd2_rn(y2[2 * u], make_float2(v.x, v.y));
-          const float2 d1 = __fadd2_rn(y2[2 * u + 1], make_float2(v.z, v.w));
-          s2 = __ffma2_rn(d0, d0, s2);
-          s2 = __ffma2_rn(d1, d1, s2);
-        }
-        qv[c] = __fadd_rn(s2.x, s2.y);
+        qv[c] = wide_q<DP>(sF, jj + c, y2);
         if (EDGE) {
           const int64_t j = jg0 + jj + c;
           if (!(i0 < j && j < n)) qv[c] = __int_as_float(0x7f800000);  // +inf -> e = 0
         }
       }
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const float2 q2 = make_float2(qv[c], qv[c]);
-        const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
-        const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
-        const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
-        const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
-        const float2 e6 = __fmul2_rn(e7, e7), e3 = __fmul2_rn(e4, e4), e0 = __fmul2_rn(e1, e1);
-        acc[7] = __fadd2_rn(acc[7], e7);
-        acc[6] = __fadd2_rn(acc[6], e6);
-        acc[5] = __ffma2_rn(e6, e6, acc[5]);
-        acc[4] = __fadd2_rn(acc[4], e4);
-        acc[3] = __fadd2_rn(acc[3], e3);
-        acc[2] = __ffma2_rn(e3, e3, acc[2]);
-        acc[1] = __fadd2_rn(acc[1], e1);
-        acc[0] = __fadd2_rn(acc[0], e0);
-        acc[8] = __ffma2_rn(e0, e0, acc[8]);
-      }
+      for (int c = 0; c < 2; ++c) octave_terms(qv[c], nca, acc);
     }
     return;
   }
@@ -276,23 +280,7 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
           const int64_t i = i0 + 32 * r, j = jg0 + jj + c;
           if (!(i < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
         }
-        // three chains per residue, each one ex2 and two squarings down: 7 -> 6 -> 5, 4 -> 3 -> 2,
-        // 1 -> 0 -> (one octave below 0); the last square of a chain feeds only its sum (FFMA2)
-        const float2 q2 = make_float2(qv, qv);
-        const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
-        const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
-        const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
-        const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
-        const float2 e6 = __fmul2_rn(e7, e7), e3 = __fmul2_rn(e4, e4), e0 = __fmul2_rn(e1, e1);
-        acc[7] = __fadd2_rn(acc[7], e7);
-        acc[6] = __fadd2_rn(acc[6], e6);
-        acc[5] = __ffma2_rn(e6, e6, acc[5]);
-        acc[4] = __fadd2_rn(acc[4], e4);
-        acc[3] = __fadd2_rn(acc[3], e3);
-        acc[2] = __ffma2_rn(e3, e3, acc[2]);
-        acc[1] = __fadd2_rn(acc[1], e1);
-        acc[0] = __fadd2_rn(acc[0], e0);
-        acc[8] = __ffma2_rn(e0, e0, acc[8]);
+        octave_terms(qv, nca, acc);
       }
     }
   }
