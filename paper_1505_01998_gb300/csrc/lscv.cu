@@ -17,9 +17,16 @@
 // column slice of the tile when a group has fewer than 8 chunks); each lane
 // holds R row samples in registers and walks the column samples staged in
 // shared memory (broadcast reads).  Per-thread sums: FP32 runs over a tile,
-// folded into Kahan-compensated FP32 accumulators; per-item totals in FP64.
-// Every item writes its own partial row, and rows are added in a fixed order,
-// so results do not depend on the grid size or on which CTA ran an item.
+// folded into Kahan-compensated FP32 accumulators; a warp's item total is a
+// double-float butterfly in FP32, written as FP64.  Every item writes its
+// own partial row, and rows are added in a fixed order, so results do not
+// depend on the grid size or on which CTA ran an item.
+//
+// Variants: on a grid with n_h/8 points per octave of 1/h^2 (the default
+// grid) the octave kernel takes 3/8 ex2 per evaluation and squares the rest
+// down the octaves; the direct kernel (any grid) takes one ex2 per
+// evaluation; grids of one or two points with wide samples (d > 4) walk
+// their items one warp per item (k_lscv_warp).
 #include "internal.cuh"
 
 namespace gbkde {
