@@ -357,6 +357,21 @@ def test_lscv_exp_sums_relation():
         assert np.allclose(st, A * (skk - 2 ** (1 + d / 2) * sk), rtol=1e-12)
 
 
+@pytest.mark.parametrize("d,n_h", [(1, 64), (2, 128), (3, 16)])
+def test_octave_grid_sum_identity(d, n_h):
+    """On the default grid (n_h/8 points per octave of 1/h^2: c_(k-P) = 2 c_k,
+    reading R6), the K-term sum at bandwidth k is the K*K-term sum at k - P:
+    exp(-S(v)/(2 h_k^2)) = exp(-S(v)/(4 h_(k-P)^2)) for every pair.  This is the
+    identity the octave kernel uses (S2(k) = S1(k - P)); here it is checked on
+    the oracle's separately evaluated sums."""
+    n = 300
+    x = datagen.correlated_mixture(n, d, seed=61 + d).astype(np.float64)
+    h = oracle.grid_default(n, d, n_h)
+    P = n_h // 8
+    ref = oracle.lscv_h(x, h)
+    assert np.allclose(ref["s_k"][P:], ref["s_kk"][:-P], rtol=1e-11, atol=0)
+
+
 def test_lscv_block_decomposition_adds_up():
     x = datagen.correlated_mixture(90, 2, seed=17).astype(np.float64)
     h = np.array([0.25, 0.9])
