@@ -428,6 +428,16 @@ def run_paper(args):
             ts.append(time.perf_counter() - t0)
         return 1e3 * statistics.median(ts)
 
+    def plan_timed(xd, methods, grid, reps):
+        """The same selection as a batch plan built once and replayed (one
+        captured graph per run), samples resident."""
+        req, keep = gbkde.make_request(xd, methods, grid)
+        plan = gbkde.BatchPlan([req], keepalive=[keep])
+        wsp = gbkde.workspace(plan.ws_bytes)
+        ms = timed(lambda: plan.run(wsp, stream), reps)
+        assert plan.run(wsp, stream)[0]["status"] == 0
+        return ms
+
     # PLUGIN, n = 32768, d = 1 (paper: 87.9 ms)
     x = datagen.mixture_1d(32768, seed=7).astype(np.float32)
     xd = torch.from_numpy(x).cuda()
@@ -435,7 +445,9 @@ def run_paper(args):
     xh = torch.from_numpy(x).pin_memory().numpy()
     e2e = timed(lambda: gbkde.kde_plugin_host(xh, None, ws, stream), args.steps)
     res = timed(lambda: gbkde.kde_plugin(xd, None, ws, stream), args.steps)
+    plan_ms = plan_timed(xd, gbkde.KDE_METHOD_PLUGIN, None, args.steps)
     out.append({"instance": "PLUGIN n=32768 d=1", "e2e_ms": e2e, "resident_ms": res,
+                "resident_plan_ms": plan_ms,
                 "paper_gpu_ms": 87.9, "paper_sse_ms": 1442.3, "paper_seq_ms": 47435.3,
                 "speedup_vs_paper_gpu_e2e": 87.9 / e2e})
     # LSCV_h, n = 1024, d = 16, 150 bandwidths (paper: 14.7 ms)
@@ -446,7 +458,9 @@ def run_paper(args):
     xh = torch.from_numpy(x).pin_memory().numpy()
     e2e = timed(lambda: gbkde.kde_lscv_host(xh, grid, None, ws, stream), args.steps)
     res = timed(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), args.steps)
+    plan_ms = plan_timed(xd, gbkde.KDE_METHOD_LSCV, grid, args.steps)
     out.append({"instance": "LSCV_h n=1024 d=16 n_h=150", "e2e_ms": e2e, "resident_ms": res,
+                "resident_plan_ms": plan_ms,
                 "paper_gpu_ms": 14.7, "paper_sse_ms": 344.1, "paper_seq_ms": 8283.6,
                 "speedup_vs_paper_gpu_e2e": 14.7 / e2e})
     # LSCV_H, one g(H), n = 16384, d = 16 (paper: 184.2 ms)
