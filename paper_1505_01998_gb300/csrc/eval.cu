@@ -496,14 +496,20 @@ int eval_layout(int64_t n, int d, int64_t m, int sms, EvalLayout* L) {
 template <typename TIN, int D>
 cudaError_t eval_launch(cudaStream_t st, const DsDev* ds, const float* yq, const EvalLayout& L,
                         const double* cent, double* part) {
-  static int per_sm = 0;
-  if (!per_sm) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eval<TIN, D>, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, per_sm);
-  }
+  struct Occupancy {
+    cudaError_t e;
+    int per_sm;
+  };
+  // looked up once per instance (thread-safe initialisation of a local static)
+  static const Occupancy occ = [] {
+    Occupancy o{cudaSuccess, 0};
+    o.e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, k_eval<TIN, D>, kThreads, 0);
+    o.per_sm = std::max(1, o.per_sm);
+    return o;
+  }();
+  if (occ.e != cudaSuccess) return occ.e;
   const int64_t items = L.q_tiles * L.n_chunks;
-  const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * per_sm);
+  const int grid = (int)std::min<int64_t>(items, (int64_t)std::max(1, device_sms()) * occ.per_sm);
   k_eval<TIN, D><<<grid, kThreads, 0, st>>>(ds, yq, L.m_pad, L.q_tiles, L.chunk, L.n_chunks, cent, part);
   return cudaGetLastError();
 }
@@ -646,13 +652,13 @@ int kde_aqp(const void* x_dev, int dtype, int64_t n, double h, const double* lo_
   cudaError_t e = cudaMemcpyAsync(rng, r2.data(), sizeof(float) * 2 * m, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = mark_event(0, st);
   const size_t smem = aqp_smem_bytes(chunk);
-  static bool attr_set = false;
-  if (e == cudaSuccess && !attr_set) {
+  static const cudaError_t attr = [] {  // once, thread-safely
     const int mx = (int)aqp_smem_bytes(kAqpChunk);
-    e = cudaFuncSetAttribute(k_aqp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_aqp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    attr_set = e == cudaSuccess;
-  }
+    cudaError_t a = cudaFuncSetAttribute(k_aqp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (a == cudaSuccess) a = cudaFuncSetAttribute(k_aqp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return a;
+  }();
+  if (e == cudaSuccess) e = attr;
   if (e == cudaSuccess) {
     if (dtype == KDE_F64)
       k_aqp<double><<<(int)chunks, kThreads, smem, st>>>(static_cast<const double*>(x_dev), n, (float)h, rng, m, chunk, part);

@@ -737,13 +737,11 @@ cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
     return cudaGetLastError();
   } else {
     const size_t smem = lscv_smem_bytes(D, B, R, KAHAN, OCT);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_lscv<D, B, R, KAHAN, OCT>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
+    // set once per instance (a function-local static is initialised once,
+    // thread-safely: the server's worker and callers may launch concurrently)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_lscv<D, B, R, KAHAN, OCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
     k_lscv<D, B, R, KAHAN, OCT><<<grid, kThreads, smem, st>>>(ph);
     return cudaGetLastError();

@@ -641,15 +641,14 @@ cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cuda
 }
 
 cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static const cudaError_t attr = [] {  // once, thread-safely
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_probe<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_probe<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_probe<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
-    if ((e = cudaFuncSetAttribute(k_probe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem))) return e;
-    attr = true;
-  }
+    return cudaFuncSetAttribute(k_probe<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kProbeSmem);
+  }();
+  if (attr != cudaSuccess) return attr;
   switch (mode) {
     case 0: k_probe<0><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
     case 1: k_probe<1><<<grid, kProbeThreads, kProbeSmem, st>>>(out, iters, 0.5f); break;
