@@ -153,22 +153,32 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        for line in open(self.path):
-            p = [s.strip() for s in line.split(",")]
-            if len(p) >= 9 and p[1].replace(".", "").isdigit():
-                rows.append(p)
+        with open(self.path) as fh:
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
-        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][2]),
-                "reasons": reasons, "samples": len(rows),
-                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
-                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+        return parse_clock_samples(lines)
+
+
+def parse_clock_samples(lines):
+    """Summary of `nvidia-smi --query-gpu=<ClockSampler.FIELDS> --format=csv,noheader,nounits`
+    lines: median SM clock over the loaded samples (at least half the highest
+    clock seen), the maximum clock, the throttle reasons seen active, the
+    sample count and the highest power draw; None without samples."""
+    rows = []
+    for line in lines:
+        p = [s.strip() for s in line.split(",")]
+        if len(p) >= 9 and p[1].replace(".", "").isdigit():
+            rows.append(p)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows]
+    names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+    reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+    loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": float(rows[0][2]),
+            "reasons": reasons, "samples": len(rows),
+            "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+            if any(r[3].replace(".", "").isdigit() for r in rows) else None}
 
 
 # --------------------------------------------------------------- oracle leg

@@ -157,6 +157,25 @@ def test_double_float_butterfly_replayed_on_the_host():
         assert abs(got - exact) <= 2.0 ** -43 * abs(exact), (trial, got, exact)
 
 
+def test_clock_sample_summary():
+    """The benchmark's summary of nvidia-smi samples taken during the timed
+    region: idle samples (below half the highest clock) leave the median, and
+    every throttle reason seen active is reported."""
+    import bench
+    idle = "0, 345, 2070, 120.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+    busy = "0, 2070, 2070, 340.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+    capped = "0, 1965, 2070, 1398.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+    hot = "0, 1800, 2070, 1200.0, 0x40, Not Active, Active, Not Active, Not Active\n"
+    out = bench.parse_clock_samples([idle, busy, busy, capped, "garbage line\n"])
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["samples"] == 4 and out["power_w_max"] == 1398.0
+    assert out["reasons"] == ["sw_power_cap"]
+    out = bench.parse_clock_samples([busy, hot, capped])
+    assert out["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert out["sm_mhz"] == 1965.0
+    assert bench.parse_clock_samples([]) is None
+
+
 def test_readme_examples_name_existing_bindings():
     """Every gbkde.<name> the README's examples use exists in the binding."""
     from paper_1505_01998_gb300 import gbkde
