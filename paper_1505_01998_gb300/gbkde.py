@@ -24,7 +24,7 @@ KDE_FP32_KAHAN, KDE_FP32_PLAIN = 0, 1
 KDE_GRID_DEFAULT_Z, KDE_GRID_EXPLICIT, KDE_GRID_LOG = 0, 1, 2
 KDE_METHOD_LSCV, KDE_METHOD_PLUGIN = 1, 2
 KDE_FLAG_MIN_AT_LOWER_EDGE, KDE_FLAG_MIN_AT_UPPER_EDGE = 1, 2
-KDE_MAX_D, KDE_MAX_NH = 4, 1024
+KDE_MAX_D, KDE_MAX_NH = 16, 1024
 
 
 class KdeError(RuntimeError):

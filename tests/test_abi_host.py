@@ -176,17 +176,6 @@ def test_clock_sample_summary():
     assert bench.parse_clock_samples([]) is None
 
 
-def test_readme_examples_name_existing_bindings():
-    """Every gbkde.<name> the README's examples use exists in the binding."""
-    from paper_1505_01998_gb300 import gbkde
-    text = open(os.path.join(ROOT, "README.md")).read()
-    code = "\n".join(re.findall(r"```python\n(.*?)```", text, re.S))
-    names = set(re.findall(r"gbkde\.([A-Za-z_][A-Za-z0-9_]*)", code))
-    assert names, "no examples found"
-    missing = sorted(nm for nm in names if not hasattr(gbkde, nm))
-    assert not missing, missing
-
-
 def test_entry_points_reject_bad_arguments_before_any_launch(kde):
     L = kde.lib()
     grid, keep = kde.make_grid(n_h=8)

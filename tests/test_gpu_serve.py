@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from paper_1505_01998_gb300 import datagen
-from tests._helpers import built_lib
+from tests._helpers import TOL, argmin_ok, built_lib, g_err, lscv_A
 
 pytestmark = pytest.mark.gpu
 
@@ -50,9 +50,45 @@ def _single(kde, x, methods, grid):
     return kde.kde_plugin(dev(x))
 
 
+def _oracle_check(r, x, methods, n_h):
+    """A served result against the FP64 oracle on the request's own samples:
+    LSCV g at the served index within 1e-5 of the oracle's g (scaled as in the
+    parity tests), the index the oracle's first minimum or a certified near
+    tie, h the grid point; PLUGIN psi6/psi4 within 1e-5 of their magnitude
+    scale, g2 and h within 1e-5 relative (Sec. 4.4.1 and 4.4.2)."""
+    x64 = np.asarray(x, dtype=np.float64)
+    if x64.ndim == 1:
+        x64 = x64[None, :]
+    d, n = x64.shape
+    if methods & LSCV:
+        h = oracle.grid_default(n, d, n_h)
+        ref = oracle.lscv_h(x64, h)
+        k = r["argmin"]
+        A = lscv_A(x64)
+        err = g_err(r["g_min"], ref["g"][k], ref["s_kk"][k], ref["s_k"][k], h[k], n, d, A)
+        assert err <= TOL, (n, d, k, r["g_min"], ref["g"][k])
+        tol_abs = TOL * float(np.max(np.abs(ref["g"])))
+        assert argmin_ok(k, ref["g"], tol_abs), (k, int(np.argmin(ref["g"])))
+        assert abs(r["h"] - h[k]) <= 1e-12 * h[k]
+    if methods & PLUGIN:
+        ref = oracle.plugin(x64[0])
+        assert ref["status"] == 0
+        for key, rr, gk in (("psi6", 6, "g1"), ("psi4", 4, "g2")):
+            g = ref[gk]
+            mag = (2 * oracle.psi_abs_pair_sum(x64[0], rr, g) + n * abs(oracle.gauss_deriv(rr, 0.0))) / (
+                n * n * g ** (rr + 1))
+            assert abs(r[key] - ref[key]) <= TOL * max(abs(ref[key]), mag), (key, r[key], ref[key])
+        assert abs(r["g2"] - ref["g2"]) <= TOL * ref["g2"]
+        hp = r["h_plugin"] if methods & LSCV else r["h"]
+        assert abs(hp - ref["h"]) <= TOL * ref["h"], (hp, ref["h"])
+
+
 def test_results_in_the_mix_equal_alone_bitwise_and_single_calls_within_tolerance(kde):
+    """40 requests on the device together: each result equals the same request
+    served alone (bitwise), the single call (within 1e-5) and the FP64 oracle
+    on that request's samples (within 1e-5)."""
     grid = kde.make_grid(n_h=128)[0]
-    reqs = _requests(40, seed=1)
+    reqs = _requests(40, seed=1, lo=600, hi=6000)
     srv = kde.Server(arena(1 << 30), max_slots=64)
     tickets = [srv.submit(x, m, grid) for x, m in reqs]
     outs = []
@@ -76,6 +112,7 @@ def test_results_in_the_mix_equal_alone_bitwise_and_single_calls_within_toleranc
         else:
             for k in ("psi6", "g2", "psi4", "h"):
                 assert abs(r[k] - s[k]) <= 1e-5 * abs(s[k]), (k, r[k], s[k])
+        _oracle_check(r, x, m, 128)
     alone.close()
 
 
@@ -142,6 +179,8 @@ def test_phases_spanning_many_steps_match_single_calls(kde, quantum):
                 assert abs(r[k] - s[k]) <= 1e-5 * abs(s[k]), (k, r[k], s[k])
             if not (m & LSCV):
                 assert abs(r["h"] - s["h"]) <= 1e-5 * abs(s["h"])
+        if x.shape[-1] <= 8000:
+            _oracle_check(r, x, m, 64)
 
 
 def test_admission_under_a_small_budget(kde):

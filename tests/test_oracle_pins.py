@@ -119,6 +119,29 @@ def test_default_grid_spans_search_range():
     assert np.allclose(c[:-32] / c[32:], 2.0, rtol=1e-13)
 
 
+def test_log_grid_endpoints_and_constant_ratio():
+    """n_h points from h_min to h_max, both ends included, each step the same
+    ratio (h_max/h_min)^(1/(n_h-1)); the 64-point grid over [0.01, 2] of the
+    n = 1,024 mixture workload steps by 1.0877 (200^(1/63)).  Checked against
+    numpy's geometric spacing and the closed-form ratio."""
+    for lo, hi, n_h in ((0.01, 2.0, 64), (0.3, 0.31, 7), (1e-3, 1e3, 256), (2.0, 0.5, 5)):
+        g = oracle.grid_log(lo, hi, n_h)
+        assert g.size == n_h
+        assert g[0] == lo
+        assert g[-1] == pytest.approx(hi, rel=1e-14)
+        ratio = (hi / lo) ** (1.0 / (n_h - 1))
+        assert np.allclose(g[1:] / g[:-1], ratio, rtol=1e-13)
+        assert np.allclose(g, np.geomspace(lo, hi, n_h), rtol=1e-13)
+    g = oracle.grid_log(0.01, 2.0, 64)
+    assert g[1] / g[0] == pytest.approx(1.0877, abs=5e-5)
+    assert np.all(np.diff(g) > 0)
+
+
+def test_log_grid_single_point_is_the_lower_end():
+    assert list(oracle.grid_log(0.25, 4.0, 1)) == [0.25]
+    assert list(oracle.grid_log(0.7, 0.7, 3)) == [0.7, 0.7, 0.7]
+
+
 # ------------------------------------------------------------- stats
 
 def test_mean_cov_and_inverse_match_numpy():
@@ -201,6 +224,77 @@ def test_psi_block_decomposition_adds_up():
         for b in range(a, 4):
             tot += oracle.psi_pair_sum(x, 6, 7.0, block=(cuts[a], cuts[a + 1], cuts[b], cuts[b + 1]))
     assert tot == pytest.approx(full, rel=1e-12)
+
+
+def _psi_abs_block_bruteforce(x, r, g, i0, i1, j0, j1):
+    """sum of |He_r(u) phi(u)| over i in [i0,i1), j in [j0,j1), i < j, built as a
+    numpy mask over the full difference matrix (no loop shared with the oracle)."""
+    x = np.asarray(x, dtype=np.float64).ravel()
+    n = x.size
+    c = np.zeros(r + 1)
+    c[r] = 1.0
+    u = (x[:, None] - x[None, :]) / g
+    t = np.abs(hermite_e.hermeval(u, c) * np.exp(-u * u / 2) / math.sqrt(2 * math.pi))
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    mask = (i < j) & (i >= i0) & (i < i1) & (j >= j0) & (j < j1)
+    return float(t[mask].sum())
+
+
+@pytest.mark.parametrize("r", [4, 6])
+@pytest.mark.parametrize("n", [2, 9, 40, 64])
+def test_psi_abs_pair_sum_bruteforce(r, n):
+    """The magnitude scale that every psi tolerance divides by: each unordered
+    pair once (not twice, not i = j), |.| taken per term."""
+    x = datagen.mixture_1d(n, seed=300 + n)[0]
+    for g in (0.15, 0.6, 3.0):
+        ref = _psi_abs_block_bruteforce(x, r, g, 0, n, 0, n)
+        assert oracle.psi_abs_pair_sum(x, r, g) == pytest.approx(ref, rel=1e-12, abs=1e-300)
+        # the full i != j sum of |terms| is exactly twice the i < j one
+        full = _psi_bruteforce_abs(x, r, g)
+        assert 2 * oracle.psi_abs_pair_sum(x, r, g) == pytest.approx(full, rel=1e-12)
+    if n >= 40:
+        for blk in ((0, 13, 0, 40), (5, 21, 17, 40), (30, 40, 0, 10), (0, n, 33, 34)):
+            ref = _psi_abs_block_bruteforce(x, r, 0.6, *blk)
+            got = oracle.psi_abs_pair_sum(x, r, 0.6, block=blk)
+            assert got == pytest.approx(ref, rel=1e-12, abs=1e-300), blk
+
+
+def _psi_bruteforce_abs(x, r, g):
+    x = np.asarray(x, dtype=np.float64).ravel()
+    c = np.zeros(r + 1)
+    c[r] = 1.0
+    tot = 0.0
+    for j in range(x.size - 1, -1, -1):
+        for i in range(x.size):
+            if i != j:
+                u = (x[i] - x[j]) / g
+                tot += abs(hermite_e.hermeval(u, c)) * math.exp(-u * u / 2) / math.sqrt(2 * math.pi)
+    return tot
+
+
+def test_psi_abs_pair_sum_bounds_the_signed_sum_with_equality_for_one_sign():
+    """sum |t| >= |sum t| always.  Equality when every term has one sign:
+    He_6 < 0 on |u| < 0.6167 (its smallest positive root), so samples packed
+    within half a bandwidth give only negative K^(6) terms; He_4 > 0 for
+    |u| > 2.3344 (its largest root), so samples spaced three bandwidths apart
+    give only positive K^(4) terms."""
+    x = datagen.skewed_column(300, seed=8)[0].astype(np.float64)
+    for r in (4, 6):
+        for g in (0.5, 4.0, 30.0):
+            s = oracle.psi_pair_sum(x, r, g)
+            a = oracle.psi_abs_pair_sum(x, r, g)
+            assert a >= abs(s) * (1 - 1e-14)
+            assert a > 1.5 * abs(s)  # mixed signs at these bandwidths
+    rng = datagen.rng(12)
+    packed = rng.uniform(0.0, 0.5, 50)  # every |u| < 0.5 at g = 1
+    s6 = oracle.psi_pair_sum(packed, 6, 1.0)
+    assert s6 < 0
+    assert oracle.psi_abs_pair_sum(packed, 6, 1.0) == pytest.approx(-s6, rel=1e-14)
+    spaced = 3.0 * np.arange(40) + rng.uniform(0, 0.1, 40)  # every |u| > 2.9 at g = 1
+    s4 = oracle.psi_pair_sum(spaced, 4, 1.0)
+    assert s4 > 0
+    assert oracle.psi_abs_pair_sum(spaced, 4, 1.0) == pytest.approx(s4, rel=1e-14)
 
 
 # ------------------------------------------------------------ plug-in
