@@ -438,9 +438,11 @@ int kde_serve_destroy(kde_server* server);
  * KDE_NOALLOC_MAX_BYTES (16 MiB) buffer compiled into the library; every GPU
  * that loads the library holds it until the process exits.  Problems whose
  * workspace (kde_workspace_size) exceeds it are rejected with KDE_ENOMEM
- * before anything is queued.  The first call on each device looks up the
- * buffer's device address (with that device current); make it before any
- * stream capture.  Every call shares the buffer, which keeps the previous
+ * before anything is queued.  The first call in each CUDA context (per
+ * device, and again after cudaDeviceReset or a re-created primary context,
+ * which can load the buffer at another address) looks up the buffer's device
+ * address with that context current; make it before any stream capture.
+ * Every call shares the buffer, which keeps the previous
  * call's contents (nothing in it needs to start at zero); calls that overlap
  * on the GPU race on it and must be serialised by the caller.  Allocates no
  * device memory; synchronises the stream like kde_lscv. */
