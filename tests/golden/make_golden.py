@@ -2,8 +2,10 @@
 
 Calls only ``oracle`` and the seeded input generators (never the CUDA
 library).  Run from the repository root: ``python tests/golden/make_golden.py``
-(toy set) and ``python tests/golden/make_golden.py --full-skewed`` (the full
-n = 65,536 skewed-column oracle; minutes on a multi-core host).
+(toy set), ``python tests/golden/make_golden.py --full-skewed`` (the full
+n = 65,536 skewed-column oracle; minutes on a multi-core host) and
+``python tests/golden/make_golden.py --full-mixture`` (the full n = 16,384,
+d = 2, 3, 4 correlated-mixture oracle; minutes).
 """
 import json
 import os
@@ -42,9 +44,38 @@ def full_skewed_column():
         json.dump(out, f, indent=1)
 
 
+def full_correlated_mixture():
+    """The full oracle of the multivariate LSCV selection: n = 16,384 samples of
+    the 4-component correlated mixture (datagen.correlated_mixture(n, d,
+    seed=3+d)) for d = 2, 3, 4, H = h^2 S on the 128-point grid over Z(h0):
+    g(h), both exponential sums and the argmin over all 1.3e8 pairs, in FP64
+    (Sec. 4.4.2, Eqs. LSCV-gh, LSCV-Kx, LSCV-KKx)."""
+    from paper_1505_01998_gb300 import datagen
+    n, n_h = 16384, 128
+    out = {
+        "_about": "FP64 oracle over all pairs of the n = 16,384 correlated mixtures "
+                  "(datagen.correlated_mixture(16384, d, seed=3+d), d = 2, 3, 4): LSCV with "
+                  "H = h^2 S, g(h), its exponential sums and argmin on the 128-point grid over "
+                  "Z(h0). Written by make_golden.py --full-mixture; calls only the oracle.",
+        "n": n, "n_h": n_h, "cases": {},
+    }
+    for d in (2, 3, 4):
+        x = datagen.correlated_mixture(n, d, seed=3 + d).astype(np.float64)
+        h = oracle.grid_default(n, d, n_h)
+        r = oracle.lscv_h(x, h)
+        out["cases"][str(d)] = {"seed": 3 + d, "h": h.tolist(), "g": r["g"].tolist(),
+                                "s_kk": r["s_kk"].tolist(), "s_k": r["s_k"].tolist(),
+                                "argmin": r["argmin"]}
+    with open(os.path.join(HERE, "mixture16384_oracle.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def main():
     if "--full-skewed" in sys.argv:
         full_skewed_column()
+        return
+    if "--full-mixture" in sys.argv:
+        full_correlated_mixture()
         return
     consts = json.load(open(os.path.join(HERE, "paper_constants.json")))
     x = np.array(consts["toy_dataset"]["x"], dtype=np.float64)

@@ -391,30 +391,31 @@ def test_full_size_skewed_column_against_full_oracle(kde):
 
 @pytest.mark.parametrize("d", [2, 3, 4])
 def test_full_size_correlated_mixture(kde, d):
-    """n = 16,384, d = 2..4, H = h^2 S on a 128-point grid: the oracle's g at
-    the device argmin and its neighbours, plus sampled tiles."""
-    n = 16384
-    x = datagen.correlated_mixture(n, d, seed=3 + d)
+    """n = 16,384, d = 2..4, H = h^2 S on the 128-point default grid, default
+    launch geometry, Kahan FP32, against the FP64 oracle over all 1.3e8 pairs
+    stored by tests/golden/make_golden.py --full-mixture: g(h), S1 and S2 at
+    every grid point and the argmin."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mixture16384_oracle.json")))
+    ref = gold["cases"][str(d)]
+    n = gold["n"]
+    x = datagen.correlated_mixture(n, d, seed=ref["seed"])
     xd = dev(x)
     x64 = host64(x)
-    h = oracle.grid_default(n, d, 128)
-    res, g, _ = kde.kde_lscv(xd, _explicit(kde, h))
-    k = res["argmin"]
-    ks = [kk for kk in (k - 1, k, k + 1) if 0 <= kk < len(h)]
-    ref = oracle.lscv_h(x64, h[ks])
-    A = lscv_A(x64)
-    err = g_err(g[ks], ref["g"], ref["s_kk"], ref["s_k"], h[ks], n, d, A)
-    assert err.max() < TOL
-    # the device minimum is a local minimum of the oracle's objective (or a tie)
-    kk = ks.index(k)
-    assert np.all(ref["g"][kk] <= ref["g"] + TOL * np.abs(ref["g"]).max())
+    h = np.asarray(ref["h"])
+    res, g, hh = kde.kde_lscv(xd, kde.make_grid(n_h=gold["n_h"])[0])
+    assert np.allclose(hh, h, rtol=1e-15, atol=0)
+    s_kk, s_k, g_ref = np.asarray(ref["s_kk"]), np.asarray(ref["s_k"]), np.asarray(ref["g"])
+    err = g_err(g, g_ref, s_kk, s_k, h, n, d, lscv_A(x64))
+    assert err.max() < TOL, (err.max(), int(err.argmax()))
+    assert argmin_ok(res["argmin"], g_ref, TOL * np.max(np.abs(g_ref)))
     T = 128
     tiles = kde.kde_tile_count(n, T)
-    for tb, te in ((0, 2), (tiles - 2, tiles)):
-        s1, s2 = kde.kde_lscv_tile_sums(xd, h, tb, te)
-        r1, r2 = oracle_tile_sums_lscv(x64, h, T, tb, te, kde)
-        assert s_err(s1, r1, (te - tb) * T * T).max() < TOL
-        assert s_err(s2, r2, (te - tb) * T * T).max() < TOL
+    s1, s2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles)
+    npairs = n * (n - 1) // 2
+    assert s_err(s1, s_kk, npairs).max() < TOL
+    assert s_err(s2, s_k, npairs).max() < TOL
 
 
 @pytest.mark.parametrize("n,d,dtype", [(1025, 1, "float32"), (131073, 3, "float32"), (300001, 2, "float64"),
