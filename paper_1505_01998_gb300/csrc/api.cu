@@ -240,6 +240,11 @@ void apply_octave(Geometry* g, const std::vector<double>& h) {
   const int nh = (int)h.size();
   if (g->B != 16 || nh < 16 || nh % 16 != 0 || g->n_h_pad != nh) return;
   const int P = nh / 8;
+  // the kernel forms octave arguments by exponent adds, exact while
+  // |1/h^2| <= 2^40, and masks pairs with a finite squared distance that
+  // zeroes every term while |1/h^2| >= 2^-40: outside, the direct kernel
+  for (int k = 0; k < nh; ++k)
+    if (!(h[k] >= 0x1p-20 && h[k] <= 0x1p20)) return;
   for (int k = P; k < nh; ++k) {
     // c_(k-P) = 2 c_k with c = 1/h^2, i.e. h_k^2 = 2 h_(k-P)^2
     const double r = (h[k] * h[k]) / (h[k - P] * h[k - P]);
@@ -425,6 +430,11 @@ int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile) {
 
 // -------------------------------------------------------------- LSCV_h
 
+// Largest partial table (item rows x 2 n_h values) that the last CTA of a
+// single-selection pair kernel reduces itself: 32 Ki doubles, a few
+// microseconds of one CTA's L2 reads, against two kernel launches.
+constexpr int64_t kFuseMaxPartials = 32768;
+
 static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std::vector<double>& h,
                       const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st,
                       int64_t tile_begin, int64_t tile_end, Geometry* gout) {
@@ -450,12 +460,15 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   CK(launch_setup(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
   CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
   Phase ph{ds, off, nullptr, 1, 0, g.items};
+  // small partial tables: the pair kernel's last CTA reduces and finishes
+  // (saves two launches); large ones keep the many-CTA reduction
+  const bool fuse = !lscv_warp_items(g.dk, g.B) && g.rows * 2 * (int64_t)g.n_h_pad <= kFuseMaxPartials;
+  ph.fuse = fuse ? 1 : 0;
   const int grid = (int)std::min<int64_t>(g.items, g.ctas);
   CK(mark(0, st));
   CK(launch_lscv(ph, g.dk, g.B, g.R, g.kahan, g.oct_P > 0, std::max(grid, 1), st));
   CK(mark(1, st));
-  CK(launch_lscv_reduce(ds, 1, nullptr, g.n_h_pad, st));
-  CK(launch_lscv_finish(ds, 1, nullptr, st));
+  if (!fuse) CK(launch_lscv_reduce(ds, 1, nullptr, g.n_h_pad, g.rows, st));
   if (gout) *gout = g;
   return KDE_OK;
 }
@@ -470,16 +483,35 @@ int kde_lscv_async(const void* x_dev, int dtype, int64_t n, int d, const kde_gri
   return lscv_queue(x_dev, dtype, n, d, h, opts, ws, ws_bytes, (cudaStream_t)stream, -1, -1, nullptr);
 }
 
+// Result (and g[], h[]) of a queued selection.  The result and g[] come
+// back in one copy of the workspace span between them (tens of KB: one copy
+// costs less than two); h[] is the grid the host built and uploaded.
 static int fetch_result(const Geometry& g, void* ws, cudaStream_t st, double* g_host,
-                        double* h_host, kde_result* out) {
+                        const std::vector<double>* h, double* h_host, kde_result* out) {
   unsigned char* w = static_cast<unsigned char*>(ws);
   kde_result r;
-  CK(cudaMemcpyAsync(&r, w + g.off_ds + offsetof(DsDev, res), sizeof(r), cudaMemcpyDeviceToHost, st));
-  if (g_host && g.n_h > 0)
-    CK(cudaMemcpyAsync(g_host, w + g.off_g, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost, st));
-  if (h_host && g.n_h > 0)
-    CK(cudaMemcpyAsync(h_host, w + g.off_h, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
+  const size_t off_r = g.off_ds + offsetof(DsDev, res);
+  if (g_host && g.n_h > 0 && g.off_g > off_r) {
+    thread_local std::vector<unsigned char> span;
+    const size_t bytes = g.off_g + sizeof(double) * g.n_h - off_r;
+    span.resize(bytes);
+    CK(cudaMemcpyAsync(span.data(), w + off_r, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    memcpy(&r, span.data(), sizeof(r));
+    memcpy(g_host, span.data() + (g.off_g - off_r), sizeof(double) * g.n_h);
+  } else {
+    CK(cudaMemcpyAsync(&r, w + off_r, sizeof(r), cudaMemcpyDeviceToHost, st));
+    if (g_host && g.n_h > 0)
+      CK(cudaMemcpyAsync(g_host, w + g.off_g, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (h_host && g.n_h > 0) {
+    if (h && (int)h->size() == g.n_h) {
+      memcpy(h_host, h->data(), sizeof(double) * g.n_h);
+    } else {
+      CK(cudaMemcpy(h_host, w + g.off_h, sizeof(double) * g.n_h, cudaMemcpyDeviceToHost));
+    }
+  }
   if (out) *out = r;
   if (r.status != KDE_OK) return fail(r.status, "selection failed on the device: %s", kde_status_string(r.status));
   return KDE_OK;
@@ -498,7 +530,7 @@ int kde_lscv(const void* x_dev, int dtype, int64_t n, int d, const kde_grid* gri
   cudaStream_t st = (cudaStream_t)stream;
   rc = lscv_queue(x_dev, dtype, n, d, h, opts, ws, ws_bytes, st, -1, -1, &g);
   if (rc) return rc;
-  return fetch_result(g, ws, st, g_host, h_host, out);
+  return fetch_result(g, ws, st, g_host, &h, h_host, out);
 }
 
 int kde_lscv_host(const void* x_host, int dtype, int64_t n, int d, const kde_grid* grid,
@@ -521,7 +553,7 @@ int kde_lscv_host(const void* x_host, int dtype, int64_t n, int d, const kde_gri
   CK(cudaMemcpyAsync(xd, x_host, bytes, cudaMemcpyHostToDevice, st));
   rc = lscv_queue(xd, dtype, n, d, h, opts, ws, ws_bytes, st, -1, -1, &g);
   if (rc) return rc;
-  return fetch_result(g, ws, st, g_host, nullptr, out);
+  return fetch_result(g, ws, st, g_host, &h, nullptr, out);
 }
 
 int kde_lscv_tile_sums(const void* x_dev, int dtype, int64_t n, int d, const double* h_host,
@@ -585,12 +617,14 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, g.prows};
   const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));
+  // the last CTA of each psi launch reduces its item partials and advances
+  // the chain (the partials are one value per item)
+  ph.fuse = 6;
   CK(mark(2, st));
   CK(launch_psi(ph, 6, g.Rp, g.kahan, psi_coef(6), grid, st));
   CK(mark(3, st));
-  CK(launch_psi_finish(ds, 1, nullptr, 6, 6, st));
+  ph.fuse = 4;
   CK(launch_psi(ph, 4, g.Rp, g.kahan, psi_coef(4), grid, st));
-  CK(launch_psi_finish(ds, 1, nullptr, 4, 4, st));
   if (gout) *gout = g;
   return KDE_OK;
 }
@@ -611,7 +645,7 @@ int kde_plugin(const void* x_dev, int dtype, int64_t n, const kde_opts* opts, vo
   cudaStream_t st = (cudaStream_t)stream;
   rc = plugin_queue(x_dev, dtype, n, opts, ws, ws_bytes, st, &g);
   if (rc) return rc;
-  return fetch_result(g, ws, st, nullptr, nullptr, out);
+  return fetch_result(g, ws, st, nullptr, nullptr, nullptr, out);
 }
 
 int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* opts, void* ws,
@@ -629,7 +663,7 @@ int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* op
   CK(cudaMemcpyAsync(xd, x_host, (size_t)n * (dtype == KDE_F64 ? 8 : 4), cudaMemcpyHostToDevice, st));
   rc = plugin_queue(xd, dtype, n, opts, ws, ws_bytes, st, &g);
   if (rc) return rc;
-  return fetch_result(g, ws, st, nullptr, nullptr, out);
+  return fetch_result(g, ws, st, nullptr, nullptr, nullptr, out);
 }
 
 int kde_set_kernel_events(void* lscv_begin, void* lscv_end, void* psi_begin, void* psi_end) {

@@ -38,6 +38,7 @@ struct kde_batch_plan {
   };
   std::vector<Group> lscv_groups, psi_groups;
   int n_h_pad_max = 0;
+  int64_t lscv_rows_max = 0;
   // workspace layout (bytes from the base)
   size_t off_desc = 0, off_offs = 0, off_tables = 0, staged = 0, total = 0;
   std::vector<size_t> off_h, off_nc, off_y, off_xc, off_lpart, off_lsum, off_g, off_ppart, off_prep;
@@ -101,6 +102,7 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
       }
       p->lscv_group[r] = it->second;
       p->n_h_pad_max = std::max(p->n_h_pad_max, g.n_h_pad);
+      p->lscv_rows_max = std::max(p->lscv_rows_max, g.rows);
     }
     if (q.methods & KDE_METHOD_PLUGIN) {
       auto k = std::make_tuple(g.Rp, g.kahan);
@@ -268,8 +270,7 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
     BK(launch_psi(ph, 6, G.Rp, G.kahan, c6, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, ctas)), st));
   }
   if (!p->lscv_groups.empty()) {
-    BK(launch_lscv_reduce(ds, n, nullptr, p->n_h_pad_max, st));
-    BK(launch_lscv_finish(ds, n, nullptr, st));
+    BK(launch_lscv_reduce(ds, n, nullptr, p->n_h_pad_max, p->lscv_rows_max, st));
   }
   if (!p->psi_groups.empty()) {
     BK(launch_psi_finish(ds, n, nullptr, 6, 6, st));

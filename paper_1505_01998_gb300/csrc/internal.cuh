@@ -56,6 +56,9 @@ struct DsDev {
   int32_t prep_parts;      // CTAs of the prologue: the samples are cut into this many ranges
   double* prep_part;       // [prep_parts][kPrepRecord] per-range count, mean, centred moments
   uint32_t prep_count;     // ranges finished (the last CTA combines them and resets it to 0)
+  uint32_t pair_count;     // CTAs of a fused pair-kernel launch finished (the last one finishes)
+  uint32_t reduce_count;   // column strips of the LSCV reduction finished (the last one finishes)
+  uint32_t strip_count[2 * KDE_MAX_NH / 32];  // row chunks of each strip finished
   int32_t oct_P;           // > 0: the grid is P points per octave of 1/h^2 (octave kernel)
   // ---- statistics (written on the device)
   double mean[KDE_MAX_D];
@@ -76,7 +79,8 @@ struct Phase {
   const int64_t* off;
   const int64_t* base;  // optional: first local item of each dataset in this launch
   int32_t n_ds;
-  int32_t pad;
+  int32_t fuse;         // 0: finishing kernels follow; else (one dataset) the CTA that
+                        // finishes last reduces the partials and finishes: LSCV 1, psi r
   int64_t total;
 };
 
@@ -229,8 +233,10 @@ cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, bool o
 size_t lscv_smem_bytes(int d, int B, int R, bool kahan, bool oct);
 // sets the kernel's shared-memory attribute without launching (call before a graph capture)
 cudaError_t prepare_lscv(int d, int B, int R, bool kahan, bool oct);
-cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, cudaStream_t st);
-cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, const int* ids, cudaStream_t st);
+// Reduction of the LSCV item rows and the finish (g(h), argmin) of n_ds
+// datasets: rows_max = the largest lscv_rows among them.
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, int64_t rows_max,
+                               cudaStream_t st);
 cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef& cf, int grid,
                        cudaStream_t st);
 // stage: 6 -> reduce psi_6, set g2; 4 -> reduce psi_4, set h; 0 -> raw sum only (into res.g_min)

@@ -45,8 +45,12 @@ struct DPad {
 // Measured at n = 16,384 with 128 bandwidths: d = 4 +2 %; d = 3 no change and
 // d = 2 -2.4 % (its scalar path walks two columns per 16-byte load), so only
 // d = 4 takes it.
+// The octave kernel (d <= 4, 4 rows per lane) may take the same packed form
+// for its squared distances, two rows per FP32x2 operation.
+constexpr bool oct_packed_q(int d) { return false && d <= 4; }
+
 template <int D, int R, bool OCT = false>
-constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT);
+constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT) || (OCT && R == 4 && oct_packed_q(D));
 
 // Wide samples (d > 4, one row per lane; the column tile holds -v): the
 // squared distance to column `col` in packed FP32x2 over coordinate pairs,
@@ -65,13 +69,33 @@ __device__ __forceinline__ float wide_q(const float* __restrict__ sF, int col, c
   return __fadd_rn(s2.x, s2.y);
 }
 
+// a * 2^k by an integer add to the exponent field (ALU pipe instead of an
+// FP32 multiply).  Exact for normal a whose exponent stays below 255; maps
+// -0 and subnormals to values of magnitude below 2^-120, whose ex2 is 1 as
+// that of the exact product is.  The octave kernel guarantees |a| < 2^105
+// (finite edge mask 2^64, |1/h^2| <= 2^40; see kOctMask).
+template <int K>
+__device__ __forceinline__ float mul_pow2(float a) {
+  return __int_as_float(__float_as_int(a) + (K << 23));
+}
+
+// Squared distance given to masked pairs of the octave kernel (diagonal
+// tiles, ragged tail): finite, so that the exponent adds of octave_terms
+// stay exact, and large enough that 2^64 * |c| >= 2^24 for every grid value
+// c = -1/h^2 admitted (|c| in [2^-40, 2^40]): every term is then exactly 0.
+constexpr float kOctMask = 18446744073709551616.0f;  // 2^64
+
 // The octave grid's 16 terms of one pair (two residues x 8 octaves) from its
 // squared distance qv: three chains per residue, each one ex2 and two
 // squarings down (7 -> 6 -> 5, 4 -> 3 -> 2, 1 -> 0 -> one octave below 0);
-// the last square of a chain feeds only its sum (FFMA2).
+// the last square of a chain feeds only its sum (FFMA2).  The arguments of
+// octaves 4 and 1 are 8 and 64 times that of octave 7 (3 and 6 octaves of
+// 1/h^2 up), formed by exponent adds.
 __device__ __forceinline__ void octave_terms(float qv, const float2 (&nca)[3], float2 (&acc)[9]) {
   const float2 q2 = make_float2(qv, qv);
-  const float2 a7 = __fmul2_rn(q2, nca[0]), a4 = __fmul2_rn(q2, nca[1]), a1 = __fmul2_rn(q2, nca[2]);
+  const float2 a7 = __fmul2_rn(q2, nca[0]);
+  const float2 a4 = make_float2(mul_pow2<3>(a7.x), mul_pow2<3>(a7.y));
+  const float2 a1 = make_float2(mul_pow2<6>(a7.x), mul_pow2<6>(a7.y));
   const float2 e7 = make_float2(ex2(a7.x), ex2(a7.y));
   const float2 e4 = make_float2(ex2(a4.x), ex2(a4.y));
   const float2 e1 = make_float2(ex2(a1.x), ex2(a1.y));
@@ -236,6 +260,54 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
                                                  const float (&y)[R][D], const float2 (&nca)[3],
                                                  float2 (&acc)[9], int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
+  if constexpr (kPackedQ<D, R, true>) {
+    // sF holds (-v, -v) per coordinate: rows 2p and 2p + 1 of the lane take
+    // their squared distances to a column in one FP32x2 chain; terms are
+    // accumulated in the same order as below (columns, then rows)
+    const float2* __restrict__ sF2 = reinterpret_cast<const float2*>(sF);
+    float2 y2[R / 2][D];
+#pragma unroll
+    for (int p = 0; p < R / 2; ++p)
+#pragma unroll
+      for (int k = 0; k < D; ++k) y2[p][k] = make_float2(y[2 * p][k], y[2 * p + 1][k]);
+    constexpr int CP = DP == 1 ? 2 : 1;  // columns per 16-byte load (d = 1) or per iteration
+#pragma unroll 1
+    for (int jj = j_lo; jj < j_hi; jj += CP) {
+      float2 nv[CP][DP];
+      if constexpr (DP == 1) {
+        const float4 v = *reinterpret_cast<const float4*>(sF2 + jj);
+        nv[0][0] = make_float2(v.x, v.y);
+        nv[1][0] = make_float2(v.z, v.w);
+      } else {
+#pragma unroll
+        for (int u = 0; u < DP / 2; ++u) {
+          const float4 v = reinterpret_cast<const float4*>(sF2 + jj * DP)[u];
+          nv[0][2 * u] = make_float2(v.x, v.y);
+          nv[0][2 * u + 1] = make_float2(v.z, v.w);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < CP; ++c)
+#pragma unroll
+        for (int p = 0; p < R / 2; ++p) {
+          float2 q = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const float2 dl = __fadd2_rn(y2[p][k], nv[c][k]);
+            q = __ffma2_rn(dl, dl, q);
+          }
+          float qa = q.x, qb = q.y;
+          if (EDGE) {
+            const int64_t ia = i0 + 64 * p, ib = ia + 32, j = jg0 + jj + c;
+            if (!(ia < j && j < n)) qa = kOctMask;  // every term exactly 0
+            if (!(ib < j && j < n)) qb = kOctMask;
+          }
+          octave_terms(qa, nca, acc);
+          octave_terms(qb, nca, acc);
+        }
+    }
+    return;
+  }
   if constexpr (D > 4) {
     // wide samples, one row per lane (sF holds -v): two columns per
     // iteration, each squared distance in packed FP32x2 over coordinate
@@ -252,7 +324,7 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
         qv[c] = wide_q<DP>(sF, jj + c, y2);
         if (EDGE) {
           const int64_t j = jg0 + jj + c;
-          if (!(i0 < j && j < n)) qv[c] = __int_as_float(0x7f800000);  // +inf -> e = 0
+          if (!(i0 < j && j < n)) qv[c] = kOctMask;  // every term exactly 0
         }
       }
 #pragma unroll
@@ -285,12 +357,46 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
         }
         if (EDGE) {
           const int64_t i = i0 + 32 * r, j = jg0 + jj + c;
-          if (!(i < j && j < n)) qv = __int_as_float(0x7f800000);  // +inf -> e = 0
+          if (!(i < j && j < n)) qv = kOctMask;  // every term exactly 0
         }
         octave_terms(qv, nca, acc);
       }
     }
   }
+}
+
+constexpr int kReduceRows = 64;  // item rows per CTA of the LSCV reduction
+
+__device__ double lscv_chunk_total(const DsDev* ds, int c0, int64_t r0, int64_t r1, double* s);
+__device__ void lscv_finish_body(DsDev* ds);
+
+// Fused single-dataset launches: the CTA that finishes last (a counter in the
+// descriptor; no CTA waits) adds the item rows and finishes, with the same
+// code and order as k_lscv_reduce and k_lscv_finish, so results are bitwise
+// those of the separate kernels.
+__device__ __noinline__ void lscv_fused_finish(const Phase& ph) {
+  __shared__ double sFin[kThreads];
+  __shared__ int sLast;
+  DsDev* ds = ph.ds;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sLast = atomicAdd(&ds->pair_count, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  if (ds->res.status == KDE_OK && (ds->methods & KDE_METHOD_LSCV)) {
+    const int W = 2 * ds->n_h_pad;
+    const int64_t rows = ds->lscv_rows;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      double x = 0.0;  // chunk totals in chunk order, as k_lscv_reduce adds them
+      for (int64_t r0 = 0; r0 < rows; r0 += kReduceRows)
+        x += lscv_chunk_total(ds, c0, r0, min(rows, r0 + kReduceRows), sFin);
+      if ((int)threadIdx.x < min(32, W - c0)) ds->lscv_sum[c0 + threadIdx.x] = x;
+    }
+    __syncthreads();
+    lscv_finish_body(ds);
+  }
+  if (threadIdx.x == 0) ds->pair_count = 0u;
 }
 
 // Wide samples (d > 4) on a grid of one or two points, e.g. one g(H) of
@@ -607,48 +713,94 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
       }
     }
   }
+  if (ph.fuse) lscv_fused_finish(ph);
 }
 
-// Sum of the per-item partial rows, one strip of up to 32 columns per CTA.
-// With wc columns in the strip, thread t takes column t % wc and row part
-// t / wc of P = 256 / wc parts: it adds rows part, part + P, ... in that
-// order, and the P part sums of a column are added in order.  A full strip
-// (wc = 32) is warp w adding rows w, w + 8, ...; a narrow one (a grid of one
-// or two points has 4 columns) spreads its rows over all 256 threads.  The
-// loads of 8 consecutive rows of a part are issued before their adds (the
-// addition order is unchanged), so the loop is not bound by load latency.
-__global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
-  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
-  __shared__ double s[kThreads];
-  if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
+// Total of item rows [r0, r1) for the columns [c0, c0 + wc) of one strip
+// (wc = min(32, 2 n_h_pad - c0)), returned to threads t < wc for column
+// c0 + t.  Thread t takes column t % wc and row part t / wc of P = 256 / wc
+// parts: it adds rows r0 + part, r0 + part + P, ... in that order, and the
+// P part sums of a column are added in order.  The loads of a part are
+// issued before its adds (kReduceRows / P <= 8 rows of a full strip).
+__device__ double lscv_chunk_total(const DsDev* ds, int c0, int64_t r0, int64_t r1, double* s) {
   const int W = 2 * ds->n_h_pad;
-  const int c0 = blockIdx.y * 32;
-  if (c0 >= W) return;
   const int wc = min(32, W - c0);
   const int P = kThreads / wc;
   const int t = threadIdx.x;
   double acc = 0.0;
   if (t < P * wc) {
     const double* p = ds->lscv_part + c0 + t % wc;
-    const int64_t rows = ds->lscv_rows;
     constexpr int U = 8;
-    int64_t r = t / wc;
-    for (; r + (U - 1) * P < rows; r += U * P) {
+    int64_t r = r0 + t / wc;
+    for (; r + (U - 1) * P < r1; r += U * P) {
       double v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = p[(r + (int64_t)u * P) * W];
+      for (int u = 0; u < U; ++u) v[u] = __ldcg(p + (r + (int64_t)u * P) * W);
 #pragma unroll
       for (int u = 0; u < U; ++u) acc += v[u];
     }
-    for (; r < rows; r += P) acc += p[r * W];
+    for (; r < r1; r += P) acc += __ldcg(p + r * W);
   }
   s[t] = acc;
   __syncthreads();
-  if (t < wc) {
-    double tot = 0.0;
+  double tot = 0.0;
+  if (t < wc)
     for (int part = 0; part < P; ++part) tot += s[part * wc + t];
-    ds->lscv_sum[c0 + t] = tot;
+  __syncthreads();  // s is reused by the next chunk
+  return tot;
+}
+
+// Sum of the per-item partial rows in two fixed-order levels, then g(h).
+// Grid: datasets x strips of 32 columns x chunks of kReduceRows item rows.
+// A CTA forms its chunk's totals (lscv_chunk_total); with one chunk they are
+// the sums.  With several, the CTA stores them in place of the chunk's first
+// row (read by no one else), and the CTA that completes a strip last (a
+// counter per strip; nobody waits) adds the chunk totals in chunk order.  The
+// CTA that completes the dataset's last strip computes g(h) and the argmin.
+// The order of every addition depends only on the dataset's geometry, so a
+// selection gets the same bits alone, in a batch, served or fused into its
+// pair kernel (which adds in the same order).
+__global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
+  __shared__ double s[kThreads];
+  __shared__ int sLast;
+  if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
+  const int W = 2 * ds->n_h_pad;
+  const int strip = blockIdx.y, c0 = strip * 32;
+  if (c0 >= W) return;
+  const int64_t rows = ds->lscv_rows;
+  const int chunks = (int)((rows + kReduceRows - 1) / kReduceRows);
+  const int chunk = blockIdx.z;
+  if (chunk >= chunks) return;
+  const int t = threadIdx.x, wc = min(32, W - c0);
+  const int64_t r0 = (int64_t)chunk * kReduceRows;
+  const double tot = lscv_chunk_total(ds, c0, r0, min(rows, r0 + kReduceRows), s);
+  if (chunks == 1) {
+    if (t < wc) ds->lscv_sum[c0 + t] = tot;
+  } else {
+    if (t < wc) ds->lscv_part[r0 * W + c0 + t] = tot;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) sLast = atomicAdd(&ds->strip_count[strip], 1u) == (unsigned)chunks - 1u;
+    __syncthreads();
+    if (!sLast) return;
+    __threadfence();
+    if (t < wc) {
+      double x = 0.0;
+      for (int k = 0; k < chunks; ++k) x += __ldcg(ds->lscv_part + (int64_t)k * kReduceRows * W + c0 + t);
+      ds->lscv_sum[c0 + t] = x;
+    }
+    if (t == 0) ds->strip_count[strip] = 0u;
   }
+  __threadfence();
+  __syncthreads();
+  const unsigned strips = (unsigned)((W + 31) / 32);
+  if (t == 0) sLast = atomicAdd(&ds->reduce_count, 1u) == strips - 1u;
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  lscv_finish_body(ds);
+  if (t == 0) ds->reduce_count = 0u;
 }
 
 // Order of (value, index) candidates for a first-index argmin: a number
@@ -663,10 +815,9 @@ __device__ __forceinline__ bool argmin_before(double g, int k, double h, int j) 
   return k < j;
 }
 
-// g(h) on the grid and its first-index argmin (Eqs. LSCV-gh, LSCV-finalH).
-__global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int* ids) {
-  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
-  if (ds->res.status != KDE_OK || !(ds->methods & KDE_METHOD_LSCV)) return;
+// g(h) on the grid and its first-index argmin (Eqs. LSCV-gh, LSCV-finalH),
+// by the threads of one CTA.
+__device__ void lscv_finish_body(DsDev* ds) {
   const int d = ds->d, n_h = ds->n_h;
   const double n = (double)ds->n;
   const double c2 = exp2(1.0 + 0.5 * d);
@@ -680,7 +831,7 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
   double gb = 0.0;
   int best = -1;
   for (int k = threadIdx.x; k < n_h; k += blockDim.x) {
-    const double s1 = ds->lscv_sum[2 * k], s2 = ds->lscv_sum[2 * k + 1];
+    const double s1 = __ldcg(ds->lscv_sum + 2 * k), s2 = __ldcg(ds->lscv_sum + 2 * k + 1);
     const double hk = ds->h[k];
     double hd = 1.0;
     for (int i = 0; i < d; ++i) hd *= hk;
@@ -728,6 +879,7 @@ __global__ void __launch_bounds__(kThreads) k_lscv_finish(DsDev* dsa, const int*
               (best == n_h - 1 ? KDE_FLAG_MIN_AT_UPPER_EDGE : 0);
   }
 }
+
 
 template <int D, int B, int R, bool KAHAN, bool OCT>
 cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
@@ -783,7 +935,7 @@ cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, bool oct, int gr
 
 size_t lscv_smem_bytes(int d, int B, int R, bool kahan, bool oct) {
   const int dp = (d == 3) ? 4 : d;
-  const bool packed = (R == 4 && d == 4 && !oct);  // kPackedQ: the column tile holds pairs
+  const bool packed = (R == 4 && d == 4 && !oct) || (oct && R == 4 && oct_packed_q(d));  // kPackedQ: pairs
   return (size_t)32 * R * dp * (packed ? 8 : 4) + (size_t)kWarps * B * 16 +
          (kahan ? (size_t)kWarps * B * 32 * 16 : 0);
 }
@@ -808,16 +960,14 @@ cudaError_t launch_lscv(const Phase& ph, int d, int B, int R, bool kahan, bool o
   }
 }
 
-cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, cudaStream_t st) {
+cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_max, int64_t rows_max,
+                               cudaStream_t st) {
   if (n_ds <= 0) return cudaSuccess;
-  dim3 grid(n_ds, (2 * n_h_pad_max + 31) / 32);
+  int64_t chunks = (rows_max + kReduceRows - 1) / kReduceRows;
+  if (chunks < 1) chunks = 1;
+  if (chunks > 65535) return cudaErrorInvalidValue;
+  dim3 grid(n_ds, (2 * n_h_pad_max + 31) / 32, (unsigned)chunks);
   k_lscv_reduce<<<grid, kThreads, 0, st>>>(ds, ids);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_lscv_finish(DsDev* ds, int n_ds, const int* ids, cudaStream_t st) {
-  if (n_ds <= 0) return cudaSuccess;
-  k_lscv_finish<<<n_ds, kThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }
 

@@ -268,19 +268,25 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   prep_range(n, parts, b, lo, hi);
   prep_moments<TIN, D>(ds, sm, lo, hi);
   const int npairs = d * (d + 1) / 2;
-  double* rec = ds->prep_part + (size_t)b * kPrepRecord;
+  // one range: the record stays in shared memory where the combination below
+  // reads it, and the CTA is the last by construction
+  const bool single = parts == 1;
+  double* rec = single ? reinterpret_cast<double*>(sm.stage) : ds->prep_part + (size_t)b * kPrepRecord;
+  __syncthreads();  // the moment pass is done with the staging buffer
   if (threadIdx.x == 0) rec[0] = (double)(hi - lo);
   if (threadIdx.x < d) {
     rec[1 + threadIdx.x] = sm.sMean[threadIdx.x];
     rec[1 + KDE_MAX_D + threadIdx.x] = sizeof(TIN) == 4 ? (double)sm.sMeanF[threadIdx.x] : sm.sMean[threadIdx.x];
   }
   if (threadIdx.x < npairs) rec[1 + 2 * KDE_MAX_D + threadIdx.x] = sm.sv[threadIdx.x];
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) sm.last = (atomicAdd(&ds->prep_count, 1u) == (unsigned)parts - 1u);
-  __syncthreads();
-  if (!sm.last) return;
-  __threadfence();
+  if (!single) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sm.last = (atomicAdd(&ds->prep_count, 1u) == (unsigned)parts - 1u);
+    __syncthreads();
+    if (!sm.last) return;
+    __threadfence();
+  }
   // ---- combine the records in range order (records staged in shared memory,
   // kChunk at a time, by coalesced loads; the sums run in range order)
   double* sMean = sm.sMean;
@@ -302,8 +308,9 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   for (int r0 = 0; r0 < parts; r0 += kChunk) {
     const int nr = min(kChunk, parts - r0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
-      cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
+    if (!single)
+      for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
+        cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
     __syncthreads();
     if (threadIdx.x < d)
       for (int r = 0; r < nr; ++r) tmean += cache[r * kPrepRecord] * cache[r * kPrepRecord + 1 + threadIdx.x];
@@ -546,13 +553,24 @@ __device__ __forceinline__ void whiten_dispatch(DsDev* ds, WhitenSmem& sm, int b
 }
 
 // grid: (parts_max, datasets); `ids` (optional) selects the datasets of a table.
-__global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const int* ids) {
+// whiten: every dataset of the launch has one range, so its CTA also
+// whitens (the statistics it needs are its own) and k_prep_whiten is not
+// launched.
+__global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const int* ids, int whiten) {
   __shared__ PrepSmem sm;
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
   if (ds->dtype == KDE_F64)
     stats_dispatch<double>(ds, sm, blockIdx.x);
   else
     stats_dispatch<float>(ds, sm, blockIdx.x);
+  if (whiten) {
+    __shared__ WhitenSmem wm;
+    __syncthreads();  // M, mean and the status are written by this CTA's threads
+    if (ds->dtype == KDE_F64)
+      whiten_dispatch<double>(ds, wm, blockIdx.x);
+    else
+      whiten_dispatch<float>(ds, wm, blockIdx.x);
+  }
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_whiten(DsDev* dsa, const int* ids) {
@@ -633,9 +651,10 @@ cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h
 cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st) {
   if (n_ds <= 0) return cudaSuccess;
   const dim3 grid((unsigned)std::max(1, parts_max), (unsigned)n_ds);
-  k_prep_stats<<<grid, kPrepThreads, 0, st>>>(ds, ids);
+  const int fused = parts_max <= 1;
+  k_prep_stats<<<grid, kPrepThreads, 0, st>>>(ds, ids, fused);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess || fused) return e;
   k_prep_whiten<<<grid, kPrepThreads, 0, st>>>(ds, ids);
   return cudaGetLastError();
 }

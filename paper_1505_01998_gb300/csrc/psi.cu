@@ -67,6 +67,24 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
   }
 }
 
+__device__ void psi_finish_body(DsDev* ds, int stage, int r, double post);
+
+// Fused single-dataset launches: the CTA that finishes last (a counter in the
+// descriptor; no CTA waits) reduces the item partials and advances the chain
+// with the code and order of k_psi_finish, so results are bitwise the same.
+__device__ __noinline__ void psi_fused_finish(const Phase& ph, int r, double post) {
+  __shared__ int sLast;
+  DsDev* ds = ph.ds;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sLast = atomicAdd(&ds->pair_count, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!sLast) return;
+  __threadfence();
+  psi_finish_body(ds, ph.fuse, r, post);
+  if (threadIdx.x == 0) ds->pair_count = 0u;
+}
+
 template <int RD, int R, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
   constexpr int T = 32 * R;
@@ -159,6 +177,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
       ds->psi_part[row] = tot;
     }
   }
+  if (ph.fuse) psi_fused_finish(ph, RD, cf.post);
 }
 
 // Reduce the per-item psi partials in a fixed order and advance the PLUGIN
@@ -168,14 +187,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
 //   stage 4: psi_4(g2) (Eq. PLUGIN-Psi4Estimate, reading R1), then h
 //            (Eq. PLUGIN-Final_h);
 //   stage 0: raw pair sum only (psi tile-sum entry point), into res.g_min.
-__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r,
-                                                         double post) {
-  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
+__device__ void psi_finish_body(DsDev* ds, int stage, int r, double post) {
   __shared__ double sRed[kWarps];
   if (ds->res.status != KDE_OK) return;
   if (stage != 0 && !(ds->methods & KDE_METHOD_PLUGIN)) return;
   double acc = 0.0;
-  for (int64_t k = threadIdx.x; k < ds->psi_rows; k += kThreads) acc += ds->psi_part[k];
+  for (int64_t k = threadIdx.x; k < ds->psi_rows; k += kThreads) acc += __ldcg(ds->psi_part + k);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -229,6 +246,12 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
       res.h_data = h;
     }
   }
+}
+
+__global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r,
+                                                         double post) {
+  DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
+  psi_finish_body(ds, stage, r, post);
 }
 
 template <int RD, int R>

@@ -7,9 +7,12 @@
 //   workspace region (the layout a single call would use) fits in the
 //   caller's arena (first-fit allocator, 256-byte aligned, coalescing).
 //   Its host samples are copied on a copy stream that overlaps compute.
-// * Step: prologue for newly admitted requests; then, for every active
-//   request in its current phase (LSCV items, psi_6 items, psi_4 items), the
-//   next slice of its items up to a per-step evaluation budget, one persistent
+// * Step: prologue for newly admitted requests; then, for the active
+//   requests in service order (a request waiting longer than 32 times its
+//   standalone kernel time, at least 0.5 s, first; then shortest remaining
+//   work first), the next slice of each one's items in its current phase
+//   (LSCV items, psi_6 items, psi_4 items) until the step's evaluation
+//   budget is spent, one persistent
 //   launch per kernel variant over a slot table; then the finishing kernels of
 //   requests whose phase completed.  Up to two steps are in flight; the host
 //   builds the next step while the device runs the current one.
@@ -121,6 +124,7 @@ struct Req {
   kde_result result{};
   Clock::time_point t_submit, t_admit, t_done;
   double evals = 0;
+  double work_total = 0;  // cost of all its phases (direct-kernel evaluations), set at admission
 };
 
 constexpr int kMaxSlots = 1024;
@@ -190,9 +194,49 @@ double step_budget(const kde_server* s) {
 // kernels' measured rates on a GB300 (direct LSCV 9.3e12 evaluations/s,
 // octave-grid LSCV 17.1e12, psi_6 5.6e12, psi_4 6.9e12), so that a step
 // takes about the same time whatever mix of kernels it runs.
-double eval_cost(const Req* r) {
-  if (r->phase == P_LSCV) return r->geo.oct_P > 0 ? 0.55 : 1.0;
-  return r->phase == P_PSI6 ? 1.65 : 1.35;
+double cost_of(const Req* r, int phase) {
+  if (phase == P_LSCV) return r->geo.oct_P > 0 ? 0.55 : 1.0;
+  return phase == P_PSI6 ? 1.65 : 1.35;
+}
+
+double eval_cost(const Req* r) { return cost_of(r, r->phase); }
+
+int64_t items_of(const Req* r, int phase) {
+  return phase == P_LSCV ? r->geo.items : r->geo.prows;
+}
+
+double evals_per_item(const Req* r, int phase) {
+  if (phase == P_LSCV)
+    return (double)r->geo.K * r->geo.T * r->geo.T * std::min(r->geo.n_h_pad, kWarps * r->geo.B);
+  return (double)r->geo.Kp * r->geo.Tp * r->geo.Tp;
+}
+
+int64_t phase_items(const Req* r) { return items_of(r, r->phase); }
+double item_evals(const Req* r) { return evals_per_item(r, r->phase); }
+
+// Work a request still needs, in direct-kernel evaluations: the rest of its
+// current phase and all of its later phases.
+double work_left(const Req* r) {
+  double w = 0.0;
+  for (int ph = std::max(r->phase, (int)P_LSCV); ph <= P_PSI4; ++ph) {
+    if (ph == P_LSCV ? !(r->methods & KDE_METHOD_LSCV) : !(r->methods & KDE_METHOD_PLUGIN)) continue;
+    const double items = (double)items_of(r, ph) - (ph == r->phase ? (double)r->cursor : 0.0);
+    w += items * evals_per_item(r, ph) * cost_of(r, ph);
+  }
+  return w;
+}
+
+// Order of service: shortest remaining work first, except that a request
+// waiting longer than max(kAgeFloorS, kAgeFactor x its work at the kernels'
+// rate) goes before all others (oldest first), so that a large request
+// cannot be starved by a stream of smaller ones.
+constexpr double kDirectEvalsPerS = 9.3e12;  // direct LSCV kernel on a GB300
+constexpr double kAgeFactor = 32.0;
+constexpr double kAgeFloorS = 0.5;
+
+bool overdue(const Req* r, Clock::time_point now) {
+  const double age = std::chrono::duration<double>(now - r->t_submit).count();
+  return age > std::max(kAgeFloorS, kAgeFactor * r->work_total / kDirectEvalsPerS);
 }
 
 void finish_req(kde_server* s, Req* r, int status) {
@@ -259,6 +303,7 @@ void admit(kde_server* s) {
     r->t_admit = Clock::now();
     r->phase = (r->methods & KDE_METHOD_LSCV) ? P_LSCV : P_PSI6;
     r->cursor = 0;
+    r->work_total = work_left(r);
     // samples -> region (copy stream, overlaps running steps)
     unsigned char* base = s->arena + r->region;
     cudaMemcpyAsync(base + r->geo.off_x, r->samples.data(), r->samples.size(), cudaMemcpyHostToDevice, s->copy);
@@ -268,15 +313,6 @@ void admit(kde_server* s) {
   }
 }
 
-int64_t phase_items(const Req* r) {
-  return r->phase == P_LSCV ? r->geo.items : r->geo.prows;
-}
-
-double item_evals(const Req* r) {
-  if (r->phase == P_LSCV)
-    return (double)r->geo.K * r->geo.T * r->geo.T * std::min(r->geo.n_h_pad, kWarps * r->geo.B);
-  return (double)r->geo.Kp * r->geo.Tp * r->geo.Tp;
-}
 
 // Build and launch one step.  Returns false if there was nothing to do.
 bool launch_step(kde_server* s, int* err) {
@@ -318,23 +354,32 @@ bool launch_step(kde_server* s, int* err) {
   st.seq = s->steps + 1;
   double used = 0, step_evals = 0;  // work in direct-kernel evaluations; evaluations run
   std::vector<Req*> new_descs;
-  // oldest admitted first
   std::vector<Req*> active;
   for (int k = 0; k < S; ++k)
     if (s->slot_owner[k]) active.push_back(s->reqs[s->slot_owner[k]]);
-  // Budget policy: the oldest request gets up to a quarter of the step (so
-  // every request progresses), the rest goes to the others by shortest
-  // remaining work first (short requests finish within a few steps even
-  // while long ones run), then any remainder back to the oldest.
-  auto remaining = [](const Req* r) {
-    return (double)(phase_items(r) - r->cursor) * item_evals(r) * eval_cost(r);
-  };
-  std::sort(active.begin(), active.end(), [](const Req* a, const Req* b) { return a->t_admit < b->t_admit; });
-  if (active.size() > 2)
-    std::sort(active.begin() + 1, active.end(),
-              [&](const Req* a, const Req* b) { return remaining(a) < remaining(b); });
-  std::vector<Req*> order = active;
-  if (!active.empty()) order.push_back(active.front());  // second pass for the oldest
+  // Budget policy: the step's budget goes down the service order (overdue
+  // requests oldest first, then shortest remaining work first), each request
+  // taking what it can use.  Short requests finish within a few steps even
+  // while long ones run; the age bound keeps long ones from starving.
+  {
+    const Clock::time_point now = Clock::now();
+    struct Key {
+      bool late;
+      double left;
+      Req* r;
+    };
+    std::vector<Key> keys;
+    keys.reserve(active.size());
+    for (Req* r : active) keys.push_back({overdue(r, now), work_left(r), r});
+    std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+      if (a.late != b.late) return a.late;
+      if (a.late) return a.r->t_submit < b.r->t_submit;
+      if (a.left != b.left) return a.left < b.left;
+      return a.r->t_submit < b.r->t_submit;
+    });
+    for (size_t k = 0; k < keys.size(); ++k) active[k] = keys[k].r;
+  }
+  const std::vector<Req*>& order = active;
   std::vector<char> seen(S, 0);
   for (size_t oi = 0; oi < order.size(); ++oi) {
     Req* r = order[oi];
@@ -358,7 +403,7 @@ bool launch_step(kde_server* s, int* err) {
     }
     const int64_t total = phase_items(r);
     const int64_t left = total - r->cursor;
-    const double cap = (oi == 0 && order.size() > 2) ? 0.25 * budget : budget;
+    const double cap = budget;
     if (left > 0 && (used < cap || st.refs.empty())) {
       const double per = item_evals(r), cost = per * eval_cost(r);
       int64_t take = (int64_t)std::max(1.0, std::floor((cap - used) / cost));
@@ -483,9 +528,13 @@ bool launch_step(kde_server* s, int* err) {
   ck(cudaEventRecord(s->ev_kdone[buf], cs), "kernels done");
   s->have_kdone = true;
   int nh_max = 0;
-  for (int k = 0; k < n_lfin; ++k) nh_max = std::max(nh_max, s->reqs[s->slot_owner[lfin_ids[k]]]->geo.n_h_pad);
-  ck(launch_lscv_reduce(table, n_lfin, d_lfin, nh_max, cs), "lscv reduce");
-  ck(launch_lscv_finish(table, n_lfin, d_lfin, cs), "lscv finish");
+  int64_t rows_max = 0;
+  for (int k = 0; k < n_lfin; ++k) {
+    const Geometry& gk = s->reqs[s->slot_owner[lfin_ids[k]]]->geo;
+    nh_max = std::max(nh_max, gk.n_h_pad);
+    rows_max = std::max(rows_max, gk.rows);
+  }
+  ck(launch_lscv_reduce(table, n_lfin, d_lfin, nh_max, rows_max, cs), "lscv reduce");
   ck(launch_psi_finish(table, n_p6, d_p6, 6, 6, cs), "psi6 finish");
   ck(launch_psi_finish(table, n_p4, d_p4, 4, 4, cs), "psi4 finish");
   ck(cudaMemcpyAsync(s->pin_table[buf], table, sizeof(DsDev) * S, cudaMemcpyDeviceToHost, cs), "table download");
