@@ -225,6 +225,14 @@ int kde_lscv_logdet(const void* x_dev, int dtype, int64_t n, int d, void* ws, si
 int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, const double* s1,
                    const double* s2, double* g_out, kde_result* out);
 
+/* Tile edge and tiles per work item of the single-GPU geometry for n
+ * samples in d dimensions and n_h bandwidths (the LSCV pair kernel) and of
+ * the psi kernels, on the current device with the given options (NULL =
+ * defaults).  Shards whose tile ranges start on multiples of the item size
+ * evaluate exactly the items of the single launch.  Any output may be NULL. */
+int kde_item_tiles(int64_t n, int d, int n_h, const kde_opts* opts, int* lscv_tile, int* lscv_K,
+                   int* psi_tile, int* psi_K);
+
 /* Bracketing search for argmin g(h) over [h_lo, h_hi] (<= 0: Z(h0), Eq.
  * LSCV-Zh0): the golden-section alternative to the dense grid named in
  * Sec. 4.4.2, evaluated 8 interior points per round (log-spaced) in one pass;
@@ -268,6 +276,19 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double g,
 
 /* Tile edge used by the psi kernels for n samples (for kde_psi_tile_sums). */
 int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile);
+
+/* One scalar step of a sharded PLUGIN selection on the host in FP64
+ * (Sec. 4.4.1, readings as in kde_plugin), updating *res in place:
+ *   stage 8: value = sigma (> 0): resets *res, sets sigma, psi_8^NS
+ *            (Eq. PLUGIN-Psi8Estimate) and g1 (Eq. PLUGIN-g1);
+ *   stage 6: value = sum_{i<j} K^(6)((x_i - x_j)/g1) over all pairs (the sum
+ *            of kde_psi_tile_sums over shards covering the tiles once): psi_6
+ *            (Eq. PLUGIN-Psi6Estimate) and g2 (Eq. PLUGIN-g2);
+ *   stage 4: value = the same sum of K^(4) at g2: psi_4 (Eq. PLUGIN-Psi4Estimate)
+ *            and h (Eq. PLUGIN-Final_h) into h, h_data and h_plugin.
+ * Errors: KDE_EINVAL (arguments, stages out of order), KDE_EDEGENERATE
+ * (sigma <= 0, psi_6 >= 0, psi_4 <= 0; res->status is set too). */
+int kde_plugin_merge(int64_t n, int stage, double value, kde_result* res);
 
 /* ------------------------------------------------------------- LSCV_H */
 

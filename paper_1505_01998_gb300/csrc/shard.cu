@@ -1,10 +1,13 @@
-// Host pieces of sharded LSCV_h: the prologue statistic a shard merge needs
-// (log det S) and the FP64 finish of g(h) from summed exponential sums.
+// Host pieces of sharded selections: the prologue statistic a shard merge
+// needs (log det S), the FP64 finish of g(h) from summed exponential sums,
+// the scalar steps of the PLUGIN chain from summed psi pair sums, and the
+// item geometry that keeps shard boundaries on item boundaries.
 //
 // A selection sharded over G GPUs gives every GPU all samples and a
-// contiguous range of the pair-triangle tiles (kde_lscv_tile_sums); the 2 n_h
-// FP64 sums are added across GPUs (one all-reduce), then kde_lscv_merge
-// finishes g(h) and the argmin on any rank.
+// contiguous range of the pair-triangle tiles (kde_lscv_tile_sums /
+// kde_psi_tile_sums); the FP64 sums are added across GPUs (one all-reduce per
+// all-pairs pass: 2 n_h values for LSCV_h, one value each for psi_6 and
+// psi_4), then kde_lscv_merge / kde_plugin_merge finish on every rank.
 #include <cmath>
 #include <cstddef>
 #include <vector>
@@ -90,6 +93,70 @@ int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, 
   r.flags = (best == 0 ? KDE_FLAG_MIN_AT_LOWER_EDGE : 0) | (best == n_h - 1 ? KDE_FLAG_MIN_AT_UPPER_EDGE : 0);
   *out = r;
   return KDE_OK;
+}
+
+int kde_item_tiles(int64_t n, int d, int n_h, const kde_opts* opts, int* lscv_tile, int* lscv_K,
+                   int* psi_tile, int* psi_K) {
+  if (n < 2 || d < 1 || d > KDE_MAX_D || n_h < 0 || n_h > KDE_MAX_NH)
+    return fail(KDE_EINVAL, "kde_item_tiles: bad sizes");
+  int rc = check_opts(opts);
+  if (rc) return rc;
+  Geometry g;
+  rc = make_geometry(n, d, n_h, opts, device_sms(), &g);
+  if (rc) return rc;
+  if (lscv_tile) *lscv_tile = g.T;
+  if (lscv_K) *lscv_K = g.K;
+  if (psi_tile) *psi_tile = g.Tp;
+  if (psi_K) *psi_K = g.Kp;
+  return KDE_OK;
+}
+
+int kde_plugin_merge(int64_t n, int stage, double value, kde_result* res) {
+  if (!res || n < 2 || !std::isfinite(value)) return fail(KDE_EINVAL, "kde_plugin_merge: bad arguments");
+  const double pi = 3.14159265358979323846;
+  const double inv_sqrt_2pi = 1.0 / std::sqrt(2.0 * pi);
+  const double k6_0 = -15.0 * inv_sqrt_2pi;  // K^(6)(0)
+  const double k4_0 = 3.0 * inv_sqrt_2pi;    // K^(4)(0)
+  const double dn = (double)n;
+  kde_result& r = *res;
+  switch (stage) {
+    case 8: {  // value = sigma: Eqs. PLUGIN-Psi8Estimate, PLUGIN-g1
+      if (!(value > 0)) return fail(KDE_EDEGENERATE, "sigma = %g", value);
+      r = kde_result{};
+      r.status = KDE_OK;
+      r.method = KDE_METHOD_PLUGIN;
+      r.d = 1;
+      r.sigma = value;
+      r.psi8_ns = 105.0 / (32.0 * std::sqrt(pi) * std::pow(value, 9.0));
+      r.g1 = std::pow(-2.0 * k6_0 / (r.psi8_ns * dn), 1.0 / 9.0);
+      return KDE_OK;
+    }
+    case 6: {  // value = sum_{i<j} K^(6)((x_i - x_j)/g1): Eqs. PLUGIN-Psi6Estimate, PLUGIN-g2
+      if (!(r.g1 > 0)) return fail(KDE_EINVAL, "kde_plugin_merge: stage 6 needs g1 (stage 8 first)");
+      r.psi6 = (2.0 * value + dn * k6_0) / (dn * dn * std::pow(r.g1, 7.0));
+      if (!(r.psi6 < 0.0)) {
+        r.status = KDE_EDEGENERATE;
+        return fail(KDE_EDEGENERATE, "psi_6 = %g is not negative", r.psi6);
+      }
+      r.g2 = std::pow(-2.0 * k4_0 / (r.psi6 * dn), 1.0 / 7.0);
+      return KDE_OK;
+    }
+    case 4: {  // value = sum_{i<j} K^(4)((x_i - x_j)/g2): Eqs. PLUGIN-Psi4Estimate, PLUGIN-Final_h
+      if (!(r.g2 > 0)) return fail(KDE_EINVAL, "kde_plugin_merge: stage 4 needs g2 (stage 6 first)");
+      r.psi4 = (2.0 * value + dn * k4_0) / (dn * dn * std::pow(r.g2, 5.0));
+      if (!(r.psi4 > 0.0)) {
+        r.status = KDE_EDEGENERATE;
+        return fail(KDE_EDEGENERATE, "psi_4 = %g is not positive", r.psi4);
+      }
+      const double rk = 1.0 / (2.0 * std::sqrt(pi));  // R(K)
+      r.h_plugin = std::pow(rk / (r.psi4 * dn), 0.2);
+      r.h = r.h_plugin;
+      r.h_data = r.h_plugin;
+      return KDE_OK;
+    }
+    default:
+      return fail(KDE_EINVAL, "kde_plugin_merge: stage %d (8, 6 or 4)", stage);
+  }
 }
 
 }  // extern "C"

@@ -130,6 +130,10 @@ SIGNATURES = {
     "kde_autotune_save": (_I, [ctypes.c_char_p]),
     "kde_autotune_load": (_I, [ctypes.c_char_p]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
+    "kde_plugin_merge": (_I, [_L, _I, _D, ctypes.POINTER(kde_result)]),
+    "kde_item_tiles": (_I, [_L, _I, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -225,6 +229,25 @@ def kde_lscv_merge(n: int, d: int, logdet_S: float, h, s1, s2):
     _check(lib().kde_lscv_merge(int(n), int(d), float(logdet_S), _dp(hh), hh.size, _dp(a), _dp(b),
                                 _dp(g), ctypes.byref(res)))
     return res.as_dict(), g
+
+def kde_plugin_merge(n: int, stage: int, value: float, res: dict | None = None) -> dict:
+    """One host step of a sharded PLUGIN chain: stage 8 (value = sigma),
+    6 (value = summed psi_6 pair sum at g1) or 4 (psi_4 pair sum at g2)."""
+    r = kde_result()
+    if res is not None:
+        for k, _ in kde_result._fields_:
+            setattr(r, k, res[k])
+    _check(lib().kde_plugin_merge(int(n), int(stage), float(value), ctypes.byref(r)))
+    return r.as_dict()
+
+
+def kde_item_tiles(n: int, d: int, n_h: int, opts: kde_opts | None = None) -> dict:
+    """Tile edges and tiles per item of the single-GPU geometry."""
+    v = [ctypes.c_int(0) for _ in range(4)]
+    _check(lib().kde_item_tiles(int(n), int(d), int(n_h), ctypes.byref(opts) if opts else None,
+                                *(ctypes.byref(x) for x in v)))
+    return {"lscv_tile": v[0].value, "lscv_K": v[1].value, "psi_tile": v[2].value, "psi_K": v[3].value}
+
 
 KDE_NOALLOC_MAX_BYTES = 16 << 20
 
