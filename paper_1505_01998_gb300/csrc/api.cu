@@ -161,14 +161,14 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   size_t o0 = 0;
   g->off_ds = o0;
   o0 = align_up(o0 + sizeof(DsDev), 256);
+  g->off_g = o0;  // right after the descriptor: the result and g[] come back in one short copy
+  o0 = align_up(o0 + KDE_MAX_NH * sizeof(double), 256);
   g->off_off = o0;
   o0 = align_up(o0 + 8 * sizeof(int64_t), 256);
   g->off_h = o0;
   o0 = align_up(o0 + KDE_MAX_NH * sizeof(double), 256);
   g->off_nc = o0;
   o0 = align_up(o0 + KDE_MAX_NH * sizeof(float), 256);
-  g->off_g = o0;
-  o0 = align_up(o0 + KDE_MAX_NH * sizeof(double), 256);
   g->off_sum = o0;
   o0 = align_up(o0 + 2 * KDE_MAX_NH * sizeof(double), 256);
   g->off_x = o0;

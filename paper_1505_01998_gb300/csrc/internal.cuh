@@ -175,17 +175,55 @@ __device__ __forceinline__ double warp_sum(double v) {
 // The result carries about 44 bits; FP32 arithmetic only, since the FP64
 // pipe of this part runs at a small fraction of the FP32 rate.  Every lane
 // ends with the same pair (each step is symmetric in its two operands).
+// (hi, lo) += (h2, l2) in double-float arithmetic: Knuth's TwoSum of the
+// high parts, the low parts and the rounding error added, then renormalised.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  const float t = __fadd_rn(__fadd_rn(lo, l2), e);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
 __device__ __forceinline__ float2 warp_sum_ff(float hi, float lo) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
     const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-    const float s = __fadd_rn(hi, h2);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
-    const float t = __fadd_rn(__fadd_rn(lo, l2), e);
-    hi = __fadd_rn(s, t);
-    lo = __fsub_rn(t, __fsub_rn(hi, s));
+    ff_add(hi, lo, h2, l2);
+  }
+  return make_float2(hi, lo);
+}
+
+// Warp totals of nsum double-float values per lane held in shared memory as
+// Kahan pairs: sum q of lane L is (v.x, -v.y) (q even) or (v.z, -v.w) (q odd)
+// of v = slots[(q >> 1) * 32 + L].  One lane adds each sum over the 32 lanes
+// (for nsum <= 16, two lanes over 16 lanes each, then the upper half into the
+// lower), in double-float arithmetic, starting at lane q and wrapping around
+// (a fixed order per sum; staggered starts keep the concurrent shared-memory
+// reads on different banks).  Lane q (< nsum) returns the total of sum q.
+// Far fewer instructions than nsum butterflies.
+__device__ __forceinline__ float2 warp_sums_ff_transposed(const float4* slots, int nsum, int lane) {
+  const bool two = nsum <= 16;
+  const int q = two ? (lane & 15) : lane;
+  const int base = two ? (lane >> 4) * 16 : 0;
+  const int cnt = two ? 16 : 32;
+  float hi = 0.f, lo = 0.f;
+  if (q < nsum) {
+    const float4* v = slots + (q >> 1) * 32 + base;
+    for (int i = 0; i < cnt; ++i) {
+      const float4 k = v[(i + q) & (cnt - 1)];
+      if (q & 1)
+        ff_add(hi, lo, k.z, -k.w);
+      else
+        ff_add(hi, lo, k.x, -k.y);
+    }
+  }
+  if (two) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, 16);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, 16);
+    if (lane < 16) ff_add(hi, lo, h2, l2);
   }
   return make_float2(hi, lo);
 }

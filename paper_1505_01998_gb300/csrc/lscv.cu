@@ -45,9 +45,10 @@ struct DPad {
 // Measured at n = 16,384 with 128 bandwidths: d = 4 +2 %; d = 3 no change and
 // d = 2 -2.4 % (its scalar path walks two columns per 16-byte load), so only
 // d = 4 takes it.
-// The octave kernel (d <= 4, 4 rows per lane) may take the same packed form
-// for its squared distances, two rows per FP32x2 operation.
-constexpr bool oct_packed_q(int d) { return false && d <= 4; }
+// The octave kernel (d <= 4, 4 rows per lane) can take the same packed form
+// for its squared distances, two rows per FP32x2 operation.  Measured on the
+// full-size launch it was within 1 % of the scalar form, so it is off.
+constexpr bool oct_packed_q(int d) { return d < 0; }
 
 template <int D, int R, bool OCT = false>
 constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT) || (OCT && R == 4 && oct_packed_q(D));
@@ -645,6 +646,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
     __syncthreads();
     if constexpr (OCT) {
       // running sums j = 0..8 per residue; local bandwidth b = residue + 2 * octave
+      // (butterflies: octave items are long, and the transposed form below
+      // raised this kernel's register count and slowed its pair loop)
       float2 vs[9][2];
 #pragma unroll
       for (int j = 0; j < 9; ++j) {
@@ -672,25 +675,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
           }
       }
     }
+    if constexpr (!OCT && KAHAN) {
+      // fold the unflushed runs into the lane's Kahan pairs (slot b: S1 in
+      // x, y and S2 in z, w), then warp totals of the 2B values in lane
+      // order: lane q = 2 b + (0: S1, 1: S2)
 #pragma unroll
-    for (int bp = 0; bp < B / 2 && !OCT; ++bp) {
+      for (int bp = 0; bp < B / 2; ++bp)
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int b = 2 * bp + half;
+          float4 k = sK[(warp * B + b) * 32 + lane];
+          kahan_add(k.x, k.y, half ? t1[bp].y : t1[bp].x);
+          kahan_add(k.z, k.w, half ? t2[bp].y : t2[bp].x);
+          if (!active) k = make_float4(0.f, 0.f, 0.f, 0.f);
+          sK[(warp * B + b) * 32 + lane] = k;
+        }
+      __syncwarp();
+      const float2 v = warp_sums_ff_transposed(sK + warp * B * 32, 2 * B, lane);
+      if (lane < 2 * B) sRed[(warp * B + (lane >> 1)) * 2 + (lane & 1)] = ff_value(v);
+    }
+#pragma unroll
+    for (int bp = 0; bp < B / 2 && !OCT && !KAHAN; ++bp) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int b = 2 * bp + half;
-        float h1, l1, h2, l2;
-        if (KAHAN) {
-          float4 k = sK[(warp * B + b) * 32 + lane];
-          const float r1 = half ? t1[bp].y : t1[bp].x;  // unflushed tail of the run
-          const float r2 = half ? t2[bp].y : t2[bp].x;
-          kahan_add(k.x, k.y, r1);
-          kahan_add(k.z, k.w, r2);
-          h1 = k.x, l1 = -k.y, h2 = k.z, l2 = -k.w;
-        } else {
-          h1 = half ? t1[bp].y : t1[bp].x, l1 = 0.f;
-          h2 = half ? t2[bp].y : t2[bp].x, l2 = 0.f;
-        }
-        if (!active) h1 = l1 = h2 = l2 = 0.f;
-        const float2 v1 = warp_sum_ff(h1, l1), v2 = warp_sum_ff(h2, l2);
+        float h1 = half ? t1[bp].y : t1[bp].x, h2 = half ? t2[bp].y : t2[bp].x;
+        if (!active) h1 = h2 = 0.f;
+        const float2 v1 = warp_sum_ff(h1, 0.f), v2 = warp_sum_ff(h2, 0.f);
         if (lane == 0) {
           sRed[(warp * B + b) * 2] = ff_value(v1);
           sRed[(warp * B + b) * 2 + 1] = ff_value(v2);
@@ -785,11 +796,19 @@ __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int*
     __syncthreads();
     if (!sLast) return;
     __threadfence();
-    if (t < wc) {
-      double x = 0.0;
-      for (int k = 0; k < chunks; ++k) x += __ldcg(ds->lscv_part + (int64_t)k * kReduceRows * W + c0 + t);
-      ds->lscv_sum[c0 + t] = x;
+    // the chunk totals are loaded together (one L2 round trip per 256), then
+    // added in chunk order
+    double x = 0.0;
+    for (int k0 = 0; k0 < chunks; k0 += kThreads / wc) {
+      const int nk = min(kThreads / wc, chunks - k0);
+      if (t < nk * wc)
+        s[t] = __ldcg(ds->lscv_part + (int64_t)(k0 + t / wc) * kReduceRows * W + c0 + t % wc);
+      __syncthreads();
+      if (t < wc)
+        for (int k = 0; k < nk; ++k) x += s[k * wc + t];
+      __syncthreads();
     }
+    if (t < wc) ds->lscv_sum[c0 + t] = x;
     if (t == 0) ds->strip_count[strip] = 0u;
   }
   __threadfence();

@@ -157,6 +157,47 @@ def test_double_float_butterfly_replayed_on_the_host():
         assert abs(got - exact) <= 2.0 ** -43 * abs(exact), (trial, got, exact)
 
 
+def _ff_add(h, l, h2, l2):
+    f = np.float32
+    s = f(h + h2)
+    bb = f(s - h)
+    e = f(f(h - f(s - bb)) + f(h2 - bb))
+    t = f(f(l + l2) + e)
+    hn = f(s + t)
+    return hn, f(t - f(hn - s))
+
+
+@pytest.mark.parametrize("two_halves", [True, False])
+def test_double_float_lane_order_sum_replayed_on_the_host(two_halves):
+    """The Kahan-mode item totals of the LSCV kernel are warp sums of FP32
+    (hi, lo) pairs taken by one lane per sum in a fixed, staggered lane order
+    (warp_sums_ff_transposed): over all 32 lanes from lane q, or over two
+    halves of 16 lanes whose totals are then added.  Replayed in numpy float32
+    with the same order: the pair carries the exact sum to about 44 bits."""
+    f = np.float32
+    rng = np.random.default_rng(6)
+    for trial in range(200):
+        q = int(rng.integers(0, 16 if two_halves else 32))
+        scale = 10.0 ** rng.uniform(-6, 9)
+        hi = (rng.lognormal(0, 2, 32) * scale).astype(f)
+        lo = (hi * rng.uniform(-1, 1, 32) * 2.0 ** -25).astype(f)
+        parts = [range(0, 16), range(16, 32)] if two_halves else [range(32)]
+        tot = []
+        for lanes in parts:
+            lanes = list(lanes)
+            h, l = f(0), f(0)
+            for i in range(len(lanes)):
+                k = lanes[(i + q) % len(lanes)]
+                h, l = _ff_add(h, l, hi[k], lo[k])
+            tot.append((h, l))
+        h, l = tot[0]
+        if two_halves:
+            h, l = _ff_add(h, l, *tot[1])
+        exact = math.fsum([float(v) for v in hi] + [float(v) for v in lo])
+        got = float(h) + float(l)
+        assert abs(got - exact) <= 2.0 ** -43 * abs(exact), (trial, got, exact)
+
+
 def test_clock_sample_summary():
     """The benchmark's summary of nvidia-smi samples taken during the timed
     region: idle samples (below half the highest clock) leave the median, and
@@ -201,6 +242,13 @@ def test_entry_points_reject_bad_arguments_before_any_launch(kde):
     g2 = kde.kde_grid(kde.KDE_GRID_DEFAULT_Z, 2000, None, 0.0, 0.0)
     assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g2), None, dummy, 1 << 20, None, None, None,
                       ctypes.byref(res)) == kde.KDE_EINVAL
+    g1025 = kde.kde_grid(kde.KDE_GRID_DEFAULT_Z, kde.KDE_MAX_NH + 1, None, 0.0, 0.0)
+    assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g1025), None, dummy, 1 << 20, None, None, None,
+                      ctypes.byref(res)) == kde.KDE_EINVAL
+    # the merge steps of sharded selections check their arguments on the host
+    assert L.kde_plugin_merge(1, 8, 1.0, ctypes.byref(res)) == kde.KDE_EINVAL
+    assert L.kde_plugin_merge(100, 8, float("nan"), ctypes.byref(res)) == kde.KDE_EINVAL
+    assert L.kde_item_tiles(100, 0, 8, None, None, None, None, None) == kde.KDE_EINVAL
     # a log grid with a non-positive bound
     g3 = kde.kde_grid(kde.KDE_GRID_LOG, 8, None, -1.0, 2.0)
     assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g3), None, dummy, 1 << 20, None, None, None,
