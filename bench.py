@@ -26,6 +26,7 @@ divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -61,12 +62,13 @@ def lscv_per_clk(probe, d, octave):
     Direct grids: one ex2 and 3 FP32 lane-operations per evaluation (the
     squared distance, 2d lanes per pair, is shared by 16 bandwidths and left
     out).  Octave grids, per 16 evaluations (one pair, two residues, eight
-    octaves): 6 ex2; 3 scalings, 3 squarings and 6 running sums in FMUL2/FADD2
-    (24 lanes); 3 squarings fused with their running sums in FFMA2 (6 lanes);
-    and 2d FMA lanes for the squared distance."""
+    octaves): 6 ex2; one scaling, 3 squarings and 6 running sums in
+    FMUL2/FADD2 (20 lanes; the other two scalings are exponent adds on the
+    integer pipe); 3 squarings fused with their running sums in FFMA2
+    (6 lanes); and 2d FMA lanes for the squared distance."""
     if not octave:
         return min(probe["mufu_ex2_per_clk_sm"], probe["ffma_lanes_per_clk_sm"] / 3.0)
-    fp32 = 1.0 / (1.5 / probe["fmul2_fadd2_lanes_per_clk_sm"] + 0.375 / probe["ffma2_lanes_per_clk_sm"]
+    fp32 = 1.0 / (1.25 / probe["fmul2_fadd2_lanes_per_clk_sm"] + 0.375 / probe["ffma2_lanes_per_clk_sm"]
                   + (2.0 * d / 16.0) / probe["ffma_lanes_per_clk_sm"])
     return min(probe["mufu_ex2_per_clk_sm"] / 0.375, fp32)
 
@@ -77,7 +79,7 @@ def lscv_basis(probe, d, octave, mhz):
                 f"{probe['ffma_lanes_per_clk_sm']:.1f}/clk/SM / 3 per eval) x {probe['sm_count']} SMs x "
                 f"{mhz:.0f} MHz")
     return (f"octave grid: min(MUFU ex2 {probe['mufu_ex2_per_clk_sm']:.1f}/clk/SM / 0.375 per eval, "
-            f"1 / (1.5 / {probe['fmul2_fadd2_lanes_per_clk_sm']:.1f} FMUL2/FADD2 lanes + 0.375 / "
+            f"1 / (1.25 / {probe['fmul2_fadd2_lanes_per_clk_sm']:.1f} FMUL2/FADD2 lanes + 0.375 / "
             f"{probe['ffma2_lanes_per_clk_sm']:.1f} FFMA2 lanes + {2 * d}/16 / "
             f"{probe['ffma_lanes_per_clk_sm']:.1f} FFMA lanes) per eval) x "
             f"{probe['sm_count']} SMs x {mhz:.0f} MHz")
@@ -91,9 +93,11 @@ def set_n(n):
     EVALS_LSCV = pairs(N) * N_H
     EVALS_PSI = 2 * pairs(N)
     EVALS_STEP = EVALS_LSCV + EVALS_PSI
-# LSCV: setup, prologue statistics, whitening, pairs, reduce, finish;
-# PLUGIN: setup, prologue statistics, whitening, 2 x (pairs, finish)
-LAUNCHES_PER_STEP = 6 + 7
+# LSCV: setup, prologue statistics, whitening, pairs, reduce, finish (the
+# n = 65,536 partial table is too large for the pair kernel to finish itself);
+# PLUGIN: setup, prologue statistics, whitening, 2 x pairs (each finished by
+# its last CTA)
+LAUNCHES_PER_STEP = 6 + 5
 
 
 def profiled_lscv_traffic():
@@ -242,13 +246,19 @@ def run_batch(args):
     each LSCV on 128 points over Z(h0) plus PLUGIN, as one graph-captured batch;
     against the plain per-dataset path (one kde_lscv + kde_plugin pair of
     calls per dataset on one stream)."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(batch_measure(args.batch_count, args.steps, args.warmup, args.autotune)), flush=True)
+    return 0
+
+
+def batch_measure(count, steps, warmup, autotune=False):
     import numpy as np
     import torch
 
     from paper_1505_01998_gb300 import datagen, gbkde
 
-    torch.cuda.set_device(0)
-    sets = datagen.batch(args.batch_count, seed=4)
+    sets = datagen.batch(count, seed=4)
     xs = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in sets]
     grid = gbkde.make_grid(n_h=128)[0]
     reqs, keep = [], []
@@ -258,7 +268,7 @@ def run_batch(args):
         keep.append(k)
     evals = sum(pairs(x.shape[1]) * (128 + 2) for x in xs)
     tuned = {}
-    if args.autotune:
+    if autotune:
         # tune the size buckets where geometry matters (n <= 16384); larger
         # datasets fill the GPU on their own and keep the default rules
         by_bucket = {}
@@ -277,10 +287,10 @@ def run_batch(args):
     ws = gbkde.workspace(plan.ws_bytes)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(1, warmup)):
         plan.run(ws)
     ms = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0.record(stream)
         plan.run_async(ws, stream)
         e1.record(stream)
@@ -300,7 +310,7 @@ def run_batch(args):
     plain()
     torch.cuda.synchronize()
     pms = []
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(max(1, steps // 2)):
         e0.record(stream)
         plain()
         e1.record(stream)
@@ -318,99 +328,130 @@ def run_batch(args):
             "bitwise_equal_to_plain": bool(same),
             "statuses_ok": sum(r["status"] == 0 for r in res),
             "autotuned_buckets": tuned}
-    print(json.dumps(line), flush=True)
     plan.close()
-    return 0
+    return line
 
 
 def run_serve(args):
     """Poisson arrivals of selection requests (n log-uniform on [1024, 262144],
-    d = 1 : 2 at 4 : 1, LSCV or PLUGIN half and half, seed 5) at a sweep of
-    rates, served under a 40 GB arena; against the plain path (the same
-    requests, one kde_lscv / kde_plugin call at a time in arrival order)."""
+    d = 1 : 2 at 4 : 1, LSCV or PLUGIN half and half) at a sweep of rates,
+    served under a 40 GB arena; against the plain path (the same requests,
+    one kde_lscv / kde_plugin call at a time in arrival order)."""
+    import torch
+    torch.cuda.set_device(0)
+    out = serve_measure(args.rates, args.serve_count, args.serve_seeds, args.serve_budget_gb,
+                        args.serve_quantum, verbose=True)
+    print(json.dumps(dict({"workload": "serve", "metric": "served selections/s", "unit": "requests/s"}, **out)),
+          flush=True)
+    return 0
+
+
+def serve_measure(rates, count, seeds, budget_gb, quantum, verbose=False, repeat_from_rate=0.0):
+    """Serve `count` requests at each rate for each arrival seed, then the same
+    requests through the plain path.  Per rate: served and plain requests/s,
+    p50 and p99 latency (median and range over the seeds), and agreement of
+    every request's selected bandwidth between the two paths.  Rates below
+    `repeat_from_rate` run the first seed only."""
     import numpy as np
     import torch
 
     from paper_1505_01998_gb300 import datagen, gbkde
 
-    torch.cuda.set_device(0)
     grid = gbkde.make_grid(n_h=128)[0]
-    arena = gbkde.workspace(args.serve_budget_gb << 30)
+    arena = gbkde.workspace(budget_gb << 30)
     stream = torch.cuda.current_stream()
     records = []
-    for rate in args.rates:
-        count = args.serve_count
-        reqs = datagen.serving_requests(rate, count, seed=5)
-        srv = gbkde.Server(arena, max_slots=256, quantum_evals=args.serve_quantum)
-        t0 = time.perf_counter()
-        tickets = []
-        for r in reqs:
-            now = time.perf_counter() - t0
-            if r.arrival_s > now:
-                time.sleep(r.arrival_s - now)
-            m = gbkde.KDE_METHOD_LSCV if r.method == "lscv" else gbkde.KDE_METHOD_PLUGIN
-            tickets.append(srv.submit(r.x, m, grid))
-        failures = []
-        served_res = {}
-        keys = ("sigma", "g1", "psi6", "g2", "psi4", "h", "argmin", "g_min", "logdet_S")
-        for k, t in enumerate(tickets):
-            rc, res = srv.wait(t, 600000)
-            if rc != 0:
-                r = reqs[k]
-                failures.append({"index": k, "status": rc, "n": r.n, "d": r.d, "method": r.method,
-                                 "seed": r.seed, "served": {q: res.get(q) for q in keys}})
-            else:
-                served_res[k] = res
-        st = srv.stats()
-        srv.close()
-        # plain path: arrivals at the same times, served one at a time
-        ws = gbkde.workspace(max(gbkde.kde_workspace_size(r.n, r.d, 128) for r in reqs))
-        lat = []
-        plain_fail = {}
-        plain_res = {}
-        t0 = time.perf_counter()
-        for k, r in enumerate(reqs):
-            now = time.perf_counter() - t0
-            if r.arrival_s > now:
-                time.sleep(r.arrival_s - now)
-            xd = torch.from_numpy(r.x).cuda()
-            try:
-                if r.method == "lscv":
-                    plain_res[k] = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
-                else:
-                    plain_res[k] = gbkde.kde_plugin(xd, None, ws, stream)
-            except gbkde.KdeError as e:
-                plain_fail[k] = e.status
-            lat.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
-        span = time.perf_counter() - t0
-        for f in failures:  # the same request through the single-call path
-            f["plain_status"] = plain_fail.get(f["index"], 0)
-            if f["index"] in plain_res:
-                f["plain"] = {q: plain_res[f["index"]].get(q) for q in keys}
-        # equal accuracy: the selected bandwidth of every request served on both paths
-        both = [k for k in served_res if k in plain_res]
-        h_rel = max((abs(served_res[k]["h"] - plain_res[k]["h"]) / abs(plain_res[k]["h"]) for k in both),
-                    default=0.0)
-        argmin_diff = sum(served_res[k]["argmin"] != plain_res[k]["argmin"] for k in both
-                          if reqs[k].method == "lscv")
-        records.append({"rate": rate, "requests": count, "failures": failures,
-                        "agreement": {"requests": len(both), "max_rel_diff_h": h_rel,
-                                      "lscv_argmin_differs": int(argmin_diff)},
-                        "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
-                                   "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
-                                   "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],
-                                   "steps": st["steps"], "arena_peak_bytes": st["arena_peak_bytes"]},
-                        "plain": {"requests_per_s": count / span,
-                                  "p50_ms": float(np.percentile(lat, 50)),
-                                  "p99_ms": float(np.percentile(lat, 99))}})
-        print(json.dumps(records[-1]), flush=True)
+    for rate in rates:
+        runs = []
+        for seed in (seeds if rate >= repeat_from_rate else seeds[:1]):
+            reqs = datagen.serving_requests(rate, count, seed=seed)
+            runs.append(_serve_once(gbkde, torch, np, reqs, grid, arena, stream, quantum))
+            if verbose:
+                print(json.dumps(dict({"rate": rate, "seed": seed}, **runs[-1])), flush=True)
+        rec = {"rate": rate, "requests": count, "seeds": list(seeds if rate >= repeat_from_rate else seeds[:1])}
+        for side in ("served", "plain"):
+            rec[side] = {}
+            for key in ("requests_per_s", "p50_ms", "p99_ms"):
+                v = [r[side][key] for r in runs]
+                rec[side][key] = statistics.median(v)
+                if len(v) > 1:
+                    rec[side][key + "_range"] = [min(v), max(v)]
+        rec["served"]["active_max"] = max(r["served"]["active_max"] for r in runs)
+        rec["agreement"] = {"requests": sum(r["agreement"]["requests"] for r in runs),
+                            "max_rel_diff_h": max(r["agreement"]["max_rel_diff_h"] for r in runs),
+                            "lscv_argmin_differs": sum(r["agreement"]["lscv_argmin_differs"] for r in runs),
+                            "failures": sum(len(r["failures"]) for r in runs)}
+        records.append(rec)
     best = max(r["served"]["requests_per_s"] for r in records)
     best_plain = max(r["plain"]["requests_per_s"] for r in records)
-    print(json.dumps({"workload": "serve", "metric": "served selections/s", "unit": "requests/s",
-                      "value": best, "plain_path_value": best_plain,
-                      "budget_bytes": args.serve_budget_gb << 30, "quantum_evals": args.serve_quantum,
-                      "rates": records}), flush=True)
-    return 0
+    return {"value": best, "plain_path_value": best_plain, "budget_bytes": budget_gb << 30,
+            "quantum_evals": quantum, "rates": records}
+
+
+def _serve_once(gbkde, torch, np, reqs, grid, arena, stream, quantum):
+    srv = gbkde.Server(arena, max_slots=256, quantum_evals=quantum)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        m = gbkde.KDE_METHOD_LSCV if r.method == "lscv" else gbkde.KDE_METHOD_PLUGIN
+        tickets.append(srv.submit(r.x, m, grid))
+    failures = []
+    served_res = {}
+    keys = ("sigma", "g1", "psi6", "g2", "psi4", "h", "argmin", "g_min", "logdet_S")
+    for k, t in enumerate(tickets):
+        rc, res = srv.wait(t, 600000)
+        if rc != 0:
+            r = reqs[k]
+            failures.append({"index": k, "status": rc, "n": r.n, "d": r.d, "method": r.method,
+                             "seed": r.seed, "served": {q: res.get(q) for q in keys}})
+        else:
+            served_res[k] = res
+    st = srv.stats()
+    srv.close()
+    # plain path: arrivals at the same times, served one at a time
+    ws = gbkde.workspace(max(gbkde.kde_workspace_size(r.n, r.d, 128) for r in reqs))
+    lat = []
+    plain_fail = {}
+    plain_res = {}
+    t0 = time.perf_counter()
+    for k, r in enumerate(reqs):
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        xd = torch.from_numpy(r.x).cuda()
+        try:
+            if r.method == "lscv":
+                plain_res[k] = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
+            else:
+                plain_res[k] = gbkde.kde_plugin(xd, None, ws, stream)
+        except gbkde.KdeError as e:
+            plain_fail[k] = e.status
+        lat.append(1e3 * (time.perf_counter() - t0 - r.arrival_s))
+    span = time.perf_counter() - t0
+    del ws
+    for f in failures:  # the same request through the single-call path
+        f["plain_status"] = plain_fail.get(f["index"], 0)
+        if f["index"] in plain_res:
+            f["plain"] = {q: plain_res[f["index"]].get(q) for q in keys}
+    # equal accuracy: the selected bandwidth of every request served on both paths
+    both = [k for k in served_res if k in plain_res]
+    h_rel = max((abs(served_res[k]["h"] - plain_res[k]["h"]) / abs(plain_res[k]["h"]) for k in both),
+                default=0.0)
+    argmin_diff = sum(served_res[k]["argmin"] != plain_res[k]["argmin"] for k in both
+                      if reqs[k].method == "lscv")
+    return {"failures": failures,
+            "agreement": {"requests": len(both), "max_rel_diff_h": h_rel,
+                          "lscv_argmin_differs": int(argmin_diff)},
+            "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
+                       "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
+                       "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],
+                       "steps": st["steps"], "arena_peak_bytes": st["arena_peak_bytes"]},
+            "plain": {"requests_per_s": len(reqs) / span,
+                      "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99))}}
 
 
 def run_paper(args):
@@ -604,6 +645,24 @@ def run_configs(args):
                     "lscv_roofline_evals_per_s": peak_d, "e2e_ms": e2e_ms,
                     "oracle_evals_per_s": o_pairs * 128 / o_s, "oracle_cores": cores,
                     "oracle_sample": f"rows 0..{rows - 1} of the pair triangle ({o_pairs} pairs, {o_s:.1f} s)"})
+    # LSCV_H minimisation (Nelder-Mead over positive-definite H, Sec. 4.4.3)
+    # of the same d = 2, 3, 4 sets from the normal-scale start
+    for d in (2, 3, 4):
+        x = datagen.correlated_mixture(n, d, seed=3 + d)
+        xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        p = d * (d + 1) // 2
+        ws = gbkde.workspace(max(gbkde.kde_workspace_size(n, d, 1),
+                                 gbkde.kde_lscv_H_workspace_size(n, d, max(4, p + 1))))
+        gbkde.kde_lscv_H_minimize(xd, max_iter=20, ws=ws)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H, g, evals = gbkde.kde_lscv_H_minimize(xd, max_iter=1000, ftol=1e-9, ws=ws)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0)
+        out.append({"config": f"d={d} n=16384 correlated mixture, LSCV_H Nelder-Mead minimisation",
+                    "g_evaluations": evals, "ms": ms, "ms_per_g_evaluation": ms / max(1, evals),
+                    "pair_evals_per_s": evals * P / (ms * 1e-3), "g_min": g,
+                    "H": np.asarray(H).tolist()})
     clocks = sampler.stop()
     print(json.dumps({"workload": "configs", "peak_evals_per_s_2070mhz": peak, "results": out,
                       "clocks": clocks}), flush=True)
@@ -719,6 +778,18 @@ def main():
     ap.add_argument("--serve-quantum", type=float, default=0.0,
                     help="work per scheduling step in direct-kernel evaluations (0 = the library default)")
     ap.add_argument("--rates", type=float, nargs="+", default=[10, 30, 100, 300, 1000, 2000])
+    ap.add_argument("--serve-seeds", type=int, nargs="+", default=[5],
+                    help="arrival seeds per rate (the serve workload reports median and range)")
+    ap.add_argument("--rates-extra", type=float, nargs="+", default=[30, 100, 2000],
+                    help="selection workload: serving rates of the line's serve object")
+    ap.add_argument("--serve-count-extra", type=int, default=200)
+    ap.add_argument("--serve-seeds-extra", type=int, nargs="+", default=[5, 6, 7])
+    ap.add_argument("--shard", action="store_true",
+                    help="selection workload: split one selection over the ranks (tile ranges + "
+                         "NCCL all-reduce, strong scaling) instead of one replica per rank")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="selection workload: skip the error, plain-precision, serving and batch "
+                         "sub-measurements (profiling runs)")
     args = ap.parse_args()
     set_n(args.n)
     world, rank, local = dist_env()
@@ -734,7 +805,170 @@ def main():
         return run_consumers(args)
     if args.workload == "configs":
         return run_configs(args)
+    if args.shard:
+        return run_shard(args, world, rank, local)
     return run_gpu(args, world, rank, local)
+
+
+def kernel_event_pair(stream):
+    """Two timing events recorded once on `stream`, so that torch treats them
+    as recorded; kde_set_kernel_events then re-records them around a kernel."""
+    import torch
+    e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    e[0].record(stream)
+    e[1].record(stream)
+    return e
+
+
+def selection_errors(gbkde, xd, grid, opts, ws_l, ws_p):
+    """Error of the selection left in the workspaces against the FP64 oracle
+    over all pairs of the same samples (tests/golden/skewed65536_oracle.json,
+    written by the oracle alone): g(h) at every grid point relative to
+    max(|g|, its positive-term scale), S1 and S2 relative, the argmin, and the
+    PLUGIN chain relative."""
+    import numpy as np
+
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "skewed65536_oracle.json")))
+    r_l, g = gbkde.read_ws_result(ws_l, N_H)
+    r_p, _ = gbkde.read_ws_result(ws_p)
+    h = np.asarray(gold["h"])
+    s_kk, s_k, g_ref = (np.asarray(gold[k]) for k in ("s_kk", "s_k", "g"))
+    T = gbkde.kde_item_tiles(N, 1, N_H, opts)["lscv_tile"]
+    s1, s2 = gbkde.kde_lscv_tile_sums(xd, h, 0, gbkde.kde_tile_count(N, T), opts)
+    A = (4 * math.pi) ** -0.5 / gold["plugin"]["sigma"]
+    scale = A * h ** -1.0 * (2.0 / N ** 2 * (s_kk + 2 ** 1.5 * s_k) + 1.0 / N)
+    g_err = np.abs(g - g_ref) / np.maximum(np.abs(g_ref), scale)
+    floor = pairs(N) * 2.0 ** -126
+    rel = lambda a, b: abs(a - b) / abs(b)
+    k_ref = int(gold["argmin"])
+    return {"vs": "FP64 oracle over all 2.1e9 pairs of the same samples (tests/golden/skewed65536_oracle.json)",
+            "tolerance": 1e-5,
+            "lscv_g_max": float(g_err.max()),
+            "lscv_s1_max_rel": float((np.abs(s1 - s_kk) / np.maximum(s_kk, floor)).max()),
+            "lscv_s2_max_rel": float((np.abs(s2 - s_k) / np.maximum(s_k, floor)).max()),
+            "lscv_argmin": int(r_l["argmin"]), "oracle_argmin": k_ref,
+            "lscv_argmin_same": int(r_l["argmin"]) == k_ref,
+            "lscv_h_rel": rel(r_l["h"], h[k_ref]),
+            "psi6_rel": rel(r_p["psi6"], gold["plugin"]["psi6"]),
+            "g2_rel": rel(r_p["g2"], gold["plugin"]["g2"]),
+            "psi4_rel": rel(r_p["psi4"], gold["plugin"]["psi4"]),
+            "plugin_h_rel": rel(r_p["h"], gold["plugin"]["h"])}
+
+
+def selection_extras(args, xd, grid, opts, ws_l, ws_p, stream, flush, probe, sm_mhz):
+    """Sub-measurements of the default line, outside its timed region: errors
+    of the timed selection against the FP64 oracle, the same selection with
+    plain FP32 per-thread sums (time and errors), the serving sweep and the
+    512-dataset batch."""
+    import torch
+
+    from paper_1505_01998_gb300 import gbkde
+
+    out = {"errors": selection_errors(gbkde, xd, grid, opts, ws_l, ws_p)}
+    # plain FP32 sums: same kernels without compensation
+    po = gbkde.make_opts(precision=gbkde.KDE_FP32_PLAIN)
+    wl = gbkde.workspace(gbkde.kde_workspace_size(N, 1, N_H, po))
+    wp = gbkde.workspace(gbkde.kde_workspace_size(N, 1, 0, po))
+    for _ in range(2):
+        gbkde.kde_lscv_async(xd, grid, po, wl, stream)
+        gbkde.kde_plugin_async(xd, po, wp, stream)
+    torch.cuda.synchronize()
+    kms, sms = [], []
+    for _ in range(5):
+        flush.zero_()
+        k0, k1 = kernel_event_pair(stream)
+        e = [torch.cuda.Event(enable_timing=True), k0, k1, torch.cuda.Event(enable_timing=True)]
+        e[0].record(stream)
+        gbkde.kde_set_kernel_events(e[1], e[2])
+        gbkde.kde_lscv_async(xd, grid, po, wl, stream)
+        gbkde.kde_set_kernel_events()
+        gbkde.kde_plugin_async(xd, po, wp, stream)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        kms.append(e[1].elapsed_time(e[2]))
+        sms.append(e[0].elapsed_time(e[3]))
+    km = statistics.median(kms)
+    out["plain"] = {"precision": "fp32 terms, plain fp32 per-thread sums, fp64 reductions",
+                    "lscv_kernel_ms": km, "lscv_kernel_evals_per_s": EVALS_LSCV / (km * 1e-3),
+                    "selection_ms": statistics.median(sms),
+                    "selection_evals_per_s": EVALS_STEP / (statistics.median(sms) * 1e-3),
+                    "errors": selection_errors(gbkde, xd, grid, po, wl, wp)}
+    del wl, wp
+    t0 = time.perf_counter()
+    out["serve"] = serve_measure(args.rates_extra, args.serve_count_extra, args.serve_seeds_extra,
+                                 args.serve_budget_gb, args.serve_quantum, repeat_from_rate=100.0)
+    out["serve"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out["batch"] = batch_measure(args.batch_count, 2, 1)
+    out["batch"]["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def run_shard(args, world, rank, local):
+    """One selection (LSCV_h + PLUGIN of the n = 65,536 skewed column) split
+    over the ranks: every rank evaluates a contiguous range of the pair
+    tiles, then one NCCL all-reduce per all-pairs pass (2 n_h values for
+    LSCV_h, one each for psi_6 and psi_4).  Strong scaling: the job is one
+    selection whatever the rank count; value = its evaluations / the slowest
+    rank's time per step (host clock between barriers: every step ends with
+    host-side merges)."""
+    import numpy as np
+    import torch
+
+    from paper_1505_01998_gb300 import datagen, gbkde
+    from paper_1505_01998_gb300.shard import sharded_lscv, sharded_plugin
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    x = datagen.skewed_column(N, seed=SEED)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    h = gbkde.kde_default_grid(N, 1, N_H)
+
+    def step():
+        res_l, _ = sharded_lscv(xd, h)
+        res_p = sharded_plugin(xd)
+        return res_l, res_p
+
+    W, K = max(3, args.warmup), args.steps
+    for _ in range(W):
+        res_l, res_p = step()
+    sampler = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        res_l, res_p = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_s = time.perf_counter() - t0
+    clocks = sampler.stop()
+    if dist:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    ms = 1e3 * total_s / K
+    line = {"metric": METRIC, "value": EVALS_STEP / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + ", one selection sharded over the ranks", "n": N, "d": 1,
+                       "n_h": N_H, "evals_per_step": EVALS_STEP, "seed": SEED,
+                       "parallelism": f"tile-range shards x{world}, NCCL all-reduce of 2 n_h + 2 FP64 values",
+                       "timing": "host clock between barriers (steps end with host merges)"},
+            "clocks": clocks,
+            "result": {"lscv_argmin": res_l["argmin"], "lscv_h": res_l["h"], "plugin_h": res_p["h"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
 
 
 def run_gpu(args, world, rank, local):
@@ -852,7 +1086,10 @@ def run_gpu(args, world, rank, local):
         e2e_s = float(t.item())
     e2e_value = EVALS_STEP * world * K / e2e_s
     h2d = 2 * N * 4
-    d2h = 2 * 128 + N_H * 8  # two kde_result structs + g[n_h]
+    # LSCV: one copy of the workspace span from the result to the end of g[n_h];
+    # PLUGIN: the result struct
+    r_off, g_off = gbkde.kde_ws_result_offset()
+    d2h = (g_off + 8 * N_H - r_off) + ctypes.sizeof(gbkde.kde_result)
 
     # ---- roofline of the dominant kernel (all-pairs LSCV)
     sm_mhz = (clocks or {}).get("sm_mhz") or probe["sm_mhz"]
@@ -877,6 +1114,15 @@ def run_gpu(args, world, rank, local):
                     "frac": EVALS_LSCV / (closed_kernel_ms * 1e-3) / 1e9
                     / (lscv_per_clk(probe, 1, False) * probe["sm_count"] * sm_mhz * 1e6 / 1e9)}}
 
+    # ratio to the basis of one MUFU ex2 per evaluation (the direct kernel's
+    # bound): above 1 on the default grid, whose octave shape lets most
+    # exponentials be formed by squaring
+    roofline["frac_vs_one_ex2_basis"] = achieved / (probe["mufu_ex2_per_clk_sm"] * probe["sm_count"] * sm_mhz * 1e6 / 1e9)
+
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras and N == 65536:
+        extras = selection_extras(args, xd, grid, opts, ws_l, ws_p, stream, flush, probe, sm_mhz)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -893,6 +1139,7 @@ def run_gpu(args, world, rank, local):
             "roofline": roofline, "clocks": clocks,
             "alu_probe": probe,
             "result": {"lscv_argmin": r_l["argmin"], "lscv_h": r_l["h"], "plugin_h": r_p["h"]}}
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(args.cpu_seconds)
         cb.pop("seconds")
