@@ -483,3 +483,47 @@ def test_octave_kernel_against_direct_kernel_and_oracle(kde, d, n, n_h):
     npairs = n * (n - 1) // 2
     assert s_err(s1, ref["s_kk"], npairs).max() < TOL
     assert s_err(s2, ref["s_k"], npairs).max() < TOL
+
+
+def test_largest_grid_octave_kernel(kde):
+    """The largest grid (1,024 points, 128 per octave of 1/h^2) on the octave
+    kernel, against the oracle."""
+    n, d = 1500, 1
+    x = datagen.mixture_1d(n, seed=611)
+    x64 = host64(x)
+    h = oracle.grid_default(n, d, 1024)
+    res, g, hh = kde.kde_lscv(dev(x), kde.make_grid(n_h=1024)[0])
+    assert np.allclose(hh, h, rtol=1e-14)
+    ref = oracle.lscv_h(x64, h)
+    assert g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, lscv_A(x64)).max() < TOL
+    assert argmin_ok(res["argmin"], ref["g"], TOL * np.max(np.abs(ref["g"])))
+
+
+@pytest.mark.parametrize("log2_end,top", [(19.9, True), (21.0, True), (-19.9, False), (-21.0, False)])
+def test_octave_grids_at_the_ends_of_the_exponent_add_range(kde, log2_end, top):
+    """Octave-shaped grids (4 points per octave of 1/h^2) whose largest (top)
+    or smallest h sits just inside or just outside [2^-20, 2^20]: inside, the
+    octave kernel forms two of its three arguments by exponent adds and masks
+    pairs with a finite squared distance (at h near 2^20 every real term is
+    about 1 and a masked pair that leaked would add 1); outside, the direct
+    kernel runs.  Both against the oracle (Eq. LSCV-gh).  At the small end
+    the samples are evenly spaced (every pair at least 1.6e-3 sigma apart):
+    near-duplicates of random samples would put g at the mercy of the FP32
+    rounding of their whitened coordinates (h ~ 1e-6 sigma), a limit of the
+    FP32 pair path rather than of the kernel's arithmetic."""
+    n, d, n_h, P = 2100, 1, 16, 4
+    x = datagen.mixture_1d(n, seed=612) if top else \
+        datagen.rng(613).permutation(np.arange(n, dtype=np.float64))[None, :]
+    x64 = host64(x)
+    k = np.arange(n_h)
+    expo = log2_end - (n_h - 1 - k) / (2.0 * P) if top else log2_end + k / (2.0 * P)
+    h = 2.0 ** expo
+    res, g, hh = kde.kde_lscv(dev(x), _explicit(kde, h))
+    ref = oracle.lscv_h(x64, h)
+    assert g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, lscv_A(x64)).max() < TOL
+    s1, s2 = kde.kde_lscv_tile_sums(dev(x), h, 0, kde.kde_tile_count(n, kde.kde_item_tiles(n, d, n_h)["lscv_tile"]))
+    npairs = n * (n - 1) // 2
+    assert s_err(s1, ref["s_kk"], npairs).max() < TOL
+    assert s_err(s2, ref["s_k"], npairs).max() < TOL
+    if top:
+        assert np.all(s1 <= npairs * (1 + 1e-6))  # no masked pair counted
