@@ -226,12 +226,14 @@ int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, 
                    const double* s2, double* g_out, kde_result* out);
 
 /* Tile edge and tiles per work item of the single-GPU geometry for n
- * samples in d dimensions and n_h bandwidths (the LSCV pair kernel) and of
- * the psi kernels, on the current device with the given options (NULL =
- * defaults).  Shards whose tile ranges start on multiples of the item size
- * evaluate exactly the items of the single launch.  Any output may be NULL. */
-int kde_item_tiles(int64_t n, int d, int n_h, const kde_opts* opts, int* lscv_tile, int* lscv_K,
-                   int* psi_tile, int* psi_K);
+ * samples in d dimensions on the LSCV grid h[n_h] (NULL: the default grid of
+ * n_h points; the grid's shape picks the octave or the direct kernel, whose
+ * item sizes differ) and of the psi kernels, on the current device with the
+ * given options (NULL = defaults).  Shards whose tile ranges start on
+ * multiples of the item size evaluate exactly the items of the single
+ * launch.  Any output may be NULL. */
+int kde_item_tiles(int64_t n, int d, const double* h, int n_h, const kde_opts* opts, int* lscv_tile,
+                   int* lscv_K, int* psi_tile, int* psi_K);
 
 /* Bracketing search for argmin g(h) over [h_lo, h_hi] (<= 0: Z(h0), Eq.
  * LSCV-Zh0): the golden-section alternative to the dense grid named in

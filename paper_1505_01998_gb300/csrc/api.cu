@@ -110,13 +110,20 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->n_pad = (int64_t)align_up((size_t)n, kPadTo);
   g->kahan = !(o && o->precision == KDE_FP32_PLAIN);
   g->cv_loo = (o && o->cv == KDE_CV_LOO) ? 1 : 0;
-  const int cps = (o && o->ctas_per_sm) ? o->ctas_per_sm : 2;
+  const bool cps_given = o && o->ctas_per_sm;
+  const int cps = cps_given ? o->ctas_per_sm : 2;
   g->ctas = std::max(1, sms) * cps;
   g->oct_P = 0;
   // LSCV
   g->T = (o && o->tile) ? o->tile : (n <= 2048 ? 32 : 128);
   if (g->dk > 4) g->T = 32;  // one row per lane keeps the d > 4 coordinates in registers
   g->R = g->T / 32;
+  g->ctas_oct = g->ctas;
+  // items: with the default CTA counts about 12 per SM (6 per CTA at 2 CTAs
+  // per SM, 4 at 3), with an explicit count, or for the server's capped
+  // items (a step spans many requests), about 4 per CTA
+  const bool balanced = !cps_given && !(max_item_evals > 0);
+  g->item_target = balanced ? 12 * (int64_t)std::max(1, sms) : 4 * (int64_t)g->ctas;
   // a one- or two-point grid (one g(H) of LSCV_H is a one-point grid) takes 2
   // bandwidths per thread unless the caller asked otherwise, whatever the
   // tuner chose for its size bucket: 8 would evaluate 6 padding bandwidths
@@ -132,19 +139,61 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->G = (g->n_chunks + kWarps - 1) / kWarps;
   if (check_warp_roles(g->T) != KDE_OK) return fail(KDE_EINTERNAL, "warp roles inconsistent for T = %d", g->T);
   g->tiles = tri_tiles(n, g->T);
+  const int64_t kcap = (max_item_evals > 0 && !(o && o->tiles_per_item))
+                           ? std::max<int64_t>(1, (int64_t)(max_item_evals / ((double)g->T * g->T *
+                                                                            std::min(g->n_h_pad, kWarps * g->B))))
+                           : 4096;
   if (o && o->tiles_per_item) {
     g->K = o->tiles_per_item;
   } else {
-    // block items: about 4 per CTA; warp items (equal tile counts, one per
+    // block items: item_target; warp items (equal tile counts, one per
     // warp) keep the partial rows, and so the reduction, short
-    const int64_t target = lscv_warp_items(g->dk, g->B) ? (int64_t)g->ctas * kWarps : 4 * (int64_t)g->ctas;
+    const int64_t target = lscv_warp_items(g->dk, g->B) ? (int64_t)g->ctas * kWarps : g->item_target;
     g->K = (int)std::min<int64_t>(4096, kscale * std::max<int64_t>(1, (g->tiles * g->G + target - 1) / target));
   }
-  if (max_item_evals > 0 && !(o && o->tiles_per_item)) {
-    const double per_tile = (double)g->T * g->T * std::min(g->n_h_pad, kWarps * g->B);
-    g->K = (int)std::max<int64_t>(1, std::min<int64_t>(g->K, (int64_t)(max_item_evals / per_tile)));
+  g->K = (int)std::min<int64_t>(g->K, kcap);
+  g->K_oct = g->K;
+  if (balanced && !(o && o->tiles_per_item) && !lscv_warp_items(g->dk, g->B)) {
+    // Items are walked in grid-stride order by persistent CTAs, so the last
+    // wave is full only when the item count is (nearly) a multiple of the
+    // CTA count.  Tiles per item are chosen within a factor 2 of the rule
+    // above for the best balance, separately for the direct kernel (2 CTAs
+    // per SM) and the octave kernel, which takes 3 CTAs per SM (d <= 4)
+    // when that balances at least as well as 2.
+    const int64_t work = g->tiles;
+    auto balance = [&](int64_t K, int64_t C) {
+      const int64_t items = (work + K - 1) / K * g->G;
+      return (double)items / ((double)C * (double)((items + C - 1) / C));
+    };
+    auto best_k = [&](int64_t C, double* eff) {
+      const int64_t k0 = g->K;
+      int64_t best = k0;
+      double be = balance(k0, C);
+      for (int64_t K = std::max<int64_t>(1, k0 / 2); K <= std::min<int64_t>(kcap, 2 * k0); ++K) {
+        const double e = balance(K, C);
+        if (e > be + 1e-12 || (e > be - 1e-12 && K > best)) {
+          best = K;
+          be = e;
+        }
+      }
+      *eff = be;
+      return (int)best;
+    };
+    const int64_t S = std::max(1, sms);
+    double e2 = 0, e3 = 0;
+    const int k2 = best_k(2 * S, &e2);
+    g->K = k2;
+    g->K_oct = k2;
+    if (oct_ctas_per_sm(g->dk) == 3) {
+      const int k3 = best_k(3 * S, &e3);
+      if (e3 >= e2) {
+        g->K_oct = k3;
+        g->ctas_oct = (int)(3 * S);
+      }
+    }
   }
   g->rows = (g->tiles + g->K - 1) / g->K;
+  g->rows_oct = (g->tiles + g->K_oct - 1) / g->K_oct;
   g->items = g->rows * g->G;
   // psi
   g->Tp = n >= 16384 ? 256 : 64;
@@ -178,7 +227,7 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->off_xc = o0;
   o0 = align_up(o0 + (size_t)g->n_pad * sizeof(float), 256);
   g->off_lpart = o0;
-  o0 = align_up(o0 + (n_h > 0 ? (size_t)g->rows * 2 * g->n_h_pad * sizeof(double) : 0), 256);
+  o0 = align_up(o0 + (n_h > 0 ? (size_t)std::max(g->rows, g->rows_oct) * 2 * g->n_h_pad * sizeof(double) : 0), 256);
   g->off_ppart = o0;
   o0 = align_up(o0 + (size_t)g->prows * sizeof(double), 256);
   g->prep_parts = prep_parts_for(n);
@@ -251,6 +300,9 @@ void apply_octave(Geometry* g, const std::vector<double>& h) {
     if (!(std::fabs(r - 2.0) <= 1e-12)) return;
   }
   g->oct_P = P;
+  g->K = g->K_oct;  // the octave kernel's item size and rows (the workspace holds either)
+  g->rows = g->rows_oct;
+  g->items = g->rows * g->G;
 }
 
 // Descriptor for one selection on workspace `ws` laid out by `g`.
@@ -464,7 +516,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   // (saves two launches); large ones keep the many-CTA reduction
   const bool fuse = !lscv_warp_items(g.dk, g.B) && g.rows * 2 * (int64_t)g.n_h_pad <= kFuseMaxPartials;
   ph.fuse = fuse ? 1 : 0;
-  const int grid = (int)std::min<int64_t>(g.items, g.ctas);
+  const int grid = (int)std::min<int64_t>(g.items, g.oct_P > 0 ? g.ctas_oct : g.ctas);
   CK(mark(0, st));
   CK(launch_lscv(ph, g.dk, g.B, g.R, g.kahan, g.oct_P > 0, std::max(grid, 1), st));
   CK(mark(1, st));

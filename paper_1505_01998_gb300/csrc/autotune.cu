@@ -64,9 +64,9 @@ double pairs_in_tiles(int64_t n, int T, int64_t tb, int64_t te) {
   return p;
 }
 
-// The default tiles-per-item rule (about 4 items per persistent CTA).
+// The default tiles-per-item rule (make_geometry's item target).
 int64_t base_k(const Geometry& g) {
-  const int64_t target = 4 * (int64_t)g.ctas;
+  const int64_t target = g.item_target;
   return std::max<int64_t>(1, (g.tiles * g.G + target - 1) / target);
 }
 

@@ -258,7 +258,9 @@ static int batch_enqueue(kde_batch_plan* p, unsigned char* ws, cudaStream_t st) 
   BK(mark_event(0, st));
   for (auto& G : p->lscv_groups) {
     Phase ph{ds, offs + k * (n + 1), nullptr, n, 0, G.total};
-    BK(launch_lscv(ph, G.d, G.B, G.R, G.kahan, G.oct, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, ctas)), st));
+    const bool cps_given = p->has_opts && p->opts.ctas_per_sm;
+    const int gctas = (G.oct && !cps_given) ? std::max(1, p->sms) * oct_ctas_per_sm(G.d) : ctas;
+    BK(launch_lscv(ph, G.d, G.B, G.R, G.kahan, G.oct, (int)std::max<int64_t>(1, std::min<int64_t>(G.total, gctas)), st));
     ++k;
   }
   BK(mark_event(1, st));

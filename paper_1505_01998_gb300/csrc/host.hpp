@@ -18,7 +18,11 @@ struct Geometry {
   int64_t n_pad;
   bool kahan;
   int cv_loo;  // KDE_CV_LOO requested
-  int ctas;  // persistent CTAs of the pair kernels
+  int ctas;      // persistent CTAs of the pair kernels
+  int ctas_oct;  // persistent CTAs of the octave LSCV kernel (2 or 3 per SM)
+  int K_oct;     // tiles per item of the octave LSCV kernel (apply_octave switches to it)
+  int64_t rows_oct;
+  int64_t item_target;  // LSCV block items aimed at (the tiles-per-item rule)
   // LSCV: tile T = 32 R, B bandwidths per thread, K tiles per item
   int T, R, B, n_h_pad, n_chunks, G, K;
   int64_t tiles, rows, items;
@@ -48,6 +52,12 @@ DsDev make_desc(const Geometry& g, const void* x, int dtype, int methods, unsign
 // multiple of 16 (n_h / 8 points per octave of 1/h^2, to 1e-12) and g already
 // takes 16 bandwidths per thread; the workspace layout does not change.
 void apply_octave(Geometry* g, const std::vector<double>& h);
+
+// CTAs per SM the octave LSCV kernel can hold for dk coordinates: its d <= 4
+// instances fit 3 (80 registers), the others 2.  Batches and the server use
+// it when the caller gave no CTA count; single calls choose 2 or 3 by the
+// balance of their items (make_geometry).
+inline int oct_ctas_per_sm(int dk) { return dk <= 4 ? 3 : 2; }
 PsiCoef psi_coef(int r);
 
 // Records the caller's timing event k (kde_set_kernel_events) on `st`, if set.

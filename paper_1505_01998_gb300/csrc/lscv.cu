@@ -493,8 +493,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
   }
 }
 
+// octave instances for d <= 4 are capped at 80 registers: 3 CTAs per SM
+// (wide ones spill there and keep 2)
 template <int D, int B, int R, bool KAHAN, bool OCT>
-__global__ void __launch_bounds__(kThreads, 2) k_lscv(Phase ph) {
+__global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phase ph) {
   constexpr int T = 32 * R;
   constexpr int DP = DPad<D>::value;
   constexpr int FB = T * DP * (kPackedQ<D, R, OCT> ? 8 : 4);  // column tile bytes

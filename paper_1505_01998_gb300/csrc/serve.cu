@@ -510,7 +510,9 @@ bool launch_step(kde_server* s, int* err) {
     forked[k] = true;
     Phase ph{table, reinterpret_cast<const int64_t*>(dparams + goff[i].first),
              reinterpret_cast<const int64_t*>(dparams + goff[i].second), S, 0, g.total};
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total, ctas));
+    const bool cps_given = s->has_opts && s->opts.ctas_per_sm;
+    const int gctas = (g.kind == P_LSCV && g.oct && !cps_given) ? std::max(1, s->sms) * oct_ctas_per_sm(g.d) : ctas;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.total, gctas));
     if (g.kind == P_LSCV)
       ck(launch_lscv(ph, g.d, g.B, g.R, g.kahan, g.oct, grid, ss), "lscv");
     else

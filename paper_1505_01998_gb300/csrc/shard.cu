@@ -95,8 +95,8 @@ int kde_lscv_merge(int64_t n, int d, double logdet_S, const double* h, int n_h, 
   return KDE_OK;
 }
 
-int kde_item_tiles(int64_t n, int d, int n_h, const kde_opts* opts, int* lscv_tile, int* lscv_K,
-                   int* psi_tile, int* psi_K) {
+int kde_item_tiles(int64_t n, int d, const double* h, int n_h, const kde_opts* opts, int* lscv_tile,
+                   int* lscv_K, int* psi_tile, int* psi_K) {
   if (n < 2 || d < 1 || d > KDE_MAX_D || n_h < 0 || n_h > KDE_MAX_NH)
     return fail(KDE_EINVAL, "kde_item_tiles: bad sizes");
   int rc = check_opts(opts);
@@ -104,6 +104,15 @@ int kde_item_tiles(int64_t n, int d, int n_h, const kde_opts* opts, int* lscv_ti
   Geometry g;
   rc = make_geometry(n, d, n_h, opts, device_sms(), &g);
   if (rc) return rc;
+  if (n_h > 0) {  // the grid decides between the octave and the direct kernel
+    std::vector<double> grid(n_h);
+    if (h) {
+      for (int k = 0; k < n_h; ++k) grid[k] = h[k];
+    } else {
+      kde_default_grid(n, d, n_h, grid.data());
+    }
+    apply_octave(&g, grid);
+  }
   if (lscv_tile) *lscv_tile = g.T;
   if (lscv_K) *lscv_K = g.K;
   if (psi_tile) *psi_tile = g.Tp;

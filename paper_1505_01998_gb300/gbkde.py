@@ -131,7 +131,7 @@ SIGNATURES = {
     "kde_autotune_load": (_I, [ctypes.c_char_p]),
     "kde_lscv_merge": (_I, [_L, _I, _D, _DP, _I, _DP, _DP, _DP, ctypes.POINTER(kde_result)]),
     "kde_plugin_merge": (_I, [_L, _I, _D, ctypes.POINTER(kde_result)]),
-    "kde_item_tiles": (_I, [_L, _I, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int),
+    "kde_item_tiles": (_I, [_L, _I, _DP, _I, ctypes.POINTER(kde_opts), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int)]),
 }
@@ -241,11 +241,15 @@ def kde_plugin_merge(n: int, stage: int, value: float, res: dict | None = None) 
     return r.as_dict()
 
 
-def kde_item_tiles(n: int, d: int, n_h: int, opts: kde_opts | None = None) -> dict:
-    """Tile edges and tiles per item of the single-GPU geometry."""
+def kde_item_tiles(n: int, d: int, n_h: int, opts: kde_opts | None = None, h=None) -> dict:
+    """Tile edges and tiles per item of the single-GPU geometry on the grid h
+    (None: the default grid of n_h points)."""
     v = [ctypes.c_int(0) for _ in range(4)]
-    _check(lib().kde_item_tiles(int(n), int(d), int(n_h), ctypes.byref(opts) if opts else None,
-                                *(ctypes.byref(x) for x in v)))
+    hh = None if h is None else np.ascontiguousarray(np.asarray(h, dtype=np.float64).ravel())
+    if hh is not None:
+        n_h = hh.size
+    _check(lib().kde_item_tiles(int(n), int(d), _dp(hh) if hh is not None else None, int(n_h),
+                                ctypes.byref(opts) if opts else None, *(ctypes.byref(x) for x in v)))
     return {"lscv_tile": v[0].value, "lscv_K": v[1].value, "psi_tile": v[2].value, "psi_K": v[3].value}
 
 

@@ -61,9 +61,9 @@ def sharded_lscv(x, h, opts=None, group=None, tile: int | None = None):
     h = np.ascontiguousarray(np.asarray(h, dtype=np.float64))
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     rank = dist.get_rank(group) if dist.is_initialized() else 0
-    geo = gbkde.kde_item_tiles(n, d, h.size, opts)
+    geo = gbkde.kde_item_tiles(n, d, h.size, opts, h=h)
     T = tile or geo["lscv_tile"]
-    K = shard_item_tiles(n, d, h.size, opts)
+    K = shard_item_tiles(n, d, h.size, opts, h=h)
     b, e = tile_shards(gbkde.kde_tile_count(n, T), world, K)[rank]
     s1, s2 = gbkde.kde_lscv_tile_sums(x, h, b, e, opts)
     s = allreduce_sum(np.concatenate([s1, s2]), group)
@@ -71,13 +71,14 @@ def sharded_lscv(x, h, opts=None, group=None, tile: int | None = None):
     return gbkde.kde_lscv_merge(n, d, logdet, h, s[: h.size], s[h.size:])
 
 
-def shard_item_tiles(n: int, d: int, n_h: int, opts=None) -> int:
-    """Tiles per LSCV item of the single-GPU geometry (explicit in opts, else
-    the library's rule for this size on this device)."""
+def shard_item_tiles(n: int, d: int, n_h: int, opts=None, h=None) -> int:
+    """Tiles per LSCV item of the single-GPU geometry on the grid h (None:
+    the default grid of n_h points): explicit in opts, else the library's
+    rule for this size and grid on this device."""
     if opts is not None and opts.tiles_per_item:
         return int(opts.tiles_per_item)
     from . import gbkde
-    return int(gbkde.kde_item_tiles(n, d, n_h, opts)["lscv_K"])
+    return int(gbkde.kde_item_tiles(n, d, n_h, opts, h=h)["lscv_K"])
 
 
 def sharded_plugin(x, opts=None, group=None):

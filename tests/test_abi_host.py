@@ -248,7 +248,7 @@ def test_entry_points_reject_bad_arguments_before_any_launch(kde):
     # the merge steps of sharded selections check their arguments on the host
     assert L.kde_plugin_merge(1, 8, 1.0, ctypes.byref(res)) == kde.KDE_EINVAL
     assert L.kde_plugin_merge(100, 8, float("nan"), ctypes.byref(res)) == kde.KDE_EINVAL
-    assert L.kde_item_tiles(100, 0, 8, None, None, None, None, None) == kde.KDE_EINVAL
+    assert L.kde_item_tiles(100, 0, None, 8, None, None, None, None, None) == kde.KDE_EINVAL
     # a log grid with a non-positive bound
     g3 = kde.kde_grid(kde.KDE_GRID_LOG, 8, None, -1.0, 2.0)
     assert L.kde_lscv(dummy, 0, 100, 1, ctypes.byref(g3), None, dummy, 1 << 20, None, None, None,

@@ -84,8 +84,8 @@ def test_default_shards_fall_on_item_boundaries():
     single, g1, _ = kde.kde_lscv(xd, kde.make_grid(h=h)[0])
     res, g = sharded_lscv(xd, h)
     assert np.allclose(g, g1, rtol=1e-12, atol=0) and res["argmin"] == single["argmin"]
-    geo = gbkde.kde_item_tiles(n, d, h.size)
-    assert shard_item_tiles(n, d, h.size) == geo["lscv_K"]
+    geo = gbkde.kde_item_tiles(n, d, h.size, h=h)
+    assert shard_item_tiles(n, d, h.size, h=h) == geo["lscv_K"]
     s1 = np.zeros(h.size)
     s2 = np.zeros(h.size)
     for b, e in tile_shards(kde.kde_tile_count(n, geo["lscv_tile"]), 4, geo["lscv_K"]):
