@@ -45,13 +45,8 @@ struct DPad {
 // Measured at n = 16,384 with 128 bandwidths: d = 4 +2 %; d = 3 no change and
 // d = 2 -2.4 % (its scalar path walks two columns per 16-byte load), so only
 // d = 4 takes it.
-// The octave kernel (d <= 4, 4 rows per lane) can take the same packed form
-// for its squared distances, two rows per FP32x2 operation.  Measured on the
-// full-size launch it was within 1 % of the scalar form, so it is off.
-constexpr bool oct_packed_q(int d) { return d < 0; }
-
 template <int D, int R, bool OCT = false>
-constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT) || (OCT && R == 4 && oct_packed_q(D));
+constexpr bool kPackedQ = (R == 4 && D == 4 && !OCT);
 
 // Wide samples (d > 4, one row per lane; the column tile holds -v): the
 // squared distance to column `col` in packed FP32x2 over coordinate pairs,
@@ -261,54 +256,6 @@ __device__ __forceinline__ void lscv_columns_oct(const float* __restrict__ sF, i
                                                  const float (&y)[R][D], const float2 (&nca)[3],
                                                  float2 (&acc)[9], int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
-  if constexpr (kPackedQ<D, R, true>) {
-    // sF holds (-v, -v) per coordinate: rows 2p and 2p + 1 of the lane take
-    // their squared distances to a column in one FP32x2 chain; terms are
-    // accumulated in the same order as below (columns, then rows)
-    const float2* __restrict__ sF2 = reinterpret_cast<const float2*>(sF);
-    float2 y2[R / 2][D];
-#pragma unroll
-    for (int p = 0; p < R / 2; ++p)
-#pragma unroll
-      for (int k = 0; k < D; ++k) y2[p][k] = make_float2(y[2 * p][k], y[2 * p + 1][k]);
-    constexpr int CP = DP == 1 ? 2 : 1;  // columns per 16-byte load (d = 1) or per iteration
-#pragma unroll 1
-    for (int jj = j_lo; jj < j_hi; jj += CP) {
-      float2 nv[CP][DP];
-      if constexpr (DP == 1) {
-        const float4 v = *reinterpret_cast<const float4*>(sF2 + jj);
-        nv[0][0] = make_float2(v.x, v.y);
-        nv[1][0] = make_float2(v.z, v.w);
-      } else {
-#pragma unroll
-        for (int u = 0; u < DP / 2; ++u) {
-          const float4 v = reinterpret_cast<const float4*>(sF2 + jj * DP)[u];
-          nv[0][2 * u] = make_float2(v.x, v.y);
-          nv[0][2 * u + 1] = make_float2(v.z, v.w);
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < CP; ++c)
-#pragma unroll
-        for (int p = 0; p < R / 2; ++p) {
-          float2 q = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < D; ++k) {
-            const float2 dl = __fadd2_rn(y2[p][k], nv[c][k]);
-            q = __ffma2_rn(dl, dl, q);
-          }
-          float qa = q.x, qb = q.y;
-          if (EDGE) {
-            const int64_t ia = i0 + 64 * p, ib = ia + 32, j = jg0 + jj + c;
-            if (!(ia < j && j < n)) qa = kOctMask;  // every term exactly 0
-            if (!(ib < j && j < n)) qb = kOctMask;
-          }
-          octave_terms(qa, nca, acc);
-          octave_terms(qb, nca, acc);
-        }
-    }
-    return;
-  }
   if constexpr (D > 4) {
     // wide samples, one row per lane (sF holds -v): two columns per
     // iteration, each squared distance in packed FP32x2 over coordinate
@@ -956,7 +903,7 @@ cudaError_t launch_b(const Phase& ph, int B, int R, bool kahan, bool oct, int gr
 
 size_t lscv_smem_bytes(int d, int B, int R, bool kahan, bool oct) {
   const int dp = (d == 3) ? 4 : d;
-  const bool packed = (R == 4 && d == 4 && !oct) || (oct && R == 4 && oct_packed_q(d));  // kPackedQ: pairs
+  const bool packed = (R == 4 && d == 4 && !oct);  // kPackedQ: the column tile holds pairs
   return (size_t)32 * R * dp * (packed ? 8 : 4) + (size_t)kWarps * B * 16 +
          (kahan ? (size_t)kWarps * B * 32 * 16 : 0);
 }

@@ -17,6 +17,10 @@ constexpr int kPrepThreads = 512;
 constexpr int kDsWords = (int)(sizeof(DsDev) / sizeof(uint64_t));
 static_assert(sizeof(DsDev) % sizeof(uint64_t) == 0, "descriptor copied as 8-byte words");
 
+// Kernel parameters of k_setup, sized for grids of up to NH points (the
+// parameter block is copied at every launch: 64-point grids and PLUGIN
+// calls take the small one).
+template <int NH>
 struct SetupParams {
   uint64_t init[kDsWords];  // the host-built descriptor, as words
   int64_t off[4];
@@ -24,13 +28,14 @@ struct SetupParams {
   int32_t n_h, n_h_pad;
   double* h_dst;            // the descriptor's h[] and nc[]
   float* nc_dst;
-  double h[KDE_MAX_NH];
-  float nc[KDE_MAX_NH];     // -1/h^2 (FP64, rounded to FP32; padding entries -1)
+  double h[NH];
+  float nc[NH];             // -1/h^2 (FP64, rounded to FP32; padding entries -1)
 };
 
 // Copies the host-built descriptor into device memory, one word per thread,
 // and the grid's h[k] and nc[k] = -1/h_k^2 into its arrays.
-__global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams p) {
+template <int NH>
+__global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams<NH> p) {
   uint64_t* d64 = reinterpret_cast<uint64_t*>(dst);
   for (int i = threadIdx.x; i < kDsWords; i += blockDim.x) d64[i] = p.init[i];
   if (threadIdx.x < p.n_off) off_dst[threadIdx.x] = p.off[threadIdx.x];
@@ -630,22 +635,30 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
 
 }  // namespace
 
-cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
-                         int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
-  SetupParams p;
+template <int NH>
+static cudaError_t launch_setup_t(DsDev* dst, const DsDev& init, const double* h, int n_h,
+                                  int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
+  SetupParams<NH> p;
   memcpy(p.init, &init, sizeof(DsDev));
   p.n_off = n_off;
   for (int k = 0; k < 4; ++k) p.off[k] = k < n_off ? off_src[k] : 0;
-  p.n_h = std::min(n_h, KDE_MAX_NH);
-  p.n_h_pad = std::min(init.n_h_pad, KDE_MAX_NH);
+  p.n_h = std::min(n_h, NH);
+  p.n_h_pad = std::min(init.n_h_pad, NH);
   p.h_dst = init.h;
   p.nc_dst = init.nc;
   for (int k = 0; k < p.n_h_pad; ++k) {
     p.h[k] = k < p.n_h ? h[k] : 0.0;
     p.nc[k] = k < p.n_h ? (float)(-1.0 / (h[k] * h[k])) : -1.0f;
   }
-  k_setup<<<1, 256, 0, st>>>(dst, off_dst, p);
+  k_setup<NH><<<1, 256, 0, st>>>(dst, off_dst, p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
+                         int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
+  if (std::max(n_h, init.n_h_pad) <= 64)
+    return launch_setup_t<64>(dst, init, h, n_h, off_dst, off_src, n_off, st);
+  return launch_setup_t<KDE_MAX_NH>(dst, init, h, n_h, off_dst, off_src, n_off, st);
 }
 
 cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st) {
