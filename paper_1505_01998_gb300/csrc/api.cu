@@ -482,10 +482,14 @@ int kde_psi_tile_edge(int64_t n, const kde_opts* opts, int* tile) {
 
 // -------------------------------------------------------------- LSCV_h
 
-// Largest partial table (item rows x 2 n_h values) that the last CTA of a
-// single-selection pair kernel reduces itself: 32 Ki doubles, a few
-// microseconds of one CTA's L2 reads, against two kernel launches.
-constexpr int64_t kFuseMaxPartials = 32768;
+// Partial tables that the last CTA of a single-selection pair kernel reduces
+// itself: at most one chunk of rows per column strip (the reduction's chunk
+// size, 64 rows) and at most 8 strips (n_h_pad <= 128), so its loads are a
+// single L2 round trip per strip.  Larger tables go to the many-CTA
+// reduction kernel: one CTA walking chunk after chunk measured slower than
+// that kernel's launch (n = 1,000, 32 bandwidths: 19 against 15 us).
+constexpr int64_t kFuseMaxRows = 64;
+constexpr int kFuseMaxStrips = 8;
 
 static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std::vector<double>& h,
                       const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st,
@@ -509,12 +513,12 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, g.items, 0, 0};
-  CK(launch_setup(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
+  CK(launch_setup_prep(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
   Phase ph{ds, off, nullptr, 1, 0, g.items};
   // small partial tables: the pair kernel's last CTA reduces and finishes
   // (saves two launches); large ones keep the many-CTA reduction
-  const bool fuse = !lscv_warp_items(g.dk, g.B) && g.rows * 2 * (int64_t)g.n_h_pad <= kFuseMaxPartials;
+  const bool fuse = !lscv_warp_items(g.dk, g.B) && g.rows <= kFuseMaxRows &&
+                    (2 * g.n_h_pad + 31) / 32 <= kFuseMaxStrips;
   ph.fuse = fuse ? 1 : 0;
   const int grid = (int)std::min<int64_t>(g.items, g.oct_P > 0 ? g.ctas_oct : g.ctas);
   CK(mark(0, st));
@@ -665,8 +669,7 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, g.prows};
-  CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
+  CK(launch_setup_prep(ds, init, nullptr, 0, off, offs, 4, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, g.prows};
   const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));
   // the last CTA of each psi launch reduces its item partials and advances
@@ -755,8 +758,7 @@ int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double gpi
   DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, init.psi_rows};
-  CK(launch_setup(ds, init, nullptr, 0, off, offs, 4, st));
-  CK(launch_prep(ds, 1, nullptr, g.prep_parts, st));
+  CK(launch_setup_prep(ds, init, nullptr, 0, off, offs, 4, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, init.psi_rows};
   const int grid = std::max(1, (int)std::min<int64_t>(init.psi_rows, g.ctas));
   CK(launch_psi(ph, r, g.Rp, g.kahan, psi_coef(r), grid, st));

@@ -279,6 +279,10 @@ cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef&
                        cudaStream_t st);
 // stage: 6 -> reduce psi_6, set g2; 4 -> reduce psi_4, set h; 0 -> raw sum only (into res.g_min)
 cudaError_t launch_psi_finish(DsDev* ds, int n_ds, const int* ids, int stage, int r, cudaStream_t st);
+// Descriptor setup and prologue of one dataset: one launch when its prologue
+// is a single range, else launch_setup then launch_prep.
+cudaError_t launch_setup_prep(DsDev* dst, const DsDev& init, const double* h, int n_h, int64_t* off_dst,
+                              const int64_t* off_src, int n_off, cudaStream_t st);
 cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
                          int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st);
 cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st);

@@ -35,7 +35,7 @@ struct SetupParams {
 // Copies the host-built descriptor into device memory, one word per thread,
 // and the grid's h[k] and nc[k] = -1/h_k^2 into its arrays.
 template <int NH>
-__global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams<NH> p) {
+__device__ __forceinline__ void setup_copy(DsDev* dst, int64_t* off_dst, const SetupParams<NH>& p) {
   uint64_t* d64 = reinterpret_cast<uint64_t*>(dst);
   for (int i = threadIdx.x; i < kDsWords; i += blockDim.x) d64[i] = p.init[i];
   if (threadIdx.x < p.n_off) off_dst[threadIdx.x] = p.off[threadIdx.x];
@@ -43,6 +43,11 @@ __global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams<NH> p) {
     if (k < p.n_h) p.h_dst[k] = p.h[k];
     p.nc_dst[k] = p.nc[k];
   }
+}
+
+template <int NH>
+__global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams<NH> p) {
+  setup_copy(dst, off_dst, p);
 }
 
 // Per-thread accumulator: FP32 with Kahan compensation for FP32 input
@@ -578,6 +583,27 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const i
   }
 }
 
+// Setup, statistics and whitening of one dataset whose prologue is a single
+// range (one CTA): the CTA writes the descriptor and the grid itself, so the
+// separate k_setup launch is not needed.  (With several ranges every CTA would
+// need the descriptor first, and a late copy would reset the range counter.)
+template <int NH>
+__global__ void __launch_bounds__(kPrepThreads) k_setup_prep1(DsDev* ds, int64_t* off_dst, SetupParams<NH> p) {
+  __shared__ PrepSmem sm;
+  __shared__ WhitenSmem wm;
+  setup_copy(ds, off_dst, p);
+  __syncthreads();  // the descriptor this CTA just wrote is read below
+  if (ds->dtype == KDE_F64)
+    stats_dispatch<double>(ds, sm, 0);
+  else
+    stats_dispatch<float>(ds, sm, 0);
+  __syncthreads();
+  if (ds->dtype == KDE_F64)
+    whiten_dispatch<double>(ds, wm, 0);
+  else
+    whiten_dispatch<float>(ds, wm, 0);
+}
+
 __global__ void __launch_bounds__(kPrepThreads) k_prep_whiten(DsDev* dsa, const int* ids) {
   __shared__ WhitenSmem sm;
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
@@ -636,20 +662,26 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
 }  // namespace
 
 template <int NH>
+static void fill_setup(SetupParams<NH>* p, const DsDev& init, const double* h, int n_h,
+                       const int64_t* off_src, int n_off) {
+  memcpy(p->init, &init, sizeof(DsDev));
+  p->n_off = n_off;
+  for (int k = 0; k < 4; ++k) p->off[k] = k < n_off ? off_src[k] : 0;
+  p->n_h = std::min(n_h, NH);
+  p->n_h_pad = std::min(init.n_h_pad, NH);
+  p->h_dst = init.h;
+  p->nc_dst = init.nc;
+  for (int k = 0; k < p->n_h_pad; ++k) {
+    p->h[k] = k < p->n_h ? h[k] : 0.0;
+    p->nc[k] = k < p->n_h ? (float)(-1.0 / (h[k] * h[k])) : -1.0f;
+  }
+}
+
+template <int NH>
 static cudaError_t launch_setup_t(DsDev* dst, const DsDev& init, const double* h, int n_h,
                                   int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams<NH> p;
-  memcpy(p.init, &init, sizeof(DsDev));
-  p.n_off = n_off;
-  for (int k = 0; k < 4; ++k) p.off[k] = k < n_off ? off_src[k] : 0;
-  p.n_h = std::min(n_h, NH);
-  p.n_h_pad = std::min(init.n_h_pad, NH);
-  p.h_dst = init.h;
-  p.nc_dst = init.nc;
-  for (int k = 0; k < p.n_h_pad; ++k) {
-    p.h[k] = k < p.n_h ? h[k] : 0.0;
-    p.nc[k] = k < p.n_h ? (float)(-1.0 / (h[k] * h[k])) : -1.0f;
-  }
+  fill_setup(&p, init, h, n_h, off_src, n_off);
   k_setup<NH><<<1, 256, 0, st>>>(dst, off_dst, p);
   return cudaGetLastError();
 }
@@ -659,6 +691,27 @@ cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h
   if (std::max(n_h, init.n_h_pad) <= 64)
     return launch_setup_t<64>(dst, init, h, n_h, off_dst, off_src, n_off, st);
   return launch_setup_t<KDE_MAX_NH>(dst, init, h, n_h, off_dst, off_src, n_off, st);
+}
+
+template <int NH>
+static cudaError_t launch_setup_prep1_t(DsDev* dst, const DsDev& init, const double* h, int n_h,
+                                        int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
+  SetupParams<NH> p;
+  fill_setup(&p, init, h, n_h, off_src, n_off);
+  k_setup_prep1<NH><<<1, kPrepThreads, 0, st>>>(dst, off_dst, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_prep(DsDev* dst, const DsDev& init, const double* h, int n_h, int64_t* off_dst,
+                              const int64_t* off_src, int n_off, cudaStream_t st) {
+  if (init.prep_parts > 1) {  // several ranges: the descriptor first, in its own launch
+    const cudaError_t e = launch_setup(dst, init, h, n_h, off_dst, off_src, n_off, st);
+    if (e != cudaSuccess) return e;
+    return launch_prep(dst, 1, nullptr, init.prep_parts, st);
+  }
+  if (std::max(n_h, init.n_h_pad) <= 64)
+    return launch_setup_prep1_t<64>(dst, init, h, n_h, off_dst, off_src, n_off, st);
+  return launch_setup_prep1_t<KDE_MAX_NH>(dst, init, h, n_h, off_dst, off_src, n_off, st);
 }
 
 cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cudaStream_t st) {
