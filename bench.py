@@ -1138,7 +1138,9 @@ def run_gpu(args, world, rank, local):
             "gpu_launches": LAUNCHES_PER_STEP * K * world,  # all ranks
             "roofline": roofline, "clocks": clocks,
             "alu_probe": probe,
-            "result": {"lscv_argmin": r_l["argmin"], "lscv_h": r_l["h"], "plugin_h": r_p["h"]}}
+            "result": {"lscv_argmin": r_l["argmin"], "lscv_h": r_l["h"], "plugin_h": r_p["h"],
+                       # the skewed column's g(h) still falls at h0/4, the lower end of Z(h0)
+                       "lscv_min_at_lower_edge": bool(r_l["flags"] & gbkde.KDE_FLAG_MIN_AT_LOWER_EDGE)}}
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_sample(args.cpu_seconds)
