@@ -1118,6 +1118,13 @@ def run_gpu(args, world, rank, local):
     # bound): above 1 on the default grid, whose octave shape lets most
     # exponentials be formed by squaring
     roofline["frac_vs_one_ex2_basis"] = achieved / (probe["mufu_ex2_per_clk_sm"] * probe["sm_count"] * sm_mhz * 1e6 / 1e9)
+    # the bound of the octave kernel's earlier form (three FMUL2 scalings per 16
+    # evaluations, 1.5 FMUL2/FADD2 lanes per evaluation): a fixed yardstick
+    # across versions, since the exponent adds moved the instruction-mix bound
+    fp32_3fmul = 1.0 / (1.5 / probe["fmul2_fadd2_lanes_per_clk_sm"] + 0.375 / probe["ffma2_lanes_per_clk_sm"]
+                        + (2.0 / 16.0) / probe["ffma_lanes_per_clk_sm"])
+    roofline["frac_vs_three_fmul2_mix"] = achieved / (
+        min(probe["mufu_ex2_per_clk_sm"] / 0.375, fp32_3fmul) * probe["sm_count"] * sm_mhz * 1e6 / 1e9)
 
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras and N == 65536:
