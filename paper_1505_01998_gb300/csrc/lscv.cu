@@ -320,8 +320,8 @@ __device__ void lscv_finish_body(DsDev* ds);
 
 // Fused single-dataset launches: the CTA that finishes last (a counter in the
 // descriptor; no CTA waits) adds the item rows and finishes, with the same
-// code and order as k_lscv_reduce and k_lscv_finish, so results are bitwise
-// those of the separate kernels.
+// code and order as k_lscv_reduce (whose last CTA also finishes), so results
+// are bitwise those of the separate reduction.
 __device__ __noinline__ void lscv_fused_finish(const Phase& ph) {
   __shared__ double sFin[kThreads];
   __shared__ int sLast;
