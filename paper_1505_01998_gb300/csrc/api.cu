@@ -13,6 +13,8 @@
 
 namespace gbkde {
 
+thread_local bool t_dependent_launch = false;
+
 namespace {
 thread_local int t_err_status = KDE_OK;
 thread_local char t_err_msg[512] = "";
@@ -513,6 +515,7 @@ static int lscv_queue(const void* x_dev, int dtype, int64_t n, int d, const std:
   DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, g.items, 0, 0};
+  DependentLaunchScope pdl;
   CK(launch_setup_prep(ds, init, h.data(), (int)h.size(), off, offs, 4, st));
   Phase ph{ds, off, nullptr, 1, 0, g.items};
   // small partial tables: the pair kernel's last CTA reduces and finishes
@@ -669,6 +672,7 @@ static int plugin_queue(const void* x_dev, int dtype, int64_t n, const kde_opts*
   DsDev* ds = reinterpret_cast<DsDev*>(w + g.off_ds);
   int64_t* off = reinterpret_cast<int64_t*>(w + g.off_off);
   const int64_t offs[4] = {0, 0, 0, g.prows};
+  DependentLaunchScope pdl;
   CK(launch_setup_prep(ds, init, nullptr, 0, off, offs, 4, st));
   Phase ph{ds, off + 2, nullptr, 1, 0, g.prows};
   const int grid = std::max(1, (int)std::min<int64_t>(g.prows, g.ctas));

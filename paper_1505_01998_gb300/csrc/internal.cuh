@@ -236,6 +236,66 @@ __device__ __forceinline__ float warp_sum_f(float v) {
   return v;
 }
 
+// Holds a kernel launched with programmatic stream serialisation until the
+// kernel before it in the stream has completed and its writes are visible
+// (PTX griddepcontrol.wait).  Every kernel that single selections launch
+// calls it first, before touching global memory; launched the plain way
+// (batches, the server, graph replays), it returns at once.
+__device__ __forceinline__ void dependent_launch_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// w^K for a small positive integer K by squarings (K = 7: w^2, w^3, w^6, w^7).
+template <int K>
+__device__ __forceinline__ double ipow(double w) {
+  if constexpr (K == 1)
+    return w;
+  else if constexpr (K % 2 == 0) {
+    const double s = ipow<K / 2>(w);
+    return s * s;
+  } else {
+    return ipow<K - 1>(w) * w;
+  }
+}
+
+// y = x^(1/K) and its reciprocal for a normal x > 0, in FP64 without pow,
+// exp or log (each a long FP64 sequence on this part, whose FP64 unit runs at
+// a small fraction of the FP32 rate; a dependent FP64 operation costs about
+// 45 clocks).  With x = m 2^(K q), m in [1, 2^K) (an exact exponent split),
+// Newton's method for f(w) = w^-K - m, whose step w <- w + w (1 - m w^K) / K
+// needs no division, converges quadratically to w = m^(-1/K).  The seed
+// 2^(-log2(m) / K) comes from the FP32 MUFU log2 and exp2 (about 20 correct
+// bits), so two steps reach FP64 rounding; then m^(1/K) = m w^(K-1) and both
+// results are scaled by 2^(+-q).  Other x (zero, negative, subnormal,
+// infinite, NaN) take the library pow.
+template <int K>
+__device__ __forceinline__ double root_newton(double x, double* inv) {
+  static_assert(K >= 2 && K <= 9, "small integer roots");
+  if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) {
+    const double y = pow(x, 1.0 / K);
+    *inv = 1.0 / y;
+    return y;
+  }
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+  int q = e / K, r = e - q * K;
+  if (r < 0) {
+    r += K;
+    --q;
+  }
+  const double m = __longlong_as_double((bits & 0x000fffffffffffffLL) | ((long long)(1023 + r) << 52));
+  float l2, s;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"((float)m));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(l2 * (-1.0f / K)));
+  double w = (double)s;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double t = fma(-m, ipow<K>(w), 1.0);
+    w = fma(w * t, 1.0 / K, w);
+  }
+  const double y = m * ipow<K - 1>(w);
+  *inv = w * __longlong_as_double((long long)(1023 - q) << 52);  // |q| <= 511
+  return y * __longlong_as_double((long long)(1023 + q) << 52);
+}
+
 // Index of the dataset owning global item `it` (largest i with off[i] <= it).
 __device__ __forceinline__ int find_ds(const int64_t* off, int n, int64_t it) {
   int lo = 0, hi = n - 1;
@@ -261,6 +321,37 @@ inline int prep_parts_for(int64_t n) {
 }
 
 // ------------------------------------------------------------- launchers
+// Programmatic dependent launch for the short launch sequences of single
+// selections: while a DependentLaunchScope lives on the calling thread,
+// launch_kernel asks for programmatic stream serialisation, so that a
+// kernel's CTAs are scheduled while the kernel before it drains (each such
+// kernel waits in dependent_launch_wait before touching global memory).
+// Measured on this part: about 2.3 us less per kernel boundary.
+extern thread_local bool t_dependent_launch;
+struct DependentLaunchScope {
+  bool prev;
+  DependentLaunchScope() : prev(t_dependent_launch) { t_dependent_launch = true; }
+  ~DependentLaunchScope() { t_dependent_launch = prev; }
+  DependentLaunchScope(const DependentLaunchScope&) = delete;
+  DependentLaunchScope& operator=(const DependentLaunchScope&) = delete;
+};
+
+template <typename... P, typename... A>
+cudaError_t launch_kernel(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                          A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = t_dependent_launch ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // (defined in the .cu files; return a cudaError_t)
 // ids: optional list of dataset indices into ds (one CTA each); NULL = ds[0..n_ds)
 // parts_max: the largest prep_parts among the datasets launched

@@ -357,6 +357,7 @@ __device__ __noinline__ void lscv_fused_finish(const Phase& ph) {
 // the partial rows and their reduction are the same.
 template <int D, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
+  dependent_launch_wait();
   constexpr int T = 32, B = 2, DP = DPad<D>::value;
   static_assert(D > 4 && DP % 4 == 0, "wide samples only");
   __shared__ __align__(16) float sFw[kWarps][T * DP];
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
 // (wide ones spill there and keep 2)
 template <int D, int B, int R, bool KAHAN, bool OCT>
 __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phase ph) {
+  dependent_launch_wait();
   constexpr int T = 32 * R;
   constexpr int DP = DPad<D>::value;
   constexpr int FB = T * DP * (kPackedQ<D, R, OCT> ? 8 : 4);  // column tile bytes
@@ -721,6 +723,7 @@ __device__ double lscv_chunk_total(const DsDev* ds, int c0, int64_t r0, int64_t 
 // selection gets the same bits alone, in a batch, served or fused into its
 // pair kernel (which adds in the same order).
 __global__ void __launch_bounds__(kThreads) k_lscv_reduce(DsDev* dsa, const int* ids) {
+  dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   __shared__ double s[kThreads];
   __shared__ int sLast;
@@ -788,9 +791,12 @@ __device__ __forceinline__ bool argmin_before(double g, int k, double h, int j) 
 __device__ void lscv_finish_body(DsDev* ds) {
   const int d = ds->d, n_h = ds->n_h;
   const double n = (double)ds->n;
-  const double c2 = exp2(1.0 + 0.5 * d);
+  // 2^(1 + d/2) exactly: a power of two, times sqrt(2) for odd d (no FP64
+  // exp2, a long sequence on this part); one FP64 division for 1/n
+  const double c2 = __longlong_as_double((long long)(1024 + d / 2) << 52) * ((d & 1) ? 1.4142135623730951 : 1.0);
+  const double inv_n = 1.0 / n, w2 = 2.0 * inv_n * inv_n;
   // K-term weight: the paper's n^-2 (Eq. LSCV-gh) or exact leave-one-out 1/(n(n-1))
-  const double wk = ds->cv_loo ? 2.0 / (n * (n - 1.0)) : 2.0 / (n * n);
+  const double wk = ds->cv_loo ? 2.0 * inv_n / (n - 1.0) : w2;
   // g(h_k) per thread (h^-d by d multiplications and one division), and the
   // first index of the minimum: per thread over its k, then lexicographic
   // (g, k) minima across lanes and warps (NaN ranks above every number)
@@ -803,7 +809,7 @@ __device__ void lscv_finish_body(DsDev* ds) {
     const double hk = ds->h[k];
     double hd = 1.0;
     for (int i = 0; i < d; ++i) hd *= hk;
-    const double gk = ds->A / hd * (2.0 / (n * n) * s1 - wk * c2 * s2 + 1.0 / n);
+    const double gk = ds->A / hd * (w2 * s1 - wk * c2 * s2 + inv_n);
     ds->g[k] = gk;
     if (argmin_before(gk, k, gb, best)) {
       gb = gk;
@@ -853,8 +859,7 @@ template <int D, int B, int R, bool KAHAN, bool OCT>
 cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
   if constexpr (lscv_warp_items(D, B)) {  // static shared memory: no attribute to set
     if (grid <= 0) return cudaSuccess;
-    k_lscv_warp<D, KAHAN><<<grid, kThreads, 0, st>>>(ph);
-    return cudaGetLastError();
+    return launch_kernel(k_lscv_warp<D, KAHAN>, dim3(grid), dim3(kThreads), 0, st, ph);
   } else {
     const size_t smem = lscv_smem_bytes(D, B, R, KAHAN, OCT);
     // set once per instance (a function-local static is initialised once,
@@ -863,8 +868,7 @@ cudaError_t launch_t(const Phase& ph, int grid, cudaStream_t st) {
         k_lscv<D, B, R, KAHAN, OCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     if (grid <= 0) return cudaSuccess;  // attribute set only (before a graph capture)
-    k_lscv<D, B, R, KAHAN, OCT><<<grid, kThreads, smem, st>>>(ph);
-    return cudaGetLastError();
+    return launch_kernel(k_lscv<D, B, R, KAHAN, OCT>, dim3(grid), dim3(kThreads), smem, st, ph);
   }
 }
 
@@ -935,8 +939,7 @@ cudaError_t launch_lscv_reduce(DsDev* ds, int n_ds, const int* ids, int n_h_pad_
   if (chunks < 1) chunks = 1;
   if (chunks > 65535) return cudaErrorInvalidValue;
   dim3 grid(n_ds, (2 * n_h_pad_max + 31) / 32, (unsigned)chunks);
-  k_lscv_reduce<<<grid, kThreads, 0, st>>>(ds, ids);
-  return cudaGetLastError();
+  return launch_kernel(k_lscv_reduce, grid, dim3(kThreads), 0, st, ds, ids);
 }
 
 }  // namespace gbkde

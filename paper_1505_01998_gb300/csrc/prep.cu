@@ -9,7 +9,7 @@ namespace gbkde {
 
 namespace {
 
-constexpr double kSqrtPi = 1.7724538509055159;           // sqrt(pi) in FP64
+constexpr double kPsi8Coef = 1.8512470710160756;         // 105 / (32 sqrt(pi)) in FP64
 constexpr double kSqrtHalfLog2e = 0.8493218002880191;     // sqrt(log2(e) / 2) in FP64
 constexpr double kSqrtQuarterLog2e = 0.6005612043932249;  // sqrt(log2(e) / 4) in FP64
 constexpr int kPrepThreads = 512;
@@ -47,6 +47,7 @@ __device__ __forceinline__ void setup_copy(DsDev* dst, int64_t* off_dst, const S
 
 template <int NH>
 __global__ void k_setup(DsDev* dst, int64_t* off_dst, SetupParams<NH> p) {
+  dependent_launch_wait();
   setup_copy(dst, off_dst, p);
 }
 
@@ -426,6 +427,24 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   // reciprocals of the diagonal); the log of each pivot alongside
   // (log|S| = sum_i log L_ii^2, summed in order below)
   if (threadIdx.x < d) ldiag[threadIdx.x] = log(piv[threadIdx.x]);
+  // sigma and the PLUGIN pilot on a thread of another warp, alongside the
+  // logs: with r = 1 / sigma from one reciprocal square root, sigma = S_00 r,
+  // psi_8^NS = 105 / (32 sqrt(pi) sigma^9) = c r^9 and
+  // g1 = (-2 K6(0) / (psi_8^NS n))^(1/9) = sigma c_g1 (c_g1 of n from the
+  // host), so no FP64 division, square root or pow lies on this chain
+  if (threadIdx.x == 32) {
+    const double s00 = S[0][0];
+    const double rs = rsqrt(s00);
+    const double sg = s00 * rs;
+    ds->sigma = sg;
+    if (d == 1) res.sigma = sg;
+    if ((ds->methods & KDE_METHOD_PLUGIN) && d == 1) {
+      const double r2 = rs * rs, r4 = r2 * r2, r8 = r4 * r4;
+      res.psi8_ns = kPsi8Coef * (r8 * rs);
+      res.g1 = sg * ds->c_g1;
+      ds->psi_scale = (float)(rs * (kSqrtHalfLog2e / ds->c_g1));
+    }
+  }
   if (threadIdx.x < d) {
     const int j = threadIdx.x;
     W[j][j] = rdiag[j];
@@ -443,11 +462,8 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     ds->M[t] = mv;
     sM[t] = mv;
   }
-  // the scalar chains on two threads, without FP64 pow/exp: log|S| and
-  // A = (4 pi)^(-d/2) |S|^(-1/2) = c_A prod_i 1 / L_ii; sigma and the PLUGIN
-  // pilot, psi_8^NS = 105 / (32 sqrt(pi) sigma^9) and
-  // g1 = (-2 K6(0) / (psi_8^NS n))^(1/9) = sigma c_g1, with the constants
-  // c_A (of d) and c_g1 (of n) from the host
+  // log|S| and A = (4 pi)^(-d/2) |S|^(-1/2) = c_A prod_i 1 / L_ii (c_A of d
+  // from the host), without FP64 pow or exp
   if (threadIdx.x == 0) {
     double logdet = 0.0, a = ds->c_A;
     for (int i = 0; i < d; ++i) {
@@ -457,18 +473,6 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     ds->logdet = logdet;
     res.logdet_S = logdet;
     ds->A = a;
-  } else if (threadIdx.x == 32) {
-    const double sg = sqrt(S[0][0]);
-    ds->sigma = sg;
-    if (d == 1) res.sigma = sg;
-    if ((ds->methods & KDE_METHOD_PLUGIN) && d == 1) {
-      const double s2 = sg * sg, s4 = s2 * s2, s8 = s4 * s4;
-      const double psi8 = 105.0 / (32.0 * kSqrtPi * (s8 * sg));
-      const double g1 = sg * ds->c_g1;
-      res.psi8_ns = psi8;
-      res.g1 = g1;
-      ds->psi_scale = (float)(kSqrtHalfLog2e / g1);
-    }
   }
 }
 
@@ -568,6 +572,7 @@ __device__ __forceinline__ void whiten_dispatch(DsDev* ds, WhitenSmem& sm, int b
 // launched.
 __global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const int* ids, int whiten) {
   __shared__ PrepSmem sm;
+  dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
   if (ds->dtype == KDE_F64)
     stats_dispatch<double>(ds, sm, blockIdx.x);
@@ -591,6 +596,7 @@ template <int NH>
 __global__ void __launch_bounds__(kPrepThreads) k_setup_prep1(DsDev* ds, int64_t* off_dst, SetupParams<NH> p) {
   __shared__ PrepSmem sm;
   __shared__ WhitenSmem wm;
+  dependent_launch_wait();
   setup_copy(ds, off_dst, p);
   __syncthreads();  // the descriptor this CTA just wrote is read below
   if (ds->dtype == KDE_F64)
@@ -606,6 +612,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_setup_prep1(DsDev* ds, int64_t
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_whiten(DsDev* dsa, const int* ids) {
   __shared__ WhitenSmem sm;
+  dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
   if (ds->dtype == KDE_F64)
     whiten_dispatch<double>(ds, sm, blockIdx.x);
@@ -682,8 +689,7 @@ static cudaError_t launch_setup_t(DsDev* dst, const DsDev& init, const double* h
                                   int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams<NH> p;
   fill_setup(&p, init, h, n_h, off_src, n_off);
-  k_setup<NH><<<1, 256, 0, st>>>(dst, off_dst, p);
-  return cudaGetLastError();
+  return launch_kernel(k_setup<NH>, dim3(1), dim3(256), 0, st, dst, off_dst, p);
 }
 
 cudaError_t launch_setup(DsDev* dst, const DsDev& init, const double* h, int n_h,
@@ -698,8 +704,7 @@ static cudaError_t launch_setup_prep1_t(DsDev* dst, const DsDev& init, const dou
                                         int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams<NH> p;
   fill_setup(&p, init, h, n_h, off_src, n_off);
-  k_setup_prep1<NH><<<1, kPrepThreads, 0, st>>>(dst, off_dst, p);
-  return cudaGetLastError();
+  return launch_kernel(k_setup_prep1<NH>, dim3(1), dim3(kPrepThreads), 0, st, dst, off_dst, p);
 }
 
 cudaError_t launch_setup_prep(DsDev* dst, const DsDev& init, const double* h, int n_h, int64_t* off_dst,
@@ -718,11 +723,9 @@ cudaError_t launch_prep(DsDev* ds, int n_ds, const int* ids, int parts_max, cuda
   if (n_ds <= 0) return cudaSuccess;
   const dim3 grid((unsigned)std::max(1, parts_max), (unsigned)n_ds);
   const int fused = parts_max <= 1;
-  k_prep_stats<<<grid, kPrepThreads, 0, st>>>(ds, ids, fused);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_kernel(k_prep_stats, grid, dim3(kPrepThreads), 0, st, ds, ids, fused);
   if (e != cudaSuccess || fused) return e;
-  k_prep_whiten<<<grid, kPrepThreads, 0, st>>>(ds, ids);
-  return cudaGetLastError();
+  return launch_kernel(k_prep_whiten, grid, dim3(kPrepThreads), 0, st, ds, ids);
 }
 
 cudaError_t launch_probe_mode(int mode, double* out, int iters, int grid, cudaStream_t st) {

@@ -26,7 +26,7 @@ namespace gbkde {
 namespace {
 
 constexpr double kSqrtHalfLog2e = 0.8493218002880191;  // sqrt(log2(e) / 2) in FP64
-constexpr double kPi = 3.14159265358979323846;
+constexpr double kRK = 0.28209479177387814;  // R(K) = 1 / (2 sqrt(pi)) of the Gaussian kernel, FP64
 
 template <int RD, int R, bool EDGE>
 __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_lo, int j_hi,
@@ -87,6 +87,7 @@ __device__ __noinline__ void psi_fused_finish(const Phase& ph, int r, double pos
 
 template <int RD, int R, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
+  dependent_launch_wait();
   constexpr int T = 32 * R;
   __shared__ __align__(16) float sF[2 * T];  // (-v, -v) per column
   __shared__ double sRed[kWarps];
@@ -203,8 +204,11 @@ __device__ void psi_finish_body(DsDev* ds, int stage, int r, double post) {
   const double kappa = 2.0 * 0.69314718055994530942;
   const double inv_sqrt_2pi = 0.39894228040143267794;
   // sum_{i<j} K^(r)((x_i - x_j)/g) = kappa^(r/2) P / sqrt(2 pi); integer
-  // powers by multiplication (FP64 pow is a long sequence on this part), the
-  // two real roots of the chain by pow
+  // powers by multiplication and the two real roots of the chain by
+  // root_newton (FP64 pow is a long sequence on this part: about 5,800
+  // clocks against 1,100).  The root's argument is formed from the same
+  // numerator and denominator as psi_r, so that its division does not wait
+  // for psi_r's.
   double kr = 1.0;
   for (int m = 0; m < r / 2; ++m) kr *= kappa;
   const double sumK = kr * P * inv_sqrt_2pi;
@@ -219,27 +223,34 @@ __device__ void psi_finish_body(DsDev* ds, int stage, int r, double post) {
     const double k4_0 = 3.0 * inv_sqrt_2pi;    // K^(4)(0), Eq. PLUGIN-g2
     const double g1 = res.g1;
     const double g1s = g1 * g1, g1q = g1s * g1s;
-    const double psi6 = (2.0 * sumK + n * k6_0) / (n * n * (g1q * g1s * g1));
+    const double num = 2.0 * sumK + n * k6_0, den = n * n * (g1q * g1s * g1);
+    const double psi6 = num / den;
+    // g2 = (-2 K4(0) / (psi6 n))^(1/7)
+    const double arg = -2.0 * k4_0 * den / (num * n);
     res.psi6 = psi6;
     if (!(psi6 < 0.0)) {
       res.status = KDE_EDEGENERATE;
       return;
     }
-    const double g2 = pow(-2.0 * k4_0 / (psi6 * n), 1.0 / 7.0);
+    double inv_g2;
+    const double g2 = root_newton<7>(arg, &inv_g2);
     res.g2 = g2;
-    ds->psi_scale = (float)(kSqrtHalfLog2e / g2);
+    ds->psi_scale = (float)(kSqrtHalfLog2e * inv_g2);
   } else {
     const double k4_0 = 3.0 * inv_sqrt_2pi;
     const double g2 = res.g2;
     const double g2s = g2 * g2;
-    const double psi4 = (2.0 * sumK + n * k4_0) / (n * n * (g2s * g2s * g2));
+    const double num = 2.0 * sumK + n * k4_0, den = n * n * (g2s * g2s * g2);
+    const double psi4 = num / den;
+    // h = (R(K) / (psi4 n))^(1/5), R(K) = 1 / (2 sqrt(pi)) (Eq. PLUGIN-Final_h)
+    const double arg = kRK * den / (num * n);
     res.psi4 = psi4;
     if (!(psi4 > 0.0)) {
       res.status = KDE_EDEGENERATE;
       return;
     }
-    const double rk = 1.0 / (2.0 * sqrt(kPi));  // R(K), Eq. PLUGIN-Final_h
-    const double h = pow(rk / (psi4 * n), 0.2);
+    double inv_h;
+    const double h = root_newton<5>(arg, &inv_h);
     res.h_plugin = h;
     if (!(ds->methods & KDE_METHOD_LSCV)) {  // otherwise h / h_data hold the LSCV choice
       res.h = h;
@@ -250,17 +261,15 @@ __device__ void psi_finish_body(DsDev* ds, int stage, int r, double post) {
 
 __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* ids, int stage, int r,
                                                          double post) {
+  dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.x] : (int)blockIdx.x);
   psi_finish_body(ds, stage, r, post);
 }
 
 template <int RD, int R>
 cudaError_t launch_k(const Phase& ph, bool kahan, const PsiCoef& cf, int grid, cudaStream_t st) {
-  if (kahan)
-    k_psi<RD, R, true><<<grid, kThreads, 0, st>>>(ph, cf);
-  else
-    k_psi<RD, R, false><<<grid, kThreads, 0, st>>>(ph, cf);
-  return cudaGetLastError();
+  if (kahan) return launch_kernel(k_psi<RD, R, true>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
+  return launch_kernel(k_psi<RD, R, false>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
 }
 
 template <int RD>
@@ -288,8 +297,7 @@ cudaError_t launch_psi(const Phase& ph, int r, int R, bool kahan, const PsiCoef&
 
 cudaError_t launch_psi_finish(DsDev* ds, int n_ds, const int* ids, int stage, int r, cudaStream_t st) {
   if (n_ds <= 0) return cudaSuccess;
-  k_psi_finish<<<n_ds, kThreads, 0, st>>>(ds, ids, stage, r, psi_coef(r).post);
-  return cudaGetLastError();
+  return launch_kernel(k_psi_finish, dim3(n_ds), dim3(kThreads), 0, st, ds, ids, stage, r, psi_coef(r).post);
 }
 
 }  // namespace gbkde

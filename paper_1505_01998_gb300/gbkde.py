@@ -341,6 +341,9 @@ class kde_serve_stats_t(ctypes.Structure):
 def lib():
     """Load libgbkde.so (raises if it has not been built)."""
     global _lib
+    L = _lib
+    if L is not None:  # loaded: no lock on the per-call path
+        return L
     with _lock:
         if _lib is not None:
             return _lib
@@ -364,6 +367,10 @@ def _check(rc: int):
 
 
 def _dp(a: np.ndarray):
+    # a ctypes array over the numpy buffer converts to double* at the call
+    # (a third of the cost of ndarray.ctypes.data_as, a few us per call)
+    if a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable and a.size > 0:
+        return (ctypes.c_double * a.size).from_buffer(a)
     return a.ctypes.data_as(_DP)
 
 

@@ -1,5 +1,6 @@
 """C ABI and host logic of libgbkde (CPU only: no kernel is launched)."""
 import ctypes
+import decimal
 import math
 import os
 import re
@@ -155,6 +156,39 @@ def test_double_float_butterfly_replayed_on_the_host():
         exact = math.fsum([float(v) for v in hi] + [float(v) for v in lo])
         got = float(h[0]) + float(l[0])
         assert abs(got - exact) <= 2.0 ** -43 * abs(exact), (trial, got, exact)
+
+
+@pytest.mark.parametrize("K", [5, 7, 9])
+def test_newton_root_replayed_on_the_host(K):
+    """The PLUGIN chain's real roots (g2 = a^(1/7), h = b^(1/5)) are formed
+    on the device by root_newton: x = m 2^(K q) with m in [1, 2^K) (the
+    exponent split by floor division), an FP32 seed 2^(-log2(m) / K), two
+    Newton steps w <- w + w (1 - m w^K) / K for w = m^(-1/K), then
+    x^(1/K) = m w^(K-1) 2^q and x^(-1/K) = w 2^-q.  Replayed here in numpy
+    FP64 with an FP32 seed perturbed by 2^-19 (looser than the MUFU seed):
+    across the whole normal range and at exponents of every residue mod K,
+    both results agree with the powers (40-digit decimal arithmetic) to a few
+    ulp."""
+    decimal.getcontext().prec = 40
+    rng = np.random.default_rng(K)
+    xs = np.concatenate([10.0 ** rng.uniform(-307, 308, 400), 2.0 ** np.arange(-1022, 1024, 37, dtype=np.float64),
+                         [2.2250738585072014e-308, 1.7976931348623157e308, 1.0, 0.5, 3.0]])
+    for x in xs:
+        bits = int(np.float64(x).view(np.int64))
+        e = ((bits >> 52) & 0x7FF) - 1023
+        q, r = e // K, e % K
+        m = float(np.int64((bits & 0x000FFFFFFFFFFFFF) | ((1023 + r) << 52)).view(np.float64))
+        assert 1.0 <= m < 2.0 ** K and m * 2.0 ** (K * q) == x
+        seed = np.float32(2.0 ** (-math.log2(float(np.float32(m))) / K)) * np.float32(1 + 2.0 ** -19)
+        w = float(seed)
+        for _ in range(2):
+            t = 1.0 - m * w ** K
+            w = w + w * t / K
+        y = m * w ** (K - 1) * 2.0 ** q
+        inv = w * 2.0 ** -q
+        ref = float(decimal.Decimal(x) ** (decimal.Decimal(1) / decimal.Decimal(K)))
+        assert abs(y - ref) <= 1.5e-15 * ref, (K, x, y, ref)
+        assert abs(inv * ref - 1.0) <= 1.5e-15, (K, x, inv, ref)
 
 
 def _ff_add(h, l, h2, l2):

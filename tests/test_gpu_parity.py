@@ -120,6 +120,31 @@ def test_plugin_matches_oracle(kde, n, dtype):
     _plugin_compare(res, oracle.plugin(x64), x64)
 
 
+@pytest.mark.parametrize("n,seed", [(1024, 1), (3000, 7), (65536, 2)])
+def test_plugin_chain_roots_match_library_roots(kde, n, seed):
+    """The device forms g2 = (-2 K4(0) / (psi6 n))^(1/7) and
+    h = (R(K) / (psi4 n))^(1/5) by Newton's iteration for the inverse root
+    from an FP32 seed, and sigma from one reciprocal square root: each agrees
+    with numpy's FP64 power of the device's own chain values (psi6, psi4 and
+    the sample variance, in the kernel's FP32 samples) to a few units in the
+    last place.  The arguments differ from numpy's by the order of their
+    divisions (at most a few ulp), which the root divides by 7 or 5; sigma is
+    checked against the device's own log|S|."""
+    x = datagen.mixture_1d(n, seed=seed)[0] if n < 65536 else datagen.skewed_column(n, seed=seed)[0]
+    res = kde.kde_plugin(dev(x))
+    k4_0 = 3.0 / math.sqrt(2.0 * math.pi)
+    rk = 1.0 / (2.0 * math.sqrt(math.pi))
+    g2 = np.power(-2.0 * k4_0 / (res["psi6"] * n), 1.0 / 7.0)
+    h = np.power(rk / (res["psi4"] * n), 0.2)
+    assert abs(res["g2"] - g2) <= 4e-15 * g2, (res["g2"], g2)
+    assert abs(res["h"] - h) <= 4e-15 * h, (res["h"], h)
+    # sigma = sqrt(S_00), S_00 = exp(log|S|) for d = 1; g1 = sigma c_g1
+    sigma = math.sqrt(math.exp(res["logdet_S"]))
+    assert abs(res["sigma"] - sigma) <= 1e-14 * sigma, (res["sigma"], sigma)
+    c_g1 = np.power(2.0 * 15.0 / math.sqrt(2.0 * math.pi) * 32.0 * math.sqrt(math.pi) / (105.0 * n), 1.0 / 9.0)
+    assert abs(res["g1"] - res["sigma"] * c_g1) <= 4e-15 * res["g1"], (res["g1"], res["sigma"] * c_g1)
+
+
 def test_plugin_plain_precision_also_within_tolerance(kde):
     x = datagen.mixture_1d(3000, seed=4)[0]
     x64 = host64(x)[0]
