@@ -1,6 +1,7 @@
 // Prologue kernels: descriptor setup, sample statistics, Cholesky whitening
 // and the first links of the PLUGIN chain; plus the ALU throughput probe.
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 
 #include "internal.cuh"
@@ -32,12 +33,33 @@ struct SetupParams {
   float nc[NH];             // -1/h^2 (FP64, rounded to FP32; padding entries -1)
 };
 
+// Words of the descriptor that the host may set: the geometry header (up to
+// the strip counters), oct_P, the host constants c_A and c_g1, the result
+// block, and the given bandwidth matrix in cov[] (LSCV_H, density estimates).
+// Every other word starts at zero.  Each parameter word a thread reads costs a
+// serialised constant-bank access (distinct addresses within a warp), so the
+// copy reads only these words (about 70 of about 500 without a given H) and
+// stores zeros elsewhere; fill_setup checks on the host that no other word is
+// nonzero.
+__host__ __device__ inline bool setup_word_copied(int i, bool given_H) {
+  constexpr int w_head = (int)(offsetof(DsDev, strip_count) / 8);
+  constexpr int w_oct = (int)(offsetof(DsDev, oct_P) / 8);
+  constexpr int w_cov0 = (int)(offsetof(DsDev, cov) / 8), w_cov1 = w_cov0 + KDE_MAX_D * KDE_MAX_D;
+  constexpr int w_c0 = (int)(offsetof(DsDev, c_A) / 8), w_c1 = (int)(offsetof(DsDev, M) / 8);
+  constexpr int w_res = (int)(offsetof(DsDev, res) / 8);
+  static_assert(offsetof(DsDev, c_g1) / 8 < offsetof(DsDev, M) / 8 && sizeof(double) == 8, "layout");
+  return i < w_head || i == w_oct || (given_H && i >= w_cov0 && i < w_cov1) || (i >= w_c0 && i < w_c1) ||
+         i >= w_res;
+}
+
 // Copies the host-built descriptor into device memory, one word per thread,
 // and the grid's h[k] and nc[k] = -1/h_k^2 into its arrays.
 template <int NH>
 __device__ __forceinline__ void setup_copy(DsDev* dst, int64_t* off_dst, const SetupParams<NH>& p) {
   uint64_t* d64 = reinterpret_cast<uint64_t*>(dst);
-  for (int i = threadIdx.x; i < kDsWords; i += blockDim.x) d64[i] = p.init[i];
+  const bool given_H = reinterpret_cast<const DsDev*>(p.init)->given_H != 0;
+  for (int i = threadIdx.x; i < kDsWords; i += blockDim.x)
+    d64[i] = setup_word_copied(i, given_H) ? p.init[i] : 0ull;
   if (threadIdx.x < p.n_off) off_dst[threadIdx.x] = p.off[threadIdx.x];
   for (int k = threadIdx.x; k < p.n_h_pad; k += blockDim.x) {
     if (k < p.n_h) p.h_dst[k] = p.h[k];
@@ -95,6 +117,33 @@ __device__ void block_sum(const V* v, int cnt, double (*scratch)[kNPairs], doubl
     out[threadIdx.x] = t;
   }
   __syncthreads();
+}
+
+// FP64 lanes (FP64 samples): the lane values go through shared memory and one
+// warp per value adds them, 16 per lane in order and then a butterfly.  That
+// is about a quarter of the FP64 work of a butterfly in every warp (FP64 runs
+// at a small fraction of the FP32 rate on this part, and 16 warps of
+// butterflies kept its FP64 unit busy for about 1,300 clocks per value).
+// Values go in rounds of 4 (4 x 512 doubles fit the scratch array).
+__device__ void block_sum(const double* v, int cnt, double (*scratch)[kNPairs], double* out) {
+  constexpr int kPer = 4;
+  static_assert(kPer * kPrepThreads <= (kPrepThreads / 32) * kNPairs, "staging fits the scratch array");
+  double* stage = &scratch[0][0];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k0 = 0; k0 < cnt; k0 += kPer) {
+    const int nk = min(kPer, cnt - k0);
+    for (int k = 0; k < nk; ++k) stage[k * kPrepThreads + threadIdx.x] = v[k0 + k];
+    __syncthreads();
+    if (warp < nk) {
+      const double* col = stage + warp * kPrepThreads;
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < kPrepThreads / 32; ++j) t += col[j * 32 + lane];
+      t = warp_sum(t);
+      if (lane == 0) out[k0 + warp] = t;
+    }
+    __syncthreads();
+  }
 }
 
 // Shared memory of the prologue kernels, declared once per kernel for every
@@ -269,89 +318,106 @@ __device__ __forceinline__ void prep_moments(const DsDev* ds, PrepSmem& sm, int6
 // threads: Cholesky S = L L^T, log|S|, the whitening matrix
 // M = sqrt(log2 e / 4) L^-1, sigma, A and, for the PLUGIN method, psi_8^NS
 // (Eq. PLUGIN-Psi8Estimate) and g1 (Eq. PLUGIN-g1).
+// Returns true (on every thread of the CTA) when this CTA completed the
+// dataset's statistics and they are usable (the CTA of a one-range dataset,
+// or the last range's CTA).
 template <typename TIN, int D>
-__device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
+__device__ __forceinline__ bool prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   const int parts = ds->prep_parts;
-  if (b >= parts) return;
+  if (b >= parts) return false;
   const int64_t n = ds->n;
   const int d = D <= 4 ? D : ds->d;  // dk = d for d <= 4: a compile-time bound there
   int64_t lo, hi;
   prep_range(n, parts, b, lo, hi);
   prep_moments<TIN, D>(ds, sm, lo, hi);
   const int npairs = d * (d + 1) / 2;
-  // one range: the record stays in shared memory where the combination below
-  // reads it, and the CTA is the last by construction
-  const bool single = parts == 1;
-  double* rec = single ? reinterpret_cast<double*>(sm.stage) : ds->prep_part + (size_t)b * kPrepRecord;
-  __syncthreads();  // the moment pass is done with the staging buffer
-  if (threadIdx.x == 0) rec[0] = (double)(hi - lo);
-  if (threadIdx.x < d) {
-    rec[1 + threadIdx.x] = sm.sMean[threadIdx.x];
-    rec[1 + KDE_MAX_D + threadIdx.x] = sizeof(TIN) == 4 ? (double)sm.sMeanF[threadIdx.x] : sm.sMean[threadIdx.x];
-  }
-  if (threadIdx.x < npairs) rec[1 + 2 * KDE_MAX_D + threadIdx.x] = sm.sv[threadIdx.x];
-  if (!single) {
+  double* sMean = sm.sMean;
+  double* sv = sm.sv;
+  float* sM = sm.sM;
+  if (parts == 1) {
+    // one range: mu is the range mean m (already in sMean), and the moments
+    // about mu follow from those about the centre c by one parallel-axis
+    // term, M - n u u^T with u = m - c -- the combination below with a single
+    // record, without its rounding of n m / n.  c = m for FP64 samples (no
+    // term); FP32 samples were centred about the FP32-rounded mean.
+    if constexpr (sizeof(TIN) == 4) {
+      if (!ds->given_H && threadIdx.x < npairs) {
+        int pa = 0, rem = threadIdx.x;
+        while (rem >= d - pa) {
+          rem -= d - pa;
+          ++pa;
+        }
+        const int pb = pa + rem;
+        const double ua = sMean[pa] - (double)sm.sMeanF[pa], ub = sMean[pb] - (double)sm.sMeanF[pb];
+        sv[threadIdx.x] -= (double)(hi - lo) * ua * ub;
+      }
+    }
+    __syncthreads();
+  } else {
+    double* rec = ds->prep_part + (size_t)b * kPrepRecord;
+    if (threadIdx.x == 0) rec[0] = (double)(hi - lo);
+    if (threadIdx.x < d) {
+      rec[1 + threadIdx.x] = sm.sMean[threadIdx.x];
+      rec[1 + KDE_MAX_D + threadIdx.x] = sizeof(TIN) == 4 ? (double)sm.sMeanF[threadIdx.x] : sm.sMean[threadIdx.x];
+    }
+    if (threadIdx.x < npairs) rec[1 + 2 * KDE_MAX_D + threadIdx.x] = sm.sv[threadIdx.x];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) sm.last = (atomicAdd(&ds->prep_count, 1u) == (unsigned)parts - 1u);
     __syncthreads();
-    if (!sm.last) return;
+    if (!sm.last) return false;
     __threadfence();
-  }
-  // ---- combine the records in range order (records staged in shared memory,
-  // kChunk at a time, by coalesced loads; the sums run in range order)
-  double* sMean = sm.sMean;
-  double* sv = sm.sv;
-  float* sM = sm.sM;
-  const double* recs = ds->prep_part;
-  constexpr int kChunk = (int)(sizeof(sm.stage) / (kPrepRecord * sizeof(double)));
-  double* cache = reinterpret_cast<double*>(sm.stage);
-  int pa = 0, pb = 0;
-  if (threadIdx.x < npairs) {
-    int rem = threadIdx.x;
-    while (rem >= d - pa) {
-      rem -= d - pa;
-      ++pa;
-    }
-    pb = pa + rem;
-  }
-  double tmean = 0.0;
-  for (int r0 = 0; r0 < parts; r0 += kChunk) {
-    const int nr = min(kChunk, parts - r0);
-    __syncthreads();
-    if (!single)
-      for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
-        cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
-    __syncthreads();
-    if (threadIdx.x < d)
-      for (int r = 0; r < nr; ++r) tmean += cache[r * kPrepRecord] * cache[r * kPrepRecord + 1 + threadIdx.x];
-  }
-  if (threadIdx.x < d) sMean[threadIdx.x] = tmean / (double)n;
-  __syncthreads();
-  double tpair = 0.0;
-  for (int r0 = 0; r0 < parts && !ds->given_H; r0 += kChunk) {  // a given H needs no S
-    const int nr = min(kChunk, parts - r0);
-    if (parts > kChunk || r0 > 0) {  // one chunk: still cached from the mean pass
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
-        cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
-      __syncthreads();
-    }
-    if (threadIdx.x < npairs)
-      for (int r = 0; r < nr; ++r) {
-        const double* q = cache + r * kPrepRecord;
-        const double nb = q[0];
-        const double ua = q[1 + pa] - q[1 + KDE_MAX_D + pa];
-        const double ub = q[1 + pb] - q[1 + KDE_MAX_D + pb];
-        const double va = q[1 + KDE_MAX_D + pa] - sMean[pa];
-        const double vb = q[1 + KDE_MAX_D + pb] - sMean[pb];
-        tpair += q[1 + 2 * KDE_MAX_D + threadIdx.x] + nb * (ua * vb + va * ub + va * vb);
+    // ---- combine the records in range order (records staged in shared
+    // memory, kChunk at a time, by coalesced loads; the sums run in range order)
+    const double* recs = ds->prep_part;
+    constexpr int kChunk = (int)(sizeof(sm.stage) / (kPrepRecord * sizeof(double)));
+    double* cache = reinterpret_cast<double*>(sm.stage);
+    int pa = 0, pb = 0;
+    if (threadIdx.x < npairs) {
+      int rem = threadIdx.x;
+      while (rem >= d - pa) {
+        rem -= d - pa;
+        ++pa;
       }
+      pb = pa + rem;
+    }
+    double tmean = 0.0;
+    for (int r0 = 0; r0 < parts; r0 += kChunk) {
+      const int nr = min(kChunk, parts - r0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
+        cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
+      __syncthreads();
+      if (threadIdx.x < d)
+        for (int r = 0; r < nr; ++r) tmean += cache[r * kPrepRecord] * cache[r * kPrepRecord + 1 + threadIdx.x];
+    }
+    if (threadIdx.x < d) sMean[threadIdx.x] = tmean / (double)n;
+    __syncthreads();
+    double tpair = 0.0;
+    for (int r0 = 0; r0 < parts && !ds->given_H; r0 += kChunk) {  // a given H needs no S
+      const int nr = min(kChunk, parts - r0);
+      if (parts > kChunk || r0 > 0) {  // one chunk: still cached from the mean pass
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < nr * kPrepRecord; idx += kPrepThreads)
+          cache[idx] = __ldcg(recs + (size_t)r0 * kPrepRecord + idx);
+        __syncthreads();
+      }
+      if (threadIdx.x < npairs)
+        for (int r = 0; r < nr; ++r) {
+          const double* q = cache + r * kPrepRecord;
+          const double nb = q[0];
+          const double ua = q[1 + pa] - q[1 + KDE_MAX_D + pa];
+          const double ub = q[1 + pb] - q[1 + KDE_MAX_D + pb];
+          const double va = q[1 + KDE_MAX_D + pa] - sMean[pa];
+          const double vb = q[1 + KDE_MAX_D + pb] - sMean[pb];
+          tpair += q[1 + 2 * KDE_MAX_D + threadIdx.x] + nb * (ua * vb + va * ub + va * vb);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < npairs) sv[threadIdx.x] = tpair;
+    if (threadIdx.x == 0) ds->prep_count = 0u;  // ready for the next run of this descriptor
+    __syncthreads();
   }
-  __syncthreads();
-  if (threadIdx.x < npairs) sv[threadIdx.x] = tpair;
-  if (threadIdx.x == 0) ds->prep_count = 0u;  // ready for the next run of this descriptor
-  __syncthreads();
   // ---- factorisation, FP64, shared by the CTA's threads (the textbook
   // loops; the inverse multiplies by the reciprocal of each diagonal entry)
   double(*S)[KDE_MAX_D] = reinterpret_cast<double(*)[KDE_MAX_D]>(&sm.scratch[0][0]);
@@ -421,7 +487,7 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   const bool pd = finite && sm.last;
   if (!finite || !pd) {
     if (threadIdx.x == 0) res.status = finite ? KDE_EDEGENERATE : KDE_EINVAL;
-    return;
+    return false;
   }
   // W = L^-1, one column per thread (forward substitution, scaled by the
   // reciprocals of the diagonal); the log of each pivot alongside
@@ -474,6 +540,7 @@ __device__ __forceinline__ void prep_stats(DsDev* ds, PrepSmem& sm, int b) {
     res.logdet_S = logdet;
     ds->A = a;
   }
+  return true;
 }
 
 // Part b of the whitening pass: y = M (x - mean) and x - mean in FP32 for
@@ -485,16 +552,20 @@ struct WhitenSmem {
   float sMeanF[KDE_MAX_D];
 };
 
+// M and the mean come from srcM / srcMean: the descriptor (a separate
+// whitening launch) or, in the CTA that just computed them, its shared memory
+// (no read-back of its own global writes).  The caller checks the status.
 template <typename TIN, int D>
-__device__ __forceinline__ void prep_whiten(const DsDev* ds, WhitenSmem& sm, int b) {
+__device__ __forceinline__ void prep_whiten(const DsDev* ds, WhitenSmem& sm, int b, const float* srcM,
+                                            const double* srcMean) {
   const int parts = ds->prep_parts;
-  if (b >= parts || ds->res.status != KDE_OK) return;
+  if (b >= parts) return;
   const TIN* __restrict__ x = static_cast<const TIN*>(ds->x);
   const int64_t n = ds->n, n_pad = ds->n_pad;
   const int d = D <= 4 ? D : ds->d, dk = D <= 4 ? D : ds->dk;  // compile-time for d <= 4
-  for (int k = threadIdx.x; k < KDE_MAX_D * KDE_MAX_D; k += kPrepThreads) sm.sM[k] = ds->M[k];
+  for (int k = threadIdx.x; k < KDE_MAX_D * KDE_MAX_D; k += kPrepThreads) sm.sM[k] = srcM[k];
   if (threadIdx.x < KDE_MAX_D) {
-    sm.sMean[threadIdx.x] = threadIdx.x < d ? ds->mean[threadIdx.x] : 0.0;
+    sm.sMean[threadIdx.x] = threadIdx.x < d ? srcMean[threadIdx.x] : 0.0;
     sm.sMeanF[threadIdx.x] = (float)sm.sMean[threadIdx.x];
   }
   __syncthreads();
@@ -541,28 +612,29 @@ __device__ __forceinline__ void prep_whiten(const DsDev* ds, WhitenSmem& sm, int
 }
 
 template <typename TIN>
-__device__ __forceinline__ void stats_dispatch(DsDev* ds, PrepSmem& sm, int b) {
+__device__ __forceinline__ bool stats_dispatch(DsDev* ds, PrepSmem& sm, int b) {
   switch (ds->dk) {
-    case 1: prep_stats<TIN, 1>(ds, sm, b); break;
-    case 2: prep_stats<TIN, 2>(ds, sm, b); break;
-    case 3: prep_stats<TIN, 3>(ds, sm, b); break;
-    case 4: prep_stats<TIN, 4>(ds, sm, b); break;
-    case 8: prep_stats<TIN, 8>(ds, sm, b); break;
-    case 12: prep_stats<TIN, 12>(ds, sm, b); break;
-    default: prep_stats<TIN, 16>(ds, sm, b); break;
+    case 1: return prep_stats<TIN, 1>(ds, sm, b);
+    case 2: return prep_stats<TIN, 2>(ds, sm, b);
+    case 3: return prep_stats<TIN, 3>(ds, sm, b);
+    case 4: return prep_stats<TIN, 4>(ds, sm, b);
+    case 8: return prep_stats<TIN, 8>(ds, sm, b);
+    case 12: return prep_stats<TIN, 12>(ds, sm, b);
+    default: return prep_stats<TIN, 16>(ds, sm, b);
   }
 }
 
 template <typename TIN>
-__device__ __forceinline__ void whiten_dispatch(DsDev* ds, WhitenSmem& sm, int b) {
+__device__ __forceinline__ void whiten_dispatch(DsDev* ds, WhitenSmem& sm, int b, const float* srcM,
+                                                const double* srcMean) {
   switch (ds->dk) {
-    case 1: prep_whiten<TIN, 1>(ds, sm, b); break;
-    case 2: prep_whiten<TIN, 2>(ds, sm, b); break;
-    case 3: prep_whiten<TIN, 3>(ds, sm, b); break;
-    case 4: prep_whiten<TIN, 4>(ds, sm, b); break;
-    case 8: prep_whiten<TIN, 8>(ds, sm, b); break;
-    case 12: prep_whiten<TIN, 12>(ds, sm, b); break;
-    default: prep_whiten<TIN, 16>(ds, sm, b); break;
+    case 1: prep_whiten<TIN, 1>(ds, sm, b, srcM, srcMean); break;
+    case 2: prep_whiten<TIN, 2>(ds, sm, b, srcM, srcMean); break;
+    case 3: prep_whiten<TIN, 3>(ds, sm, b, srcM, srcMean); break;
+    case 4: prep_whiten<TIN, 4>(ds, sm, b, srcM, srcMean); break;
+    case 8: prep_whiten<TIN, 8>(ds, sm, b, srcM, srcMean); break;
+    case 12: prep_whiten<TIN, 12>(ds, sm, b, srcM, srcMean); break;
+    default: prep_whiten<TIN, 16>(ds, sm, b, srcM, srcMean); break;
   }
 }
 
@@ -574,17 +646,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_prep_stats(DsDev* dsa, const i
   __shared__ PrepSmem sm;
   dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
-  if (ds->dtype == KDE_F64)
-    stats_dispatch<double>(ds, sm, blockIdx.x);
-  else
-    stats_dispatch<float>(ds, sm, blockIdx.x);
-  if (whiten) {
+  const bool ok = ds->dtype == KDE_F64 ? stats_dispatch<double>(ds, sm, blockIdx.x)
+                                       : stats_dispatch<float>(ds, sm, blockIdx.x);
+  if (whiten && ok) {  // one range: this CTA's M and mean, from its shared memory
     __shared__ WhitenSmem wm;
-    __syncthreads();  // M, mean and the status are written by this CTA's threads
+    __syncthreads();
     if (ds->dtype == KDE_F64)
-      whiten_dispatch<double>(ds, wm, blockIdx.x);
+      whiten_dispatch<double>(ds, wm, blockIdx.x, sm.sM, sm.sMean);
     else
-      whiten_dispatch<float>(ds, wm, blockIdx.x);
+      whiten_dispatch<float>(ds, wm, blockIdx.x, sm.sM, sm.sMean);
   }
 }
 
@@ -599,25 +669,24 @@ __global__ void __launch_bounds__(kPrepThreads) k_setup_prep1(DsDev* ds, int64_t
   dependent_launch_wait();
   setup_copy(ds, off_dst, p);
   __syncthreads();  // the descriptor this CTA just wrote is read below
-  if (ds->dtype == KDE_F64)
-    stats_dispatch<double>(ds, sm, 0);
-  else
-    stats_dispatch<float>(ds, sm, 0);
+  const bool ok = ds->dtype == KDE_F64 ? stats_dispatch<double>(ds, sm, 0) : stats_dispatch<float>(ds, sm, 0);
+  if (!ok) return;
   __syncthreads();
   if (ds->dtype == KDE_F64)
-    whiten_dispatch<double>(ds, wm, 0);
+    whiten_dispatch<double>(ds, wm, 0, sm.sM, sm.sMean);
   else
-    whiten_dispatch<float>(ds, wm, 0);
+    whiten_dispatch<float>(ds, wm, 0, sm.sM, sm.sMean);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_prep_whiten(DsDev* dsa, const int* ids) {
   __shared__ WhitenSmem sm;
   dependent_launch_wait();
   DsDev* ds = dsa + (ids ? ids[blockIdx.y] : (int)blockIdx.y);
+  if (ds->res.status != KDE_OK) return;
   if (ds->dtype == KDE_F64)
-    whiten_dispatch<double>(ds, sm, blockIdx.x);
+    whiten_dispatch<double>(ds, sm, blockIdx.x, ds->M, ds->mean);
   else
-    whiten_dispatch<float>(ds, sm, blockIdx.x);
+    whiten_dispatch<float>(ds, sm, blockIdx.x, ds->M, ds->mean);
 }
 
 constexpr int kProbeThreads = 1024;
@@ -669,9 +738,11 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe(double* out, int iters,
 }  // namespace
 
 template <int NH>
-static void fill_setup(SetupParams<NH>* p, const DsDev& init, const double* h, int n_h,
-                       const int64_t* off_src, int n_off) {
+static cudaError_t fill_setup(SetupParams<NH>* p, const DsDev& init, const double* h, int n_h,
+                              const int64_t* off_src, int n_off) {
   memcpy(p->init, &init, sizeof(DsDev));
+  for (int i = 0; i < kDsWords; ++i)  // the device copies only these words (setup_word_copied)
+    if (p->init[i] != 0 && !setup_word_copied(i, init.given_H != 0)) return cudaErrorInvalidValue;
   p->n_off = n_off;
   for (int k = 0; k < 4; ++k) p->off[k] = k < n_off ? off_src[k] : 0;
   p->n_h = std::min(n_h, NH);
@@ -682,13 +753,15 @@ static void fill_setup(SetupParams<NH>* p, const DsDev& init, const double* h, i
     p->h[k] = k < p->n_h ? h[k] : 0.0;
     p->nc[k] = k < p->n_h ? (float)(-1.0 / (h[k] * h[k])) : -1.0f;
   }
+  return cudaSuccess;
 }
 
 template <int NH>
 static cudaError_t launch_setup_t(DsDev* dst, const DsDev& init, const double* h, int n_h,
                                   int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams<NH> p;
-  fill_setup(&p, init, h, n_h, off_src, n_off);
+  const cudaError_t e = fill_setup(&p, init, h, n_h, off_src, n_off);
+  if (e != cudaSuccess) return e;
   return launch_kernel(k_setup<NH>, dim3(1), dim3(256), 0, st, dst, off_dst, p);
 }
 
@@ -703,7 +776,8 @@ template <int NH>
 static cudaError_t launch_setup_prep1_t(DsDev* dst, const DsDev& init, const double* h, int n_h,
                                         int64_t* off_dst, const int64_t* off_src, int n_off, cudaStream_t st) {
   SetupParams<NH> p;
-  fill_setup(&p, init, h, n_h, off_src, n_off);
+  const cudaError_t e = fill_setup(&p, init, h, n_h, off_src, n_off);
+  if (e != cudaSuccess) return e;
   return launch_kernel(k_setup_prep1<NH>, dim3(1), dim3(kPrepThreads), 0, st, dst, off_dst, p);
 }
 
