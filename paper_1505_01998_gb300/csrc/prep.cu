@@ -121,10 +121,10 @@ __device__ void block_sum(const V* v, int cnt, double (*scratch)[kNPairs], doubl
 
 // FP64 lanes (FP64 samples): the lane values go through shared memory and one
 // warp per value adds them, 16 per lane in order and then a butterfly.  That
-// is about a quarter of the FP64 work of a butterfly in every warp (FP64 runs
-// at a small fraction of the FP32 rate on this part, and 16 warps of
-// butterflies kept its FP64 unit busy for about 1,300 clocks per value).
-// Values go in rounds of 4 (4 x 512 doubles fit the scratch array).
+// is about a quarter of the FP64 operations of a butterfly in every warp (FP64
+// runs at a small fraction of the FP32 rate on this part); measured at
+// n = 1,024, about 900 clocks less per moment pass.  Values go in rounds of 4
+// (4 x 512 doubles fit the scratch array).
 __device__ void block_sum(const double* v, int cnt, double (*scratch)[kNPairs], double* out) {
   constexpr int kPer = 4;
   static_assert(kPer * kPrepThreads <= (kPrepThreads / 32) * kNPairs, "staging fits the scratch array");
