@@ -93,19 +93,16 @@ struct Acc<double> {
   __device__ double lane() const { return s; }
 };
 
-// Warp total of one value per lane into *dst (lane 0): FP64 lanes by an FP64
-// butterfly; double-float lanes (FP32 input) in FP32 arithmetic.
-__device__ __forceinline__ void warp_total(double v, double* dst, int lane) {
-  v = warp_sum(v);
-  if (lane == 0) *dst = v;
-}
+// Warp total of one double-float value per lane (FP32 samples) into *dst
+// (lane 0), in FP32 arithmetic.
 __device__ __forceinline__ void warp_total(float2 v, double* dst, int lane) {
   const float2 t = warp_sum_ff(v.x, v.y);
   if (lane == 0) *dst = ff_value(t);
 }
 
 // Block-wide sum of `cnt` values per thread, deterministic order; results
-// land in out[0..cnt) (shared memory, FP64) for every thread.
+// land in out[0..cnt) (shared memory, FP64) for every thread.  Double-float
+// lanes (FP32 samples): a butterfly per warp, then the warp totals in FP64.
 template <typename V>
 __device__ void block_sum(const V* v, int cnt, double (*scratch)[kNPairs], double* out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
