@@ -290,6 +290,48 @@ def test_lscv_host_and_async_paths_match(kde):
     assert np.array_equal(g1, g3) and r3 == r1
 
 
+def test_back_to_back_async_calls_on_one_stream(kde):
+    """Single calls launch with programmatic dependent launch: each kernel
+    may be scheduled while the previous one drains and waits (PTX
+    griddepcontrol.wait) before touching memory.  Queued without any
+    synchronisation on one stream -- samples written by a torch kernel just
+    before, a workspace reused while the earlier selection that used it may
+    still run, LSCV and PLUGIN interleaved -- every result equals the same
+    call made alone and synchronised."""
+    import torch
+    n1, n2, n3 = 3000, 1000, 20000
+    xa = datagen.mixture_1d(n1, seed=31)[0].astype(np.float32)
+    xb = datagen.skewed_column(n2, seed=32)[0].astype(np.float32)
+    xc = datagen.skewed_column(n3, seed=33)[0].astype(np.float32)
+    ga = _explicit(kde, oracle.grid_log(0.02, 2.0, 64))
+    gc = _explicit(kde, oracle.grid_default(n3, 1, 256))
+    ref_a = kde.kde_lscv(dev(xa), ga)
+    ref_b = kde.kde_plugin(dev(xb))
+    ref_c = kde.kde_lscv(dev(xc), gc)
+    ws1 = kde.workspace(max(kde.kde_workspace_size(n, 1, 256) for n in (n1, n3)))
+    ws2 = kde.workspace(kde.kde_workspace_size(n2, 1, 0))
+    da, db, dc = (torch.empty((1, n), dtype=torch.float32, device="cuda") for n in (n1, n2, n3))
+    src = [dev(x) for x in (xa, xb, xc)]
+    torch.cuda.synchronize()
+    for rep in range(3):
+        for t, sx in zip((da, db, dc), src):
+            t.fill_(float("nan"))
+            torch.add(sx, 0.0, out=t)  # the samples come from a torch kernel right before the calls
+        kde.kde_lscv_async(da, ga, None, ws1)
+        kde.kde_plugin_async(db, None, ws2)
+        torch.cuda.synchronize()
+        res_a, g_a = kde.read_ws_result(ws1, 64)
+        assert res_a == ref_a[0] and np.array_equal(g_a, ref_a[1]), rep
+        kde.kde_lscv_async(da, ga, None, ws1)
+        kde.kde_plugin_async(db, None, ws2)
+        kde.kde_lscv_async(dc, gc, None, ws1)  # ws1 reused right behind the first selection
+        torch.cuda.synchronize()
+        res_c, g_c = kde.read_ws_result(ws1, 256)
+        res_b, _ = kde.read_ws_result(ws2, 0)
+        assert res_c == ref_c[0] and np.array_equal(g_c, ref_c[1]), rep
+        assert res_b == ref_b, rep
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_two_and_three_samples(kde):
