@@ -561,12 +561,12 @@ def run_configs(args):
     time.sleep(0.3)
     out = []
 
-    def median_ms(fn, kernel_events=False):
+    def median_ms(fn, kernel_events=False, reps=None):
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
         call, kern = [], []
-        for _ in range(K):
+        for _ in range(reps or K):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             e1.record(stream)
@@ -590,20 +590,23 @@ def run_configs(args):
     ws = gbkde.workspace(max(gbkde.kde_workspace_size(n, 1, 64), gbkde.kde_workspace_size(n, 1, 0)))
     P = n * (n - 1) // 2
     evals = P * (64 + 2)
-    sel_ms, _ = median_ms(lambda: (gbkde.kde_lscv(xd, grid, None, ws, stream), gbkde.kde_plugin(xd, None, ws, stream)))
+    # n = 1,024 calls take about 0.1 ms: medians of 200 (host-side jitter of a few us per call)
+    K1 = max(K, 200)
+    sel_ms, _ = median_ms(lambda: (gbkde.kde_lscv(xd, grid, None, ws, stream), gbkde.kde_plugin(xd, None, ws, stream)),
+                          reps=K1)
     # both selections as one replayed batch plan (one prologue, one graph launch)
     req, req_keep = gbkde.make_request(xd, gbkde.KDE_METHOD_LSCV | gbkde.KDE_METHOD_PLUGIN, grid)
     plan = gbkde.BatchPlan([req], keepalive=[req_keep])
     ws_plan = gbkde.workspace(plan.ws_bytes)
-    plan_ms, _ = median_ms(lambda: plan.run(ws_plan, stream))
+    plan_ms, _ = median_ms(lambda: plan.run(ws_plan, stream), reps=K1)
     plan_res = plan.run(ws_plan, stream)[0]
     sep_l = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
     sep_p = gbkde.kde_plugin(xd, None, ws, stream)
     plan_same = plan_res["h"] == sep_l["h"] and plan_res["h_plugin"] == sep_p["h"]
-    _, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True)
+    _, kern_ms = median_ms(lambda: gbkde.kde_lscv(xd, grid, None, ws, stream), kernel_events=True, reps=K1)
     xh = torch.from_numpy(x).pin_memory().numpy()
     e2e_ms, _ = median_ms(lambda: (gbkde.kde_lscv_host(xh, grid, None, ws, stream),
-                                   gbkde.kde_plugin_host(xh, None, ws, stream)))
+                                   gbkde.kde_plugin_host(xh, None, ws, stream)), reps=K1)
     t0 = time.perf_counter()
     oracle.lscv_h(x, h)
     oracle.plugin(x)
