@@ -494,7 +494,8 @@ __device__ __forceinline__ bool prep_stats(DsDev* ds, PrepSmem& sm, int b) {
   // logs: with r = 1 / sigma from one reciprocal square root, sigma = S_00 r,
   // psi_8^NS = 105 / (32 sqrt(pi) sigma^9) = c r^9 and
   // g1 = (-2 K6(0) / (psi_8^NS n))^(1/9) = sigma c_g1 (c_g1 of n from the
-  // host), so no FP64 division, square root or pow lies on this chain
+  // host): the chain's one long FP64 operation is the reciprocal square root
+  // (the division of the psi scale, of two known constants, runs beside it)
   if (threadIdx.x == 32) {
     const double s00 = S[0][0];
     const double rs = rsqrt(s00);
