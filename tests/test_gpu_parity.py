@@ -332,6 +332,36 @@ def test_back_to_back_async_calls_on_one_stream(kde):
         assert res_b == ref_b, rep
 
 
+def test_single_calls_captured_in_a_cuda_graph(kde):
+    """Async single calls captured into a CUDA graph by the caller (their
+    programmatic dependent launches become graph edges) and replayed: the
+    results equal those of the same calls made directly, on every replay."""
+    import torch
+    n = 5000
+    x = datagen.skewed_column(n, seed=41)[0].astype(np.float32)
+    grid = _explicit(kde, oracle.grid_default(n, 1, 128))
+    ref_l = kde.kde_lscv(dev(x), grid)
+    ref_p = kde.kde_plugin(dev(x))
+    xd = dev(x)
+    ws_l = kde.workspace(kde.kde_workspace_size(n, 1, 128))
+    ws_p = kde.workspace(kde.kde_workspace_size(n, 1, 0))
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = torch.cuda.current_stream()
+        kde.kde_lscv_async(xd, grid, None, ws_l, st)
+        kde.kde_plugin_async(xd, None, ws_p, st)
+    for _ in range(3):
+        ws_l.zero_()
+        ws_p.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        res_l, g_l = kde.read_ws_result(ws_l, 128)
+        res_p, _ = kde.read_ws_result(ws_p, 0)
+        assert res_l == ref_l[0] and np.array_equal(g_l, ref_l[1])
+        assert res_p == ref_p
+
+
 # ------------------------------------------------------------ edge cases
 
 def test_two_and_three_samples(kde):
