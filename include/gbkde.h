@@ -270,7 +270,7 @@ int kde_plugin_host(const void* x_host, int dtype, int64_t n, const kde_opts* op
                     size_t ws_bytes, void* stream, kde_result* out);
 
 /* Raw psi pair sum over the tiles [tile_begin, tile_end) of the pair
- * triangle (tile edge 32 * psi rows per lane, see kde_psi_tile_edge):
+ * triangle (tile edge 64, 256 or 512 by n, see kde_psi_tile_edge):
  *   sum K^(r)((x_i - x_j)/g) over pairs i < j < n in those tiles, r in {4,6,8}. */
 int kde_psi_tile_sums(const void* x_dev, int dtype, int64_t n, int r, double g,
                       int64_t tile_begin, int64_t tile_end, const kde_opts* opts, void* ws,

@@ -197,13 +197,34 @@ int make_geometry(int64_t n, int d, int n_h, const kde_opts* o, int sms, Geometr
   g->rows = (g->tiles + g->K - 1) / g->K;
   g->rows_oct = (g->tiles + g->K_oct - 1) / g->K_oct;
   g->items = g->rows * g->G;
-  // psi
-  g->Tp = n >= 16384 ? 256 : 64;
+  // psi: tiles of 512 (two row groups per CTA) from n = 65,536, where the
+  // per-tile work is the larger share of a 256-tile; about 4 items per CTA,
+  // and with the default CTA count the tiles per item, between half that
+  // rule's and the rule's, that fill the last wave best.  The server's item
+  // cap applies after that choice and is above the rule's count at the
+  // sizes it serves, so a served request has the items, and so the bits, of
+  // the same single call.
+  g->Tp = n >= 65536 ? 512 : (n >= 16384 ? 256 : 64);
   g->Rp = g->Tp / 32;
   g->ptiles = tri_tiles(n, g->Tp);
   {
     const int64_t target = 4 * (int64_t)g->ctas;
     g->Kp = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (g->ptiles + target - 1) / target));
+    if (!cps_given) {
+      const int64_t C = g->ctas, k0 = g->Kp;
+      auto balance = [&](int64_t K) {
+        const int64_t items = (g->ptiles + K - 1) / K;
+        return (double)items / ((double)C * (double)((items + C - 1) / C));
+      };
+      double be = balance(k0);
+      for (int64_t K = std::max<int64_t>(1, k0 / 2); K <= k0; ++K) {
+        const double e = balance(K);
+        if (e > be + 1e-12 || (e > be - 1e-12 && K > g->Kp)) {
+          g->Kp = (int)K;
+          be = e;
+        }
+      }
+    }
     if (max_item_evals > 0)
       g->Kp = (int)std::max<int64_t>(1, std::min<int64_t>(g->Kp, (int64_t)(max_item_evals / ((double)g->Tp * g->Tp))));
   }

@@ -12,7 +12,7 @@ namespace gbkde {
 
 constexpr int kThreads = 256;  // threads per CTA of every pair kernel (8 warps)
 constexpr int kWarps = kThreads / 32;
-constexpr int kPadTo = 256;    // sample arrays are zero-padded to a multiple of this
+constexpr int kPadTo = 512;    // sample arrays are zero-padded to a multiple of this (the largest tile edge)
 
 // Per-dataset descriptor, resident in device memory for the whole selection.
 // Host code fills the geometry; the prologue kernel fills the statistics; the

@@ -14,10 +14,14 @@
 // time in FP32x2 -- r/2 + 2 FP32 lane-operations per pair.
 //
 // Schedule: T x T tiles of the pair triangle in the numbering of Sec. 5.4.2;
-// items of K consecutive tiles; persistent CTAs of 8 warps; each warp covers
-// all T rows (R per lane, in registers) against a slice of T/8 columns staged
-// in shared memory.  Per-lane FP32 runs over a tile are folded into a Kahan
-// pair; item totals are reduced in FP64 and written to a per-item slot.
+// items of K consecutive tiles; persistent CTAs of 8 warps in RG row groups
+// of 32 R rows (R per lane, in registers), T = 32 R RG; each warp covers its
+// group's rows against a slice of RG T / 8 columns staged in shared memory.
+// Two row groups (T = 512) give each warp four times the pairs per tile of
+// one (T = 256), so the per-tile work (row loads, scaling, Kahan fold, tile
+// bookkeeping) is spread over more evaluations.  Per-lane FP32 runs over a
+// tile are folded into a Kahan pair; item totals are reduced in FP64 and
+// written to a per-item slot.
 #include "host.hpp"
 #include "internal.cuh"
 
@@ -28,11 +32,16 @@ namespace {
 constexpr double kSqrtHalfLog2e = 0.8493218002880191;  // sqrt(log2(e) / 2) in FP64
 constexpr double kRK = 0.28209479177387814;  // R(K) = 1 / (2 sqrt(pi)) of the Gaussian kernel, FP64
 
-template <int RD, int R, bool EDGE>
+// Columns [j_lo, j_hi) of one tile for this lane's R rows, CPI columns per
+// iteration.  Edge tiles mask by tile-local 32-bit indices: row il0 + 64 p
+// (+ 32 for the second of a packed pair) and column jj + c, kept when
+// il < jl < jlim.  il0 is the lane's first row relative to the column tile
+// (negative for tiles off the diagonal, whose rows all precede their
+// columns) and jlim the number of real columns of the tile.
+template <int RD, int R, int CPI, bool EDGE>
 __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_lo, int j_hi,
                                             const float2 (&z)[R / 2], float2 (&acc)[R / 2],
-                                            const PsiCoef& cf, int64_t i0, int64_t jg0,
-                                            int64_t n) {
+                                            const PsiCoef& cf, int il0, int jlim) {
   constexpr int M = RD / 2;
   float2 cc[M - 1];
 #pragma unroll
@@ -40,13 +49,16 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
   const float2 sh2 = make_float2(cf.shift, cf.shift);
   // sF holds each column sample as the pair (-v, -v): two columns per 16 bytes
 #pragma unroll 1
-  for (int jj = j_lo; jj < j_hi; jj += 4) {
-    const float4 v01 = *reinterpret_cast<const float4*>(sF + 2 * jj);
-    const float4 v23 = *reinterpret_cast<const float4*>(sF + 2 * jj + 4);
-    const float2 nfs[4] = {make_float2(v01.x, v01.y), make_float2(v01.z, v01.w),
-                           make_float2(v23.x, v23.y), make_float2(v23.z, v23.w)};
+  for (int jj = j_lo; jj < j_hi; jj += CPI) {
+    float2 nfs[CPI];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int u = 0; u < CPI / 2; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(sF + 2 * jj + 4 * u);
+      nfs[2 * u] = make_float2(v.x, v.y);
+      nfs[2 * u + 1] = make_float2(v.z, v.w);
+    }
+#pragma unroll
+    for (int c = 0; c < CPI; ++c) {
       const float2 nf = nfs[c];
 #pragma unroll
       for (int p = 0; p < R / 2; ++p) {
@@ -54,9 +66,9 @@ __device__ __forceinline__ void psi_columns(const float* __restrict__ sF, int j_
         const float2 w = __ffma2_rn(dl, dl, sh2);  // y + shift
         float2 e = make_float2(ex2_neg(w.x), ex2_neg(w.y));
         if (EDGE) {
-          const int64_t i = i0 + 64 * p, j = jg0 + jj + c;
-          if (!(i < j && j < n)) e.x = 0.f;
-          if (!(i + 32 < j && j < n)) e.y = 0.f;
+          const int il = il0 + 64 * p, jl = jj + c;
+          if (!(il < jl && jl < jlim)) e.x = 0.f;
+          if (!(il + 32 < jl && jl < jlim)) e.y = 0.f;
         }
         float2 q = __ffma2_rn(w, w, cc[0]);
 #pragma unroll
@@ -85,15 +97,20 @@ __device__ __noinline__ void psi_fused_finish(const Phase& ph, int r, double pos
   if (threadIdx.x == 0) ds->pair_count = 0u;
 }
 
-template <int RD, int R, bool KAHAN>
+template <int RD, int R, int RG, bool KAHAN>
 __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
   dependent_launch_wait();
-  constexpr int T = 32 * R;
+  constexpr int T = 32 * R * RG;
+  constexpr int SL = kWarps / RG;     // column slices per tile
+  constexpr int CPI = R >= 8 ? 8 : 4;  // columns per inner iteration
+  static_assert(kWarps % RG == 0 && (T / SL) % CPI == 0, "psi warp layout");
   __shared__ __align__(16) float sF[2 * T];  // (-v, -v) per column
   __shared__ double sRed[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int cols = T / kWarps;
-  const int j_lo = warp * cols, j_hi = j_lo + cols;
+  const int rg = warp / SL;
+  constexpr int cols = T / SL;
+  const int j_lo = (warp % SL) * cols, j_hi = j_lo + cols;
+  const int r0 = rg * 32 * R + lane;  // the lane's first row within a tile
 
   for (int64_t it = blockIdx.x; it < ph.total; it += gridDim.x) {
     const int di = find_ds(ph.off, ph.n_ds, it);
@@ -117,7 +134,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
     // so an exposed global-load latency per tile would cost ~10 %)
     float zr[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) zr[k] = X[q * T + lane + 32 * k];
+    for (int k = 0; k < R; ++k) zr[k] = X[q * T + r0 + 32 * k];
     for (int64_t t = t0; t < t1; ++t) {
       if (l != l_loaded) {
         __syncthreads();
@@ -135,15 +152,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_psi(Phase ph, PsiCoef cf) {
         const int64_t qn = (q + 1 > l) ? 0 : q + 1;
         if (t + 1 < t1) {
 #pragma unroll
-          for (int k = 0; k < R; ++k) zr[k] = X[qn * T + lane + 32 * k];
+          for (int k = 0; k < R; ++k) zr[k] = X[qn * T + r0 + 32 * k];
         }
       }
       const bool edge = (q == l) || ((l + 1) * T > n);
-      const int64_t i0 = q * T + lane, jg0 = l * T;
-      if (edge)
-        psi_columns<RD, R, true>(sF, j_lo, j_hi, z, acc, cf, i0, jg0, n);
-      else
-        psi_columns<RD, R, false>(sF, j_lo, j_hi, z, acc, cf, i0, jg0, n);
+      if (edge) {
+        const int il0 = (q == l) ? r0 : -(1 << 30);
+        const int jlim = (int)min((int64_t)T, n - l * T);
+        psi_columns<RD, R, CPI, true>(sF, j_lo, j_hi, z, acc, cf, il0, jlim);
+      } else {
+        psi_columns<RD, R, CPI, false>(sF, j_lo, j_hi, z, acc, cf, 0, 0);
+      }
       if (KAHAN) {
         float run = 0.f;
 #pragma unroll
@@ -266,18 +285,21 @@ __global__ void __launch_bounds__(kThreads) k_psi_finish(DsDev* dsa, const int* 
   psi_finish_body(ds, stage, r, post);
 }
 
-template <int RD, int R>
+template <int RD, int R, int RG>
 cudaError_t launch_k(const Phase& ph, bool kahan, const PsiCoef& cf, int grid, cudaStream_t st) {
-  if (kahan) return launch_kernel(k_psi<RD, R, true>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
-  return launch_kernel(k_psi<RD, R, false>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
+  if (kahan) return launch_kernel(k_psi<RD, R, RG, true>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
+  return launch_kernel(k_psi<RD, R, RG, false>, dim3(grid), dim3(kThreads), 0, st, ph, cf);
 }
 
+// Rp = T / 32: 2 (T = 64), 8 (T = 256) or 16 (T = 512: two row groups of 8
+// rows per lane).
 template <int RD>
-cudaError_t launch_r(const Phase& ph, int R, bool kahan, const PsiCoef& cf, int grid,
+cudaError_t launch_r(const Phase& ph, int Rp, bool kahan, const PsiCoef& cf, int grid,
                      cudaStream_t st) {
-  switch (R) {
-    case 2: return launch_k<RD, 2>(ph, kahan, cf, grid, st);
-    case 8: return launch_k<RD, 8>(ph, kahan, cf, grid, st);
+  switch (Rp) {
+    case 2: return launch_k<RD, 2, 1>(ph, kahan, cf, grid, st);
+    case 8: return launch_k<RD, 8, 1>(ph, kahan, cf, grid, st);
+    case 16: return launch_k<RD, 8, 2>(ph, kahan, cf, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -94,6 +94,29 @@ def test_psi_tile_ranges_add_up(kde, n):
     assert abs(parts[3] - ref) <= TOL * max(abs(ref), mag)
 
 
+def test_psi_largest_tiles_ragged_tail(kde):
+    """n = 65,869 (a ragged last tile column): psi tiles of 512 (two row
+    groups of 256 rows per CTA) against the oracle's block sums on the first
+    tiles (two diagonal), a middle range and the ragged last column, and the
+    full range of psi_6 against the oracle's whole double sum."""
+    n = 65536 + 333
+    x = datagen.skewed_column(n, seed=41)[0]
+    xd = dev(x)
+    x64 = host64(x)[0]
+    T = kde.kde_psi_tile_edge(n)
+    assert T == 512
+    tiles = kde.kde_tile_count(n, T)
+    for r, g in ((6, 3.0), (4, 0.7)):
+        for tb, te in ((0, 3), (tiles // 2, tiles // 2 + 2), (tiles - 3, tiles)):
+            got = kde.kde_psi_tile_sums(xd, r, g, tb, te)
+            ref, mag = oracle_tile_sums_psi(x64, r, g, T, tb, te, kde)
+            assert abs(got - ref) <= TOL * max(abs(ref), mag), (r, tb, te, got, ref, mag)
+    got = kde.kde_psi_tile_sums(xd, 6, 3.0, 0, tiles)
+    ref = oracle.psi_pair_sum(x64, 6, 3.0)
+    mag = oracle.psi_abs_pair_sum(x64, 6, 3.0)
+    assert abs(got - ref) <= TOL * max(abs(ref), mag), (got, ref, mag)
+
+
 # -------------------------------------------------------------- plug-in
 
 def _plugin_compare(res, ref, x64):
