@@ -499,7 +499,10 @@ __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phas
     }
     const int64_t n = ds->n, n_pad = ds->n_pad;
     const float* __restrict__ Y = ds->y;
-    const int flush_every = max(1, 256 / (R * cols));
+    // tiles per Kahan fold: FP32 runs of at least 256 terms per running sum,
+    // 1,024 in the octave kernel (its fold of 9 packed sums per tile was
+    // 0.35 % of a full-size launch: 30.60 -> 30.49 ms with every other tile)
+    const int flush_every = OCT ? max(1, 1024 / (R * cols)) : max(1, 256 / (R * cols));
     int64_t l, q;
     tile_coords(tb, l, q);
     int64_t l_loaded = -1;
