@@ -5,7 +5,10 @@ library).  Run from the repository root: ``python tests/golden/make_golden.py``
 (toy set), ``python tests/golden/make_golden.py --full-skewed`` (the full
 n = 65,536 skewed-column oracle; minutes on a multi-core host) and
 ``python tests/golden/make_golden.py --full-mixture`` (the full n = 16,384,
-d = 2, 3, 4 correlated-mixture oracle; minutes).
+d = 2, 3, 4 correlated-mixture oracle; minutes) and
+``python tests/golden/make_golden.py --batch`` (the 512-dataset batch: the
+full oracle of every dataset with n <= 16,384 and of the 16 smallest above;
+about an hour on 8 host cores).
 """
 import json
 import os
@@ -70,7 +73,58 @@ def full_correlated_mixture():
         json.dump(out, f, indent=1)
 
 
+def batch_subset():
+    """The full oracle of the batched workload's datasets (datagen.batch(512,
+    seed=4): sizes log-uniform on [256, 131072], each a 1-5 component mixture
+    or a lognormal): every dataset with n <= 16,384 and the 16 smallest above
+    it, each LSCV_h on the 128-point grid over Z(h0) (Sec. 4.4.2, Eq.
+    LSCV-Zh0) and the PLUGIN chain (Sec. 4.4.1).  Stored per dataset: the
+    argmin, g(h) with both exponential sums at the indices within 2 of it and
+    at every 32nd index and the last, A = (4 pi)^(-1/2) S^(-1/2), and the
+    PLUGIN values with the magnitude sums sum|K^(r)| of psi_6 at g1 and psi_4
+    at g2 (the scales of their tolerances)."""
+    from paper_1505_01998_gb300 import datagen
+    n_h = 128
+    sets = datagen.batch(512, seed=4)
+    sizes = np.array([x.shape[1] for x in sets])
+    above = sorted((int(n), i) for i, n in enumerate(sizes) if n > 16384)[:16]
+    chosen = sorted([i for i, n in enumerate(sizes) if n <= 16384] + [i for _, i in above])
+    cases = []
+    for i in chosen:
+        x = sets[i].astype(np.float64)  # the FP32 values the device sees
+        n = x.shape[1]
+        h = oracle.grid_default(n, 1, n_h)
+        r = oracle.lscv_h(x, h)
+        p = oracle.plugin(x[0])
+        k0 = int(r["argmin"])
+        idx = sorted(set(range(max(0, k0 - 2), min(n_h, k0 + 3))) | set(range(0, n_h, 32)) | {n_h - 1})
+        _, S = oracle.mean_cov(x)
+        case = {"i": i, "n": int(n), "argmin": k0, "idx": idx,
+                "g": [float(r["g"][k]) for k in idx], "s_kk": [float(r["s_kk"][k]) for k in idx],
+                "s_k": [float(r["s_k"][k]) for k in idx],
+                "A": float((4 * np.pi) ** -0.5 / np.sqrt(S[0, 0])),
+                "plugin_status": int(p["status"]),
+                "plugin": {k: float(p[k]) for k in ("sigma", "g1", "psi6", "g2", "psi4", "h")}}
+        if p["status"] == 0:
+            case["psi6_abs"] = float(oracle.psi_abs_pair_sum(x[0], 6, p["g1"]))
+            case["psi4_abs"] = float(oracle.psi_abs_pair_sum(x[0], 4, p["g2"]))
+        cases.append(case)
+        print(f"dataset {i}: n = {n}, argmin {k0}", flush=True)
+    out = {
+        "_about": "FP64 oracle of the 512-dataset batch (datagen.batch(512, seed=4)): every "
+                  "dataset with n <= 16,384 and the 16 smallest above, LSCV_h on the 128-point "
+                  "grid over Z(h0) (argmin; g and both exponential sums at sampled indices) and "
+                  "the PLUGIN chain. Written by make_golden.py --batch; calls only the oracle.",
+        "count": 512, "seed": 4, "n_h": n_h, "cases": cases,
+    }
+    with open(os.path.join(HERE, "batch512_oracle.json"), "w") as f:
+        json.dump(out, f, separators=(",", ":"))
+
+
 def main():
+    if "--batch" in sys.argv:
+        batch_subset()
+        return
     if "--full-skewed" in sys.argv:
         full_skewed_column()
         return

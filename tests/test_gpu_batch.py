@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1505_01998_gb300 import datagen
-from tests._helpers import TOL, built_lib, g_err, lscv_A
+from tests._helpers import H_TOL, TOL, built_lib, g_err, lscv_A
 
 pytestmark = pytest.mark.gpu
 
@@ -223,3 +223,51 @@ def test_lscv_H_rejects_non_pd_and_asymmetric(kde):
     with pytest.raises(kde.KdeError) as e:
         kde.kde_lscv_H(x, np.array([[[1.0, 0.1], [0.2, 1.0]]]))
     assert e.value.status == kde.KDE_EINVAL
+
+
+def test_batch_workload_against_oracle(kde):
+    """The batched workload itself (datagen.batch(512, seed=4): 512 datasets of
+    256 to 131,072 samples, LSCV_h on the 128-point grid over Z(h0) plus
+    PLUGIN, one plan, the launch configuration the benchmark times) against
+    the FP64 oracle stored by tests/golden/make_golden.py --batch for every
+    dataset with n <= 16,384 and the 16 smallest above: g(h) at the stored
+    indices, the argmin (the same, or a near tie inside the stored window),
+    psi_6 and psi_4 relative to their magnitude scales, and the plug-in h
+    within the selected-bandwidth tolerance."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "batch512_oracle.json")))
+    n_h = gold["n_h"]
+    sets = datagen.batch(gold["count"], seed=gold["seed"])
+    xs = [dev(x) for x in sets]
+    grid, gk = kde.make_grid(n_h=n_h)
+    reqs, keep = [], [gk, xs]
+    for x in xs:
+        r, k = kde.make_request(x, LSCV | PLUGIN, grid)
+        reqs.append(r)
+        keep.append(k)
+    plan = kde.BatchPlan(reqs, keepalive=keep)
+    ws = kde.workspace(plan.ws_bytes)
+    out = plan.run(ws)
+    assert len(gold["cases"]) >= 300
+    for c in gold["cases"]:
+        i, n, idx = c["i"], c["n"], c["idx"]
+        res = out[i]
+        assert res["status"] == 0 and res["n_h"] == n_h, (i, res["status"])
+        h = oracle.grid_default(n, 1, n_h)[idx]
+        g = plan.g(ws, i, n_h)
+        err = g_err(g[idx], c["g"], c["s_kk"], c["s_k"], h, n, 1, c["A"])
+        assert err.max() < TOL, (i, n, err.max())
+        if res["argmin"] != c["argmin"]:
+            assert res["argmin"] in idx, (i, res["argmin"], c["argmin"])
+            g_ref = dict(zip(idx, c["g"]))
+            assert g_ref[res["argmin"]] - g_ref[c["argmin"]] <= TOL * max(abs(v) for v in c["g"]), i
+        p = c["plugin"]
+        assert c["plugin_status"] == 0
+        for key, mag_key, r, gk_ in (("psi6", "psi6_abs", 6, "g1"), ("psi4", "psi4_abs", 4, "g2")):
+            gp = p[gk_]
+            mag = (2 * c[mag_key] + n * abs(oracle.gauss_deriv(r, 0.0))) / (n * n * gp ** (r + 1))
+            assert abs(res[key] - p[key]) <= TOL * max(abs(p[key]), mag), (i, key, res[key], p[key])
+        # the plug-in h: the selected-bandwidth tolerance (psi_4 of these
+        # datasets cancels to as little as 1/400 of its magnitude scale)
+        assert abs(res["h_plugin"] - p["h"]) <= H_TOL * p["h"], (i, res["h_plugin"], p["h"])
