@@ -380,6 +380,9 @@ def serve_measure(rates, count, seeds, budget_gb, quantum, verbose=False, repeat
         rec["agreement"] = {"requests": sum(r["agreement"]["requests"] for r in runs),
                             "max_rel_diff_h": max(r["agreement"]["max_rel_diff_h"] for r in runs),
                             "lscv_argmin_differs": sum(r["agreement"]["lscv_argmin_differs"] for r in runs),
+                            "lscv_argmin_near_ties": sum(r["agreement"]["lscv_argmin_near_ties"] for r in runs),
+                            "lscv_argmin_gap_rel_max": max(r["agreement"]["lscv_argmin_gap_rel_max"]
+                                                           for r in runs),
                             "failures": sum(len(r["failures"]) for r in runs)}
         records.append(rec)
     best = max(r["served"]["requests_per_s"] for r in records)
@@ -416,6 +419,7 @@ def _serve_once(gbkde, torch, np, reqs, grid, arena, stream, quantum):
     lat = []
     plain_fail = {}
     plain_res = {}
+    plain_g = {}
     t0 = time.perf_counter()
     for k, r in enumerate(reqs):
         now = time.perf_counter() - t0
@@ -424,7 +428,7 @@ def _serve_once(gbkde, torch, np, reqs, grid, arena, stream, quantum):
         xd = torch.from_numpy(r.x).cuda()
         try:
             if r.method == "lscv":
-                plain_res[k] = gbkde.kde_lscv(xd, grid, None, ws, stream)[0]
+                plain_res[k], plain_g[k], _ = gbkde.kde_lscv(xd, grid, None, ws, stream)
             else:
                 plain_res[k] = gbkde.kde_plugin(xd, None, ws, stream)
         except gbkde.KdeError as e:
@@ -440,11 +444,23 @@ def _serve_once(gbkde, torch, np, reqs, grid, arena, stream, quantum):
     both = [k for k in served_res if k in plain_res]
     h_rel = max((abs(served_res[k]["h"] - plain_res[k]["h"]) / abs(plain_res[k]["h"]) for k in both),
                 default=0.0)
-    argmin_diff = sum(served_res[k]["argmin"] != plain_res[k]["argmin"] for k in both
-                      if reqs[k].method == "lscv")
+    differ = [k for k in both if reqs[k].method == "lscv"
+              and served_res[k]["argmin"] != plain_res[k]["argmin"]]
+    # a differing grid index is a near tie when the single call's own g at the
+    # served index is within the g tolerance (1e-5 of |g|) of its minimum: the
+    # two summation groupings (served items are capped in size) round apart
+    gaps = [(plain_g[k][served_res[k]["argmin"]] - plain_g[k][plain_res[k]["argmin"]])
+            / abs(plain_g[k][plain_res[k]["argmin"]]) for k in differ]
     return {"failures": failures,
             "agreement": {"requests": len(both), "max_rel_diff_h": h_rel,
-                          "lscv_argmin_differs": int(argmin_diff)},
+                          "lscv_argmin_differs": len(differ),
+                          "lscv_argmin_near_ties": int(sum(bool(g <= 1e-5) for g in gaps)),
+                          "lscv_argmin_gap_rel_max": float(max(gaps, default=0.0)),
+                          "lscv_argmin_differing": [
+                              {"n": int(reqs[k].n), "d": int(reqs[k].d),
+                               "served": int(served_res[k]["argmin"]),
+                               "single_call": int(plain_res[k]["argmin"]), "gap_rel": float(g)}
+                              for k, g in zip(differ, gaps)]},
             "served": {"requests_per_s": st["requests_per_s"], "p50_ms": st["p50_ms"],
                        "p99_ms": st["p99_ms"], "p50_wait_ms": st["p50_wait_ms"],
                        "evals_per_s": st["evals_per_s"], "active_max": st["active_max"],
