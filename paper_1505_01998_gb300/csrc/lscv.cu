@@ -108,13 +108,20 @@ __device__ __forceinline__ void octave_terms(float qv, const float2 (&nca)[3], f
 }
 
 // Columns [j_lo, j_hi) of one tile for this lane's R rows and B bandwidths.
-// Bandwidths are processed in pairs with packed FP32x2 arithmetic.
-template <int D, int B, int R, bool EDGE>
+// Bandwidths are processed in pairs with packed FP32x2 arithmetic.  ONE (a
+// grid of one bandwidth, B = 2, both halves of nc2[0] holding it): the two
+// halves of a packed evaluation take two pairs at that bandwidth instead of
+// a real and a padding bandwidth -- rows 2p, 2p + 1 (R even) or the two
+// columns of an iteration (wide samples) -- so t1/t2 .x and .y hold sums
+// of the same bandwidth over different pairs: half the exponentials and
+// bandwidth lane-operations of the padded form.
+template <int D, int B, int R, bool EDGE, bool ONE = false>
 __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j_lo, int j_hi,
                                              const float (&y)[R][D], const float2 (&nc2)[B / 2],
                                              float2 (&t1)[B / 2], float2 (&t2)[B / 2],
                                              int64_t i0, int64_t jg0, int64_t n) {
   constexpr int DP = DPad<D>::value;
+  static_assert(!ONE || (B == 2 && (D > 4 || R % 2 == 0)), "one-bandwidth pairing: B = 2, rows two by two");
   if constexpr (kPackedQ<D, R>) {
     // sF holds float2 (-v, -v) per coordinate: [T][DP]
     const float2* __restrict__ sF2 = reinterpret_cast<const float2*>(sF);
@@ -147,11 +154,11 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
           if (!(ia < j && j < n)) qa = __int_as_float(0x7f800000);  // +inf -> e = 0
           if (!(ib < j && j < n)) qb = __int_as_float(0x7f800000);
         }
-        q2[2 * p] = make_float2(qa, qa);
+        q2[2 * p] = ONE ? make_float2(qa, qb) : make_float2(qa, qa);
         q2[2 * p + 1] = make_float2(qb, qb);
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < R; r += (ONE ? 2 : 1)) {
 #pragma unroll
         for (int bp = 0; bp < B / 2; ++bp) {
           const float2 a = __fmul2_rn(q2[r], nc2[bp]);
@@ -184,8 +191,9 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
         }
         q2[c] = make_float2(qv, qv);
       }
+      if (ONE) q2[0].y = q2[1].x;
 #pragma unroll
-      for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < (ONE ? 1 : 2); ++c)
 #pragma unroll
         for (int bp = 0; bp < B / 2; ++bp) {
           const float2 a = __fmul2_rn(q2[c], nc2[bp]);
@@ -226,8 +234,12 @@ __device__ __forceinline__ void lscv_columns(const float* __restrict__ sF, int j
         }
         q2[r] = make_float2(acc, acc);
       }
+      if constexpr (ONE && R % 2 == 0) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+        for (int r = 0; r < R; r += 2) q2[r].y = q2[r + 1].x;
+      }
+#pragma unroll
+      for (int r = 0; r < R; r += (ONE ? 2 : 1)) {
 #pragma unroll
         for (int bp = 0; bp < B / 2; ++bp) {
           const float2 a = __fmul2_rn(q2[r], nc2[bp]);
@@ -371,7 +383,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
     const int64_t row = it - ph.off[di] + (ph.base ? ph.base[di] : 0);
     const int64_t tb = ds->lscv_t0 + row * ds->lscv_K;
     const int64_t te = min(tb + (int64_t)ds->lscv_K, ds->lscv_tiles);
-    const float2 nc2[1] = {make_float2(ds->nc[0], ds->nc[1])};
+    const bool one = ds->n_h == 1;  // two columns per packed evaluation (see lscv_columns)
+    const float2 nc2[1] = {make_float2(ds->nc[0], ds->nc[one ? 0 : 1])};
     float2 t1[1] = {make_float2(0.f, 0.f)}, t2[1] = {make_float2(0.f, 0.f)};
     float ks[4] = {0.f, 0.f, 0.f, 0.f}, kc[4] = {0.f, 0.f, 0.f, 0.f};  // Kahan (s, c): S1 b0, S1 b1, S2 b0, S2 b1
     const int64_t n = ds->n, n_pad = ds->n_pad;
@@ -402,10 +415,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
       }
       const bool edge = (q == l) || ((l + 1) * T > n);
       const int64_t i0 = q * T + lane, jg0 = l * T;
-      if (edge)
-        lscv_columns<D, B, 1, true>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
-      else
-        lscv_columns<D, B, 1, false>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+      if (one) {
+        if (edge)
+          lscv_columns<D, B, 1, true, true>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+        else
+          lscv_columns<D, B, 1, false, true>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+      } else {
+        if (edge)
+          lscv_columns<D, B, 1, true>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+        else
+          lscv_columns<D, B, 1, false>(sF, 0, T, y, nc2, t1, t2, i0, jg0, n);
+      }
       if (KAHAN && ++run >= 8) {  // runs of 256 terms
         kahan_add(ks[0], kc[0], t1[0].x);
         kahan_add(ks[1], kc[1], t1[0].y);
@@ -431,12 +451,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_lscv_warp(Phase ph) {
       }
     }
     if (lane == 0) {
-      // row layout of the block kernel: (S1, S2) of bandwidth 0, then of bandwidth 1
+      // row layout of the block kernel: (S1, S2) of bandwidth 0, then of
+      // bandwidth 1 (one bandwidth: both halves are bandwidth 0)
       double* out = ds->lscv_part + row * (2 * (int64_t)ds->n_h_pad);
-      out[0] = ff_value(tot[0]);
-      out[1] = ff_value(tot[2]);
-      out[2] = ff_value(tot[1]);
-      out[3] = ff_value(tot[3]);
+      if (one) {
+        out[0] = ff_value(tot[0]) + ff_value(tot[1]);
+        out[1] = ff_value(tot[2]) + ff_value(tot[3]);
+        out[2] = 0.0;
+        out[3] = 0.0;
+      } else {
+        out[0] = ff_value(tot[0]);
+        out[1] = ff_value(tot[2]);
+        out[2] = ff_value(tot[1]);
+        out[3] = ff_value(tot[3]);
+      }
     }
   }
 }
@@ -474,6 +502,9 @@ __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phas
     const int j_hi = active ? j_lo + cols : 0;
     const int hbase = (hg * kWarps + my_chunk) * B;
 
+    // a grid of one bandwidth (B = 2, rows paired; see lscv_columns)
+    constexpr bool kOne = (B == 2) && !OCT && (R % 2 == 0) && D <= 4;
+    const bool one = kOne && ds->n_h == 1;
     float2 nc2[B / 2], t1[B / 2], t2[B / 2];
     // octave grids: residues rb, rb + 1 of P; ex2 at octaves 7, 4 and 1; 9 running sums
     const int P = OCT ? ds->oct_P : 0;
@@ -488,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phas
     } else {
 #pragma unroll
       for (int bp = 0; bp < B / 2; ++bp) {
-        nc2[bp] = make_float2(ds->nc[hbase + 2 * bp], ds->nc[hbase + 2 * bp + 1]);
+        nc2[bp] = make_float2(ds->nc[hbase + 2 * bp], ds->nc[hbase + 2 * bp + (one ? 0 : 1)]);
         t1[bp] = make_float2(0.f, 0.f);
         t2[bp] = make_float2(0.f, 0.f);
       }
@@ -556,6 +587,11 @@ __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phas
           lscv_columns_oct<D, R, true>(sF, j_lo, j_hi, y, nca, oacc, i0, jg0, n);
         else
           lscv_columns_oct<D, R, false>(sF, j_lo, j_hi, y, nca, oacc, i0, jg0, n);
+      } else if (one) {
+        if (edge)
+          lscv_columns<D, B, R, true, kOne>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
+        else
+          lscv_columns<D, B, R, false, kOne>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
       } else {
         if (edge)
           lscv_columns<D, B, R, true>(sF, j_lo, j_hi, y, nc2, t1, t2, i0, jg0, n);
@@ -660,6 +696,18 @@ __global__ void __launch_bounds__(kThreads, (OCT && D <= 4) ? 3 : 2) k_lscv(Phas
           sRed[(warp * B + b) * 2] = ff_value(v1);
           sRed[(warp * B + b) * 2 + 1] = ff_value(v2);
         }
+      }
+    }
+    if (kOne && one) {
+      // one bandwidth: the second half's (S1, S2) join the first's; the
+      // padding slot is left empty
+      __syncwarp();
+      if (lane == 0) {
+        double* r0 = sRed + warp * B * 2;
+        r0[0] += r0[2];
+        r0[1] += r0[3];
+        r0[2] = 0.0;
+        r0[3] = 0.0;
       }
     }
     __syncthreads();
