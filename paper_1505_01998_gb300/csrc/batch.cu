@@ -352,6 +352,62 @@ void batch_free(kde_batch_plan* p) {
   delete p;
 }
 
+// g(H) of m bandwidth matrices (H: m x d x d) as one batch of one-point
+// grids at h = 1, through *plan: built on the first call or when m changes,
+// and afterwards reused with only the descriptors' matrices replaced (the
+// geometry and the pinned staging do not depend on H, so the results are
+// those of a freshly built plan).  Synchronises `st`.  The caller frees
+// *plan with batch_free.
+int lscv_H_eval(kde_batch_plan** plan, const void* x_dev, int dtype, int64_t n, int d, const double* H,
+                int m, const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st, double* g_host) {
+  if (!plan || !H || !g_host) return fail(KDE_EINVAL, "H or g is NULL");
+  if (m < 1 || m > KDE_MAX_NH) return fail(KDE_EINVAL, "m = %d outside [1, %d]", m, KDE_MAX_NH);
+  int rc = check_common(x_dev, dtype, n, d, ws);
+  if (rc) return rc;
+  for (int k = 0; k < m; ++k)
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        const double v = H[(size_t)k * d * d + a * d + b];
+        if (!std::isfinite(v) || v != H[(size_t)k * d * d + b * d + a])
+          return fail(KDE_EINVAL, "H[%d] not finite and symmetric", k);
+      }
+  kde_batch_plan* p = *plan;
+  if (p && (p->n_req != m || p->desc[0].x != x_dev || p->desc[0].n != n || p->desc[0].d != d ||
+            p->desc[0].dtype != dtype)) {
+    batch_free(p);
+    p = *plan = nullptr;
+  }
+  if (!p) {
+    std::vector<kde_request> reqs(m);
+    const double one = 1.0;
+    for (int k = 0; k < m; ++k)
+      reqs[k] = kde_request{x_dev, dtype, d, n, KDE_METHOD_LSCV, kde_grid{KDE_GRID_EXPLICIT, 1, &one, 0, 0}};
+    p = new (std::nothrow) kde_batch_plan();
+    if (!p) return fail(KDE_ENOMEM, "plan");
+    rc = batch_plan_build(reqs.data(), m, opts, H, p);
+    if (rc) {
+      batch_free(p);
+      return rc;
+    }
+    *plan = p;
+  } else {
+    for (int k = 0; k < m; ++k)
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b) p->desc[k].cov[a * d + b] = H[(size_t)k * d * d + a * d + b];
+  }
+  rc = batch_run(p, ws, ws_bytes, st, false);
+  if (rc) return rc;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  std::vector<kde_result> res(m);
+  batch_collect(p, res.data());
+  for (int k = 0; k < m; ++k) {
+    if (res[k].status != KDE_OK) return fail(res[k].status, "H[%d]: %s", k, kde_status_string(res[k].status));
+    g_host[k] = res[k].g_min;  // one grid point h = 1: g(H) itself
+  }
+  return KDE_OK;
+}
+
 }  // namespace gbkde
 
 extern "C" {
@@ -448,42 +504,9 @@ int kde_lscv_H_workspace_size(int64_t n, int d, int m, const kde_opts* opts, siz
 
 int kde_lscv_H(const void* x_dev, int dtype, int64_t n, int d, const double* H_host, int m,
                const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host) {
-  if (!H_host || !g_host) return fail(KDE_EINVAL, "H or g is NULL");
-  if (m < 1 || m > KDE_MAX_NH) return fail(KDE_EINVAL, "m = %d outside [1, %d]", m, KDE_MAX_NH);
-  int rc = check_common(x_dev, dtype, n, d, ws);
-  if (rc) return rc;
-  for (int k = 0; k < m; ++k)
-    for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) {
-        const double v = H_host[(size_t)k * d * d + a * d + b];
-        if (!std::isfinite(v) || v != H_host[(size_t)k * d * d + b * d + a])
-          return fail(KDE_EINVAL, "H[%d] not finite and symmetric", k);
-      }
-  std::vector<kde_request> reqs(m);
-  const double one = 1.0;
-  for (int k = 0; k < m; ++k)
-    reqs[k] = kde_request{x_dev, dtype, d, n, KDE_METHOD_LSCV, kde_grid{KDE_GRID_EXPLICIT, 1, &one, 0, 0}};
-  kde_batch_plan* p = new (std::nothrow) kde_batch_plan();
-  if (!p) return fail(KDE_ENOMEM, "plan");
-  rc = batch_plan_build(reqs.data(), m, opts, H_host, p);
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!rc) rc = batch_run(p, ws, ws_bytes, st, false);
-  if (!rc) {
-    cudaError_t e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
-  }
-  if (!rc) {
-    std::vector<kde_result> res(m);
-    batch_collect(p, res.data());
-    for (int k = 0; k < m; ++k) {
-      if (res[k].status != KDE_OK) {
-        rc = fail(res[k].status, "H[%d]: %s", k, kde_status_string(res[k].status));
-        break;
-      }
-      g_host[k] = res[k].g_min;  // one grid point h = 1: g(H) itself
-    }
-  }
-  batch_free(p);
+  kde_batch_plan* plan = nullptr;
+  const int rc = lscv_H_eval(&plan, x_dev, dtype, n, d, H_host, m, opts, ws, ws_bytes, (cudaStream_t)stream, g_host);
+  batch_free(plan);
   return rc;
 }
 

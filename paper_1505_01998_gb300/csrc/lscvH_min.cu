@@ -96,13 +96,24 @@ extern "C" int kde_lscv_H_minimize(const void* x_dev, int dtype, int64_t n, int 
   }
   cudaStream_t st = (cudaStream_t)stream;
   int evals = 0;
+  // one batch plan per pass size (the first simplex, the four candidates of
+  // an iteration, a shrink), built once and reused with new matrices: a pass
+  // then costs its launches and one synchronisation, not a plan (geometry,
+  // pinned staging) built and freed every time
+  struct Plans {
+    kde_batch_plan* by_m[3] = {nullptr, nullptr, nullptr};
+    ~Plans() {
+      for (kde_batch_plan* q : by_m) batch_free(q);
+    }
+  } plans;
   auto eval = [&](const std::vector<std::vector<double>>& pts, std::vector<double>* f) -> int {
     const int m = (int)pts.size();
     std::vector<double> Hs((size_t)m * d * d);
     for (int k = 0; k < m; ++k) theta_to_H(pts[k], d, Hs.data() + (size_t)k * d * d);
     f->assign(m, 0.0);
     evals += m;
-    return kde_lscv_H(x_dev, dtype, n, d, Hs.data(), m, opts, ws, ws_bytes, st, f->data());
+    const int slot = (m == 4) ? 0 : (m == p ? 1 : 2);
+    return lscv_H_eval(&plans.by_m[slot], x_dev, dtype, n, d, Hs.data(), m, opts, ws, ws_bytes, st, f->data());
   };
   std::vector<double> F;
   rc = eval(X, &F);
