@@ -46,6 +46,12 @@ struct kde_batch_plan {
   // host staging and graph
   unsigned char* pin_in = nullptr;   // image of ws[0, staged)
   unsigned char* pin_out = nullptr;  // copy of the descriptor table after a run
+  // one-shot plans (built, run once and freed inside one call) stage through
+  // pageable memory: a pinned allocation and its release cost far more than
+  // the copies of a few kilobytes they would speed up (kde_lscv_H at
+  // n = 16,384, d = 2: 436 -> 123 us per call with one matrix, 597 -> 271 us
+  // with four); plans that are kept and replayed stay pinned
+  bool pageable = false;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   void* bound_ws = nullptr;
@@ -196,9 +202,14 @@ int batch_plan_build(const kde_request* reqs, int n_req, const kde_opts* opts, c
 
 static int batch_bind(kde_batch_plan* p, unsigned char* ws) {
   if (!p->pin_in) {
-    if (cudaMallocHost(&p->pin_in, std::max<size_t>(p->staged, 256)) != cudaSuccess ||
-        cudaMallocHost(&p->pin_out, sizeof(DsDev) * p->n_req) != cudaSuccess)
+    if (p->pageable) {
+      p->pin_in = new (std::nothrow) unsigned char[std::max<size_t>(p->staged, 256)];
+      p->pin_out = new (std::nothrow) unsigned char[sizeof(DsDev) * p->n_req];
+      if (!p->pin_in || !p->pin_out) return fail(KDE_ENOMEM, "batch: host staging");
+    } else if (cudaMallocHost(&p->pin_in, std::max<size_t>(p->staged, 256)) != cudaSuccess ||
+               cudaMallocHost(&p->pin_out, sizeof(DsDev) * p->n_req) != cudaSuccess) {
       return fail(KDE_ENOMEM, "batch: pinned host staging");
+    }
   }
   unsigned char* img = p->pin_in;
   memset(img, 0, p->staged);
@@ -347,19 +358,26 @@ void batch_free(kde_batch_plan* p) {
   if (!p) return;
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->cap) cudaStreamDestroy(p->cap);
-  if (p->pin_in) cudaFreeHost(p->pin_in);
-  if (p->pin_out) cudaFreeHost(p->pin_out);
+  if (p->pageable) {
+    delete[] p->pin_in;
+    delete[] p->pin_out;
+  } else {
+    if (p->pin_in) cudaFreeHost(p->pin_in);
+    if (p->pin_out) cudaFreeHost(p->pin_out);
+  }
   delete p;
 }
 
 // g(H) of m bandwidth matrices (H: m x d x d) as one batch of one-point
 // grids at h = 1, through *plan: built on the first call or when m changes,
 // and afterwards reused with only the descriptors' matrices replaced (the
-// geometry and the pinned staging do not depend on H, so the results are
-// those of a freshly built plan).  Synchronises `st`.  The caller frees
-// *plan with batch_free.
-int lscv_H_eval(kde_batch_plan** plan, const void* x_dev, int dtype, int64_t n, int d, const double* H,
-                int m, const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st, double* g_host) {
+// geometry and the staging do not depend on H, so the results are those of
+// a freshly built plan).  keep: the plan will be reused (pinned staging);
+// otherwise it stages through pageable memory.  Synchronises `st`.  The
+// caller frees *plan with batch_free.
+int lscv_H_eval(kde_batch_plan** plan, bool keep, const void* x_dev, int dtype, int64_t n, int d,
+                const double* H, int m, const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st,
+                double* g_host) {
   if (!plan || !H || !g_host) return fail(KDE_EINVAL, "H or g is NULL");
   if (m < 1 || m > KDE_MAX_NH) return fail(KDE_EINVAL, "m = %d outside [1, %d]", m, KDE_MAX_NH);
   int rc = check_common(x_dev, dtype, n, d, ws);
@@ -384,6 +402,7 @@ int lscv_H_eval(kde_batch_plan** plan, const void* x_dev, int dtype, int64_t n, 
       reqs[k] = kde_request{x_dev, dtype, d, n, KDE_METHOD_LSCV, kde_grid{KDE_GRID_EXPLICIT, 1, &one, 0, 0}};
     p = new (std::nothrow) kde_batch_plan();
     if (!p) return fail(KDE_ENOMEM, "plan");
+    p->pageable = !keep;
     rc = batch_plan_build(reqs.data(), m, opts, H, p);
     if (rc) {
       batch_free(p);
@@ -477,6 +496,7 @@ int kde_select_batch(const kde_request* reqs, int n_req, const kde_opts* opts, v
   kde_batch_plan* p = nullptr;
   int rc = kde_batch_plan_create(reqs, n_req, opts, &p, nullptr);
   if (rc) return rc;
+  p->pageable = true;  // built, run once and freed here
   rc = batch_run(p, ws, ws_bytes, (cudaStream_t)stream, false);
   if (!rc) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
@@ -505,7 +525,8 @@ int kde_lscv_H_workspace_size(int64_t n, int d, int m, const kde_opts* opts, siz
 int kde_lscv_H(const void* x_dev, int dtype, int64_t n, int d, const double* H_host, int m,
                const kde_opts* opts, void* ws, size_t ws_bytes, void* stream, double* g_host) {
   kde_batch_plan* plan = nullptr;
-  const int rc = lscv_H_eval(&plan, x_dev, dtype, n, d, H_host, m, opts, ws, ws_bytes, (cudaStream_t)stream, g_host);
+  const int rc = lscv_H_eval(&plan, false, x_dev, dtype, n, d, H_host, m, opts, ws, ws_bytes,
+                             (cudaStream_t)stream, g_host);
   batch_free(plan);
   return rc;
 }

@@ -70,7 +70,8 @@ bool tuned_lookup(int mode, int d, int n_h, int64_t n, kde_opts* out);
 // Batch machinery shared with the autotuner and the LSCV_H minimiser (batch.cu).
 int batch_run(kde_batch_plan* p, void* ws, size_t ws_bytes, cudaStream_t st, bool use_graph);
 void batch_free(kde_batch_plan* p);
-int lscv_H_eval(kde_batch_plan** plan, const void* x_dev, int dtype, int64_t n, int d, const double* H,
-                int m, const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st, double* g_host);
+int lscv_H_eval(kde_batch_plan** plan, bool keep, const void* x_dev, int dtype, int64_t n, int d,
+                const double* H, int m, const kde_opts* opts, void* ws, size_t ws_bytes, cudaStream_t st,
+                double* g_host);
 
 }  // namespace gbkde

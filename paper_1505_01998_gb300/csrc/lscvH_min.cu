@@ -113,7 +113,8 @@ extern "C" int kde_lscv_H_minimize(const void* x_dev, int dtype, int64_t n, int 
     f->assign(m, 0.0);
     evals += m;
     const int slot = (m == 4) ? 0 : (m == p ? 1 : 2);
-    return lscv_H_eval(&plans.by_m[slot], x_dev, dtype, n, d, Hs.data(), m, opts, ws, ws_bytes, st, f->data());
+    return lscv_H_eval(&plans.by_m[slot], true, x_dev, dtype, n, d, Hs.data(), m, opts, ws, ws_bytes, st,
+                       f->data());
   };
   std::vector<double> F;
   rc = eval(X, &F);
