@@ -200,6 +200,25 @@ def test_lscv_H_general_matrices_vs_oracle(kde, d):
         assert abs(g[k] - ref) <= TOL * scale * 10 ** 0, (k, g[k], ref)
 
 
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [3001, 5000])
+def test_lscv_H_one_point_pairing_at_larger_n(kde, d, n):
+    """Above n = 2,048 (tiles of 128, four rows per lane) each one-point grid
+    of LSCV_H pairs rows two by two in the packed evaluation instead of
+    adding a padding bandwidth; d = 4 takes the packed squared-distance path.
+    Against the oracle, with a ragged tail at n = 3,001."""
+    x = datagen.correlated_mixture(n, d, seed=40 + d)
+    x64 = x.astype(np.float32).astype(np.float64)
+    _, S = oracle.mean_cov(x64)
+    Hs = np.array([0.05 * S, 0.3 * S])
+    g = kde.kde_lscv_H(dev(x), Hs)
+    for k, H in enumerate(Hs):
+        ref = oracle.lscv_H(x64, H)
+        ckk = (4 * math.pi) ** (-d / 2) / math.sqrt(np.linalg.det(H))
+        scale = max(abs(ref), ckk / n)
+        assert abs(g[k] - ref) <= TOL * scale, (d, n, k, g[k], ref)
+
+
 def test_lscv_H_at_scaled_covariance_equals_lscv_h(kde):
     n, d = 1200, 2
     x = datagen.correlated_mixture(n, d, seed=4)
