@@ -188,7 +188,7 @@ def _lscv_check(kde, x, h, opts=None, dtype="float32"):
     err = g_err(g, ref["g"], ref["s_kk"], ref["s_k"], h, n, d, A)
     assert err.max() < TOL, (err.max(), int(err.argmax()))
     # exponential sums over the whole triangle
-    T = opts.tile if (opts and opts.tile) else (32 if n <= 2048 else 128)
+    T = kde.kde_item_tiles(n, d, len(h), opts, h=h)["lscv_tile"]
     tiles = kde.kde_tile_count(n, T)
     s1, s2 = kde.kde_lscv_tile_sums(xd, h, 0, tiles, opts)
     npairs = n * (n - 1) // 2
@@ -228,10 +228,12 @@ def test_lscv_dims_sizes_grids(kde, d, n, n_h):
 
 
 @pytest.mark.parametrize("d", [1, 3, 6, 16])
-@pytest.mark.parametrize("n,n_h", [(1100, 1), (2000, 2)])
+@pytest.mark.parametrize("n,n_h", [(1100, 1), (2000, 2), (3001, 1), (5000, 2)])
 def test_lscv_one_and_two_point_grids(kde, d, n, n_h):
     """Grids of one or two points take 2 bandwidths per thread (one g(H) of
-    LSCV_H is such a grid); d = 6 and 16 also prefetch the next tile's rows."""
+    LSCV_H is such a grid); d = 6 and 16 also prefetch the next tile's rows;
+    above n = 2,048 d <= 4 takes tiles of 256 (8 rows per lane) and a
+    one-point grid pairs rows in the packed evaluation."""
     x = datagen.correlated_mixture(n, d, seed=500 + d + n)
     h = oracle.grid_default(n, d, 8)[3:3 + n_h]
     _lscv_check(kde, x, h)
