@@ -339,3 +339,36 @@ def test_normal_tail_approximation_of_the_range_aggregates():
     Q = np.where(t >= 0, q, np.float32(1.0) - q).astype(np.float64)
     ref = 0.5 * erfc(t.astype(np.float64) / np.sqrt(2.0))
     assert np.abs(Q - ref).max() < 4e-7
+
+
+@pytest.mark.parametrize("R,RG", [(2, 1), (8, 1), (8, 2)])
+def test_psi_edge_masks_in_tile_local_indices(R, RG):
+    """The psi kernel masks the pairs of edge tiles (the diagonal and the
+    ragged last column) by tile-local 32-bit indices: lane row
+    il = il0 + 64 p (+ 32 for the second of a packed pair) with
+    il0 = row-group offset + lane on a diagonal tile and -2^30 off it, column
+    jl within the tile, kept when il < jl < jlim, jlim = min(T, n - l T).
+    Replayed here for every lane, packed pair and column of the edge tiles of
+    ragged sizes against the global rule i < j < n with i, j sample indices."""
+    T = 32 * R * RG
+    SL = 8 // RG
+    for n in (T + 1, 2 * T - 7, 3 * T, 3 * T + 5):
+        NT = (n + T - 1) // T
+        for l in range(NT):
+            for q in range(l + 1):
+                edge = q == l or (l + 1) * T > n
+                if not edge:
+                    continue
+                jlim = min(T, n - l * T)
+                for warp in range(8):
+                    rg = warp // SL
+                    r0 = rg * 32 * R  # + lane below
+                    for lane in range(32):
+                        il0 = (r0 + lane) if q == l else -(1 << 30)
+                        for p in range(R // 2):
+                            for half in (0, 1):
+                                il = il0 + 64 * p + 32 * half
+                                i = q * T + r0 + lane + 64 * p + 32 * half
+                                for jl in range(T):
+                                    j = l * T + jl
+                                    assert (il < jl < jlim) == (i < j < n), (n, l, q, warp, lane, p, half, jl)
